@@ -1,0 +1,209 @@
+/*
+ * claire.h -- C-ABI of the GB300 (sm_103a) hot path of the reduced-space Gauss--Newton--Krylov solver for
+ * stationary-velocity diffeomorphic image registration (Mang, Gholami, Davatzikos, Biros, "CLAIRE",
+ * arXiv 1808.04487).
+ *
+ * Problem (Sec. 2.1, Eq. (2)): find a stationary velocity v on the periodic box [0, 2*pi)^3 minimising
+ *     J(v) = 1/2 <m_1 - m_R, m_1 - m_R> + beta/2 sum_c <v_c, A v_c>,
+ * where m_1 = m(t = 1) and m solves the transport equation d_t m + grad m . v = 0, m(0) = m_T, optionally with
+ * div v = 0 (Leray projection K, Sec. 2.2). The calls below evaluate the transport solves (Eq. (2), (4)), the
+ * reduced gradient (Eq. (5)), the Gauss--Newton Hessian matvec (Eq. (7)-(9), Sec. 2.3.2), the spectral
+ * preconditioner (Sec. 2.3.3) and the full inexact GN--Krylov solve (Alg. 1, Alg. 2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid        n = (n1, n2, n3), every n_a even and >= 4; node x = (2 pi i1/n1, 2 pi i2/n2, 2 pi i3/n3).
+ * Scalars     C-ordered [n1][n2][n3] arrays, i3 fastest (N = n1*n2*n3 values).
+ * Vectors     planar [3][n1][n2][n3] arrays; component c points along axis c (3N values).
+ * Precision   the _f32 calls take float arrays and the _f64 calls double arrays; a context is created for one
+ *             precision (claire_opts.precision) and rejects calls of the other with CLAIRE_EINVAL.
+ *             Reductions (objective, inner products, norms, PCG scalars, Armijo test) accumulate in FP64.
+ * Memory      unless a call says otherwise, every array argument is a DEVICE pointer (cudaMalloc'd or from a
+ *             framework allocator) on the current device, owned by the caller; the library never frees or keeps
+ *             caller memory beyond the call. The context owns its own workspace (allocated by claire_create).
+ * Streams     calls enqueue work on the caller's cudaStream_t (passed as void*; NULL = legacy default stream)
+ *             and return without synchronising, except where a host scalar or report is returned: those calls
+ *             synchronise that stream before returning.
+ * Errors      no exception crosses the ABI; every call returns a claire_status. On failure the context keeps a
+ *             message readable with claire_last_error(). Inputs are not validated for NaN on the device, but
+ *             a non-finite objective, gradient norm or PCG scalar makes the solver return CLAIRE_ENAN.
+ * Threads     a context is not thread safe; use one context per host thread (or serialise calls).
+ * Discrete    inner product <a, b> = h1 h2 h3 sum a*b; forward FFT unnormalised, inverse scaled by 1/N;
+ * readings    first-order spectral symbols use k' (Nyquist set to 0), even-order symbols the full k; RK2 (Heun)
+ *             characteristics; tricubic Lagrange interpolation on the 4^3 stencil b-1..b+2 around b = floor(xi)
+ *             with periodic wrap; trapezoidal time quadrature on n_t + 1 nodes.
+ */
+#ifndef CLAIRE_GB300_H
+#define CLAIRE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CLAIRE_OK = 0,
+    CLAIRE_EINVAL = 1,       /* bad argument: null pointer, odd or < 4 grid size, nt < 1, beta <= 0, wrong dtype */
+    CLAIRE_ENOMEM = 2,       /* device or host allocation failed in claire_create */
+    CLAIRE_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed; see claire_last_error */
+    CLAIRE_ENAN = 4,         /* a non-finite objective, gradient norm or PCG scalar was produced */
+    CLAIRE_ENOTCONV = 5,     /* register: max_gn Gauss-Newton iterations reached; v holds the last iterate */
+    CLAIRE_ELINESEARCH = 6,  /* register: Armijo failed after max_ls trials; v holds the last accepted iterate */
+    CLAIRE_EBREAKDOWN = 7    /* PCG: <s, H s> <= 0 (reported in the report's flags; the solve continues) */
+} claire_status;
+
+typedef enum { CLAIRE_F32 = 0, CLAIRE_F64 = 1 } claire_precision;
+
+/* Solver parameters (Sec. 2.3.2, Table 2). claire_default_opts fills the paper's defaults. */
+typedef struct {
+    int n[3];            /* grid size n1, n2, n3 (even, >= 4) */
+    int precision;       /* claire_precision */
+    double beta;         /* regularisation weight beta_v > 0 */
+    int nt;              /* number of semi-Lagrangian time steps (default 4, Sec. 2.3.1) */
+    int regnorm;         /* 1: H1 seminorm, A = -Laplacian; 2: H2 seminorm, A = Laplacian^2 (Sec. 2.1) */
+    int divfree;         /* 0: K = I; 1: div v = 0 via the Leray projection K = I - grad Lap^-1 div (Sec. 2.2) */
+    double gtol_rel;     /* eps_g: stop when ||g_k|| <= eps_g ||g(v=0)|| (default 5e-2, Sec. 2.3.2) */
+    double gtol_abs;     /* stop when ||g_k|| <= gtol_abs (default 1e-6, Sec. 2.3.2) */
+    int max_gn;          /* Gauss-Newton iteration cap (default 50, Sec. 4.4) */
+    int max_krylov;      /* PCG iteration cap per GN step (default 100, Sec. 4.4) */
+    double pcg_rtol;     /* > 0: fixed relative PCG tolerance; <= 0: eps_H = min(0.5, sqrt(||g_k||/||g_0||)) (Alg. 2) */
+    int max_ls;          /* Armijo trials (default 10); alpha starts at 1 and is halved */
+    double armijo_c1;    /* sufficient-decrease constant (default 1e-4) */
+} claire_opts;
+
+/* What claire_register reports (the quantities of Table 3 plus timing). Host struct, filled on return. */
+typedef struct {
+    int gn_iters;        /* Gauss-Newton iterations taken */
+    int matvecs;         /* Hessian matvecs (each = one incremental state + one incremental adjoint solve) */
+    int pde_solves;      /* transport solves: gradient 2 (+1 per accepted step), matvec 2, line-search trial 1 */
+    int ls_trials;       /* objective evaluations in the Armijo search */
+    int pcg_breakdowns;  /* PCG iterations stopped by <s, H s> <= 0 */
+    int converged;       /* 1 if a gradient tolerance was met */
+    double J0, J;        /* objective at the initial guess and at the returned v */
+    double mismatch0;    /* 1/2 ||m_T - m_R||^2 (v = 0) */
+    double mismatch;     /* 1/2 ||m_1 - m_R||^2 at the returned v */
+    double gnorm0;       /* ||g(v = 0)||, the reference of the relative stopping test */
+    double gnorm;        /* ||g|| at the returned v */
+    double ms_total;     /* wall time of the call on the stream, milliseconds (CUDA events) */
+} claire_report;
+
+typedef struct claire_ctx claire_ctx;
+
+/* Fill *opts with the paper's defaults for grid n (beta = 1e-2, nt = 4, H1, no constraint, eps_g = 5e-2, ...). */
+claire_status claire_default_opts(claire_opts* opts, int n1, int n2, int n3, int precision);
+
+/* Validate *opts, build FFT plans (twiddle tables computed on the host in FP64) and allocate the context's
+ * device workspace for grid opts->n. The context keeps a copy of *opts. Returns CLAIRE_EINVAL for bad options,
+ * CLAIRE_ENOMEM / CLAIRE_ECUDA on allocation failure (then *out is NULL). Uses the current CUDA device. */
+claire_status claire_create(const claire_opts* opts, claire_ctx** out);
+
+/* Free the context and its workspace (synchronises the device first). NULL is accepted. */
+claire_status claire_destroy(claire_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none). The pointer stays valid until the next call on ctx. */
+const char* claire_last_error(const claire_ctx* ctx);
+
+/* Bytes of device workspace the context holds. */
+size_t claire_workspace_bytes(const claire_ctx* ctx);
+
+/* ---- transport (Eq. (2) state, Eq. (4) continuity-form adjoint; Sec. 2.3.1 semi-Lagrangian RK2) ----------------
+ * dir = +1: m1 = m(t=1) of d_t m + grad m . v = 0 with m(0) = m0 (state equation, n_t steps forward).
+ * dir = -1: m1 = lambda(t=0) of -d_t lambda - div(lambda v) = 0 with lambda(1) = m0 (adjoint, n_t steps backward;
+ *           the div v source is dropped when opts.divfree = 1). m0, m1: scalars; v: vector. m0 and m1 may alias. */
+claire_status claire_transport_f32(claire_ctx* ctx, const float* m0, const float* v, int dir, float* m1, void* stream);
+claire_status claire_transport_f64(claire_ctx* ctx, const double* m0, const double* v, int dir, double* m1, void* stream);
+
+/* ---- reduced gradient (Eq. (5); Alg. 1 lines 2-5) ----------------------------------------------------------
+ * Solves the state forward and the adjoint backward at v and writes g = beta A v + K[int_0^1 lambda grad m dt]
+ * (vector). If J is not NULL the objective J(v) is written to *J (host double; the call then synchronises).
+ * The linearisation at v (departure points, state history and its gradients) stays cached in the context for
+ * claire_hessvec_cached_*. */
+claire_status claire_gradient_f32(claire_ctx* ctx, const float* mT, const float* mR, const float* v, float* g,
+                                  double* J, void* stream);
+claire_status claire_gradient_f64(claire_ctx* ctx, const double* mT, const double* mR, const double* v, double* g,
+                                  double* J, void* stream);
+
+/* ---- Gauss-Newton Hessian matvec (Eq. (7) with Eq. (8), (9); lambda terms dropped, Sec. 2.3.2) --------------
+ * Hvt = beta A vt + K[int_0^1 lambda~ grad m dt] at the linearisation point v. claire_hessvec_* re-linearises at
+ * (mT, v) first (departure points, state solve, spectral gradients of the state history); mR is not used by the
+ * Gauss-Newton approximation and may be NULL. vt and Hvt are vectors and must not alias. */
+claire_status claire_hessvec_f32(claire_ctx* ctx, const float* mT, const float* mR, const float* v, const float* vt,
+                                 float* Hvt, void* stream);
+claire_status claire_hessvec_f64(claire_ctx* ctx, const double* mT, const double* mR, const double* v,
+                                 const double* vt, double* Hvt, void* stream);
+/* Same matvec at the linearisation cached by the last claire_gradient_* / claire_linearize_* / claire_hessvec_*
+ * call on ctx (CLAIRE_EINVAL if there is none). This is the operator PCG applies (Alg. 2 lines 6-8). */
+claire_status claire_hessvec_cached_f32(claire_ctx* ctx, const float* vt, float* Hvt, void* stream);
+claire_status claire_hessvec_cached_f64(claire_ctx* ctx, const double* vt, double* Hvt, void* stream);
+/* Cache the linearisation at (mT, v) without computing anything else. */
+claire_status claire_linearize_f32(claire_ctx* ctx, const float* mT, const float* v, void* stream);
+claire_status claire_linearize_f64(claire_ctx* ctx, const double* mT, const double* v, void* stream);
+
+/* ---- spectral preconditioner (Sec. 2.3.3 and its Remark) -----------------------------------------------------
+ * z = (beta A)^-1 r in the Fourier domain, the zero eigenvalue of beta A (k = 0) replaced by 1. r, z: vectors;
+ * they may alias. */
+claire_status claire_precond_f32(claire_ctx* ctx, const float* r, float* z, void* stream);
+claire_status claire_precond_f64(claire_ctx* ctx, const double* r, double* z, void* stream);
+
+/* ---- full inexact Gauss-Newton-Krylov solve (Alg. 1 with Alg. 2, Armijo line search, Sec. 2.3.2) -------------
+ * v is in/out: on entry the initial guess (zeros = the plain method), on return the solution. The relative
+ * stopping test always uses ||g(v = 0)|| (Sec. 2.3.2), also for a nonzero initial guess. rep (host) may be NULL.
+ * Returns CLAIRE_OK on convergence, CLAIRE_ENOTCONV when max_gn is reached, CLAIRE_ELINESEARCH when Armijo
+ * fails (v = last accepted iterate), CLAIRE_ENAN on a non-finite objective or gradient. Synchronises stream. */
+claire_status claire_register_f32(claire_ctx* ctx, const float* mT, const float* mR, float* v, claire_report* rep,
+                                  void* stream);
+claire_status claire_register_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
+                                  claire_report* rep, void* stream);
+/* Same solve with HOST arrays (pageable or pinned): mT, mR and v are copied to the context's device buffers on
+ * stream, the solve runs, and v is copied back before the call returns. */
+claire_status claire_register_host_f32(claire_ctx* ctx, const float* mT, const float* mR, float* v,
+                                       claire_report* rep, void* stream);
+claire_status claire_register_host_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
+                                       claire_report* rep, void* stream);
+
+/* ---- building blocks exposed for testing and for callers composing their own solver --------------------------
+ * claire_departure_*: RK2 departure points of one time step (dt = 1/nt) in grid units, disp = (X - x) / h per
+ *   axis (dir = +1: state characteristics X of v; dir = -1: adjoint characteristics Y of -v). v, disp: vectors.
+ * claire_interp_*: out(x) = tricubic Lagrange interpolant of f at x + disp(x) (grid units, periodic).
+ * claire_spectral_*: op = 0 gradient (scalar in, vector out), 1 divergence (vector in, scalar out),
+ *   2 Leray projection K (vector -> vector), 3 A = regnorm operator (vector -> vector), 4 Laplacian
+ *   (scalar -> scalar). in and out must not alias.
+ * claire_objective_*: *J = 1/2 <m1 - mR, m1 - mR> + beta/2 sum_c <v_c, A v_c> (host double; synchronises).
+ * claire_dot_*: *out = <a, b> = h1 h2 h3 sum a*b over count values, accumulated in FP64 (host double;
+ *   synchronises). */
+claire_status claire_departure_f32(claire_ctx* ctx, const float* v, int dir, float* disp, void* stream);
+claire_status claire_departure_f64(claire_ctx* ctx, const double* v, int dir, double* disp, void* stream);
+claire_status claire_interp_f32(claire_ctx* ctx, const float* f, const float* disp, float* out, void* stream);
+claire_status claire_interp_f64(claire_ctx* ctx, const double* f, const double* disp, double* out, void* stream);
+claire_status claire_spectral_f32(claire_ctx* ctx, int op, const float* in, float* out, void* stream);
+claire_status claire_spectral_f64(claire_ctx* ctx, int op, const double* in, double* out, void* stream);
+claire_status claire_objective_f32(claire_ctx* ctx, const float* m1, const float* mR, const float* v, double* J,
+                                   void* stream);
+claire_status claire_objective_f64(claire_ctx* ctx, const double* m1, const double* mR, const double* v, double* J,
+                                   void* stream);
+claire_status claire_dot_f32(claire_ctx* ctx, const float* a, const float* b, long long count, double* out,
+                             void* stream);
+claire_status claire_dot_f64(claire_ctx* ctx, const double* a, const double* b, long long count, double* out,
+                             void* stream);
+
+/* Unnormalised forward 3D real FFT of a scalar (Sec. 2.3.1): spec is the half spectrum [n1][n2][n3/2+1] of
+ * interleaved (re, im) pairs, i.e. 2*n1*n2*(n3/2+1) values. claire_ifft_* is the inverse, scaled by 1/N; it
+ * reads spec as a Hermitian half spectrum and does not modify it. */
+claire_status claire_fft_f32(claire_ctx* ctx, const float* f, float* spec, void* stream);
+claire_status claire_fft_f64(claire_ctx* ctx, const double* f, double* spec, void* stream);
+claire_status claire_ifft_f32(claire_ctx* ctx, const float* spec, float* f, void* stream);
+claire_status claire_ifft_f64(claire_ctx* ctx, const double* spec, double* f, void* stream);
+
+/* Number of kernel launches the library has made on this context since claire_create. */
+typedef struct {
+    long long launches;
+} claire_counters;
+claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLAIRE_GB300_H */

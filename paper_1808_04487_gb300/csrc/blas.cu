@@ -1,0 +1,155 @@
+// Streaming vector kernels of the Krylov and Gauss-Newton loops (Alg. 1, Alg. 2): FP64-accumulated inner products
+// (warp-shuffle + shared-memory block reduction into a fixed number of partials, then a one-block deterministic
+// finish, so results are reproducible run to run) and the fused PCG updates.
+#include "impl.cuh"
+
+namespace claire {
+
+__device__ __forceinline__ void block_partial(double acc, double* __restrict__ partials) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    partials[blockIdx.x] = t;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dot(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                             double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += double(a[i]) * double(b[i]);
+  block_partial(acc, partials);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_diffsq(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                                double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double e = double(a[i]) - double(b[i]);
+    acc += e * e;
+  }
+  block_partial(acc, partials);
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partials, int np, double scale,
+                                                       double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *out = scale * t;
+  }
+}
+
+template <class T>
+__global__ void k_axpy(long long n, T a, const T* __restrict__ x, T* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+template <class T>
+__global__ void k_xpay(long long n, const T* __restrict__ x, T a, T* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, y[i], x[i]);
+}
+template <class T>
+__global__ void k_waxpy(long long n, const T* __restrict__ x, T a, const T* __restrict__ y, T* __restrict__ z) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = fma(a, y[i], x[i]);
+}
+template <class T>
+__global__ void k_scale_copy(long long n, T a, const T* __restrict__ x, T* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+template <class T>
+__global__ void __launch_bounds__(256) k_pcg_update(long long n, T k, const T* __restrict__ s,
+                                                    const T* __restrict__ Hs, T* __restrict__ vt, T* __restrict__ r,
+                                                    double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    vt[i] = fma(k, s[i], vt[i]);
+    const T ri = fma(-k, Hs[i], r[i]);
+    r[i] = ri;
+    acc += double(ri) * double(ri);
+  }
+  block_partial(acc, partials);
+}
+
+static inline unsigned stream_blocks(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < 8 * 152 * 4 ? b : 8 * 152 * 4);
+}
+
+template <class T>
+claire_status dot_partial(claire_ctx* c, const T* a, const T* b, long long n, double* partials, cudaStream_t st) {
+  k_dot<T><<<kReduceBlocks, 256, 0, st>>>(a, b, n, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status diffsq_partial(claire_ctx* c, const T* a, const T* b, long long n, double* partials, cudaStream_t st) {
+  k_diffsq<T><<<kReduceBlocks, 256, 0, st>>>(a, b, n, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+claire_status reduce_final(claire_ctx* c, const double* partials, double scale, double* out, cudaStream_t st) {
+  k_reduce_final<<<1, 1024, 0, st>>>(partials, kReduceBlocks, scale, out);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T> claire_status axpy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st) {
+  k_axpy<T><<<stream_blocks(n), kThreads, 0, st>>>(n, T(a), x, y);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T> claire_status xpay(claire_ctx* c, long long n, const T* x, double a, T* y, cudaStream_t st) {
+  k_xpay<T><<<stream_blocks(n), kThreads, 0, st>>>(n, x, T(a), y);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status waxpy(claire_ctx* c, long long n, const T* x, double a, const T* y, T* z, cudaStream_t st) {
+  k_waxpy<T><<<stream_blocks(n), kThreads, 0, st>>>(n, x, T(a), y, z);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status pcg_update(claire_ctx* c, long long n, double k, const T* s, const T* Hs, T* vt, T* r, double* partials,
+                         cudaStream_t st) {
+  k_pcg_update<T><<<kReduceBlocks, 256, 0, st>>>(n, T(k), s, Hs, vt, r, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st) {
+  k_scale_copy<T><<<stream_blocks(n), kThreads, 0, st>>>(n, T(a), x, y);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+
+#define INST(T)                                                                                                   \
+  template claire_status dot_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);       \
+  template claire_status diffsq_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);    \
+  template claire_status axpy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);                     \
+  template claire_status xpay<T>(claire_ctx*, long long, const T*, double, T*, cudaStream_t);                     \
+  template claire_status waxpy<T>(claire_ctx*, long long, const T*, double, const T*, T*, cudaStream_t);          \
+  template claire_status pcg_update<T>(claire_ctx*, long long, double, const T*, const T*, T*, T*, double*,       \
+                                       cudaStream_t);                                                             \
+  template claire_status scale_copy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace claire

@@ -1,0 +1,147 @@
+// Internal interfaces between the translation units of the library (not part of the C-ABI).
+#pragma once
+
+#include <string>
+
+#include "common.cuh"
+
+namespace claire {
+
+// Twiddle tables and radix schedules of the three 1D passes of a 3D real FFT (Sec. 2.3.1 spectral operators).
+template <class T> struct FFTPlan {
+  RadixPlan ax1{}, ax2{}, ax3{};  // complex lengths n1, n2 and n3/2
+  cplx<T>* tw1 = nullptr;          // exp(-2 pi i t / n1), t < n1
+  cplx<T>* tw2 = nullptr;          // exp(-2 pi i t / n2), t < n2
+  cplx<T>* tw3 = nullptr;          // exp(-2 pi i t / n3), t < n3 (the z pass uses every other entry)
+  int ti12 = 16;                   // columns per CTA of the strided passes
+  int lpc3 = 16;                   // lines per CTA of the contiguous pass
+};
+
+// Device workspace of one context (all owned by the context arena).
+template <class T> struct Work {
+  T* dX = nullptr;      // [3][N] state departure displacement (grid units)
+  T* dY = nullptr;      // [3][N] adjoint departure displacement
+  T* m = nullptr;       // [nt+1][N] state history
+  T* gm = nullptr;      // [nt+1][3][N] spectral gradients of the state history
+  T* rho = nullptr;     // [N] div v (only without the div v = 0 constraint)
+  T* la = nullptr;      // [N] adjoint ping
+  T* lb = nullptr;      // [N] adjoint pong
+  T* ra = nullptr;      // [N] rho * adjoint ping
+  T* rb = nullptr;      // [N] rho * adjoint pong
+  T* b = nullptr;       // [3][N] time integral accumulator
+  cplx<T>* spec = nullptr;  // 6 half spectra of Ns values
+  T* g = nullptr;       // solver vectors, [3][N] each
+  T* vt = nullptr;
+  T* r = nullptr;
+  T* z = nullptr;
+  T* s = nullptr;
+  T* Hs = nullptr;
+  T* vtrial = nullptr;
+  T* vdev = nullptr;    // device copy of v for the host-array API
+  T* mTdev = nullptr;   // [N]
+  T* mRdev = nullptr;   // [N]
+  T* m1trial = nullptr; // [N] final state of a line-search trial
+  double* partials = nullptr;  // reduction partials
+  double* scal = nullptr;      // device scalars
+};
+
+constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs
+constexpr int kThreads = 256;
+
+}  // namespace claire
+
+struct claire_ctx {
+  claire_opts o{};
+  claire::Dims d{};
+  claire::Counters counters{};
+  std::string err;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  size_t arena_used = 0;
+  claire::FFTPlan<float> pf{};
+  claire::FFTPlan<double> pd{};
+  claire::Work<float> wf{};
+  claire::Work<double> wd{};
+  bool lin_valid = false;
+  double* hscal = nullptr;  // pinned host mirror of Work::scal
+  void set_error(const std::string& s) { err = s; }
+  template <class T> claire::Work<T>& work();
+  template <class T> claire::FFTPlan<T>& plan();
+  void* take(size_t bytes) {
+    size_t off = (arena_used + 255) & ~size_t(255);
+    if (off + bytes > arena_bytes) return nullptr;
+    arena_used = off + bytes;
+    return arena + off;
+  }
+};
+template <> inline claire::Work<float>& claire_ctx::work<float>() { return wf; }
+template <> inline claire::Work<double>& claire_ctx::work<double>() { return wd; }
+template <> inline claire::FFTPlan<float>& claire_ctx::plan<float>() { return pf; }
+template <> inline claire::FFTPlan<double>& claire_ctx::plan<double>() { return pd; }
+
+namespace claire {
+
+// ---- fft.cu ---------------------------------------------------------------------------------------------------
+bool radix_plan(int L, RadixPlan& p);
+template <class T> size_t fft_table_bytes(const Dims& d);
+template <class T> claire_status fft_init(claire_ctx* c);
+// forward R2C of a scalar: in [N] real -> out [Ns] half spectrum (unnormalised)
+template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* out, cudaStream_t st);
+// inverse C2R: spec [Ns] (overwritten) -> out [N], multiplied by `scale` (1/N for the true inverse)
+template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st);
+
+// ---- spectral.cu ----------------------------------------------------------------------------------------------
+template <class T> claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G1, cplx<T>* G2,
+                                           cudaStream_t st);
+template <class T> claire_status spec_div(claire_ctx* c, const cplx<T>* V0, const cplx<T>* V1, const cplx<T>* V2,
+                                          cplx<T>* D, cudaStream_t st);
+template <class T> claire_status spec_leray(claire_ctx* c, cplx<T>* V0, cplx<T>* V1, cplx<T>* V2, cudaStream_t st);
+// mode 0: V *= scale * a(k); mode 1: V *= 1/(beta a(k)) (1 where a = 0); mode 2: V *= -|k|^2 (Laplacian)
+template <class T> claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp, long long comp_stride, int mode,
+                                            double beta, cudaStream_t st);
+// B = beta a(k) V + K^ B (K^ = I or Leray)
+template <class T> claire_status spec_combine(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st);
+// partial sums of sum_c sum_{half k} w(k3) a(k) |V_c(k)|^2 into partials[kReduceBlocks]
+template <class T> claire_status spec_reg_partial(claire_ctx* c, const cplx<T>* V, double* partials, cudaStream_t st);
+
+// ---- sl.cu ----------------------------------------------------------------------------------------------------
+template <class T> claire_status sl_hadamard(claire_ctx* c, const T* a, const T* x, T* y, cudaStream_t st);
+template <class T> claire_status sl_departure(claire_ctx* c, const T* v, int dir, T* disp, cudaStream_t st);
+template <class T> claire_status sl_interp(claire_ctx* c, const T* f, const T* disp, T* out, cudaStream_t st);
+// lam = mR - m1; optionally rl = rho*lam; b = w * lam * gm  (terminal condition of the adjoint, Eq. (4))
+template <class T> claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR, const T* m1, const T* rho, T* lam,
+                                                     T* rl, T* b, const T* gmj, T w, cudaStream_t st);
+// one backward continuity step along Y; rho/rl_next: div source (or null); lam/rl: stores (or null);
+// b: accumulation b += w lam grad m (or null)
+template <class T> claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next, const T* rho,
+                                                 const T* dY, T* lam, T* rl, T* b, const T* gmj, T w,
+                                                 cudaStream_t st);
+// q^0 = -(dt/2) vt . grad m^0
+template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, const T* gm0, T* q, cudaStream_t st);
+// m~^{j+1} = q^j(X) + dt/2 f^{j+1}; writes q^{j+1}, or on the last step lam~ = -m~, rho*lam~, b = w lam~ grad m
+template <class T> claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* vt, const T* gmj1,
+                                                  T* qout, bool last, const T* rho, T* rl, T* b, T w,
+                                                  cudaStream_t st);
+
+// ---- blas.cu --------------------------------------------------------------------------------------------------
+// partials[kReduceBlocks] of sum a*b (FP64 accumulation); a == b allowed
+template <class T> claire_status dot_partial(claire_ctx* c, const T* a, const T* b, long long n, double* partials,
+                                             cudaStream_t st);
+// partials of sum (a - b)^2
+template <class T> claire_status diffsq_partial(claire_ctx* c, const T* a, const T* b, long long n, double* partials,
+                                                cudaStream_t st);
+// out[slot] = scale * sum(partials[0..kReduceBlocks))
+claire_status reduce_final(claire_ctx* c, const double* partials, double scale, double* out, cudaStream_t st);
+// y = a*x + y
+template <class T> claire_status axpy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st);
+// y = x + a*y
+template <class T> claire_status xpay(claire_ctx* c, long long n, const T* x, double a, T* y, cudaStream_t st);
+// z = x + a*y
+template <class T> claire_status waxpy(claire_ctx* c, long long n, const T* x, double a, const T* y, T* z,
+                                       cudaStream_t st);
+// vt += k s; r -= k Hs; partials of ||r||^2
+template <class T> claire_status pcg_update(claire_ctx* c, long long n, double k, const T* s, const T* Hs, T* vt, T* r,
+                                            double* partials, cudaStream_t st);
+template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st);
+
+}  // namespace claire

@@ -1,0 +1,858 @@
+// Operators and the inexact Gauss-Newton-Krylov solver on top of the kernels, and the C-ABI entry points.
+//
+// Memory-reduced Gauss-Newton (Sec. 3.5): the state history m^j and its spectral gradients are kept per
+// linearisation (departure points are computed once per v, Sec. 3.4); the adjoint and incremental adjoint are
+// never stored in time, their time integrals are accumulated during the backward sweeps. The host drives the
+// outer (Alg. 1) and inner (Alg. 2) loops; every scalar it needs (objective, norms, PCG scalars, Armijo test)
+// is reduced in FP64 on the device and read back once per use.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "impl.cuh"
+
+using namespace claire;
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+inline double cellvol(const Dims& d) { return kTwoPi * kTwoPi * kTwoPi / double(d.N); }
+
+template <class T> claire_status alloc_work(claire_ctx* c) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N, Ns = c->d.Ns;
+  const int nt = c->o.nt;
+  auto takeT = [&](T*& p, long long count) -> bool {
+    p = static_cast<T*>(c->take(sizeof(T) * size_t(count)));
+    return p != nullptr;
+  };
+  bool ok = true;
+  ok &= takeT(W.dX, 3 * N);
+  ok &= takeT(W.dY, 3 * N);
+  ok &= takeT(W.m, (nt + 1) * N);
+  ok &= takeT(W.gm, 3 * (nt + 1) * N);
+  if (!c->o.divfree) ok &= takeT(W.rho, N);
+  ok &= takeT(W.la, N);
+  ok &= takeT(W.lb, N);
+  ok &= takeT(W.ra, N);
+  ok &= takeT(W.rb, N);
+  ok &= takeT(W.b, 3 * N);
+  W.spec = static_cast<cplx<T>*>(c->take(sizeof(cplx<T>) * size_t(6 * Ns)));
+  ok &= W.spec != nullptr;
+  for (T** p : {&W.g, &W.vt, &W.r, &W.z, &W.s, &W.Hs, &W.vtrial, &W.vdev}) ok &= takeT(*p, 3 * N);
+  ok &= takeT(W.mTdev, N);
+  ok &= takeT(W.mRdev, N);
+  ok &= takeT(W.m1trial, N);
+  W.partials = static_cast<double*>(c->take(sizeof(double) * kReduceBlocks));
+  W.scal = static_cast<double*>(c->take(sizeof(double) * 32));
+  ok &= W.partials != nullptr && W.scal != nullptr;
+  if (!ok) {
+    c->set_error("workspace arena too small");
+    return CLAIRE_ENOMEM;
+  }
+  return CLAIRE_OK;
+}
+
+template <class T> size_t work_bytes(const claire_opts& o, const Dims& d) {
+  const long long N = d.N, Ns = d.Ns;
+  const int nt = o.nt;
+  long long elems = 3 * N * 2 + (nt + 1) * N + 3 * (nt + 1) * N + (o.divfree ? 0 : N) + 4 * N + 3 * N + 8 * 3 * N +
+                    3 * N;
+  size_t bytes = sizeof(T) * size_t(elems) + sizeof(cplx<T>) * size_t(6 * Ns) +
+                 sizeof(double) * (kReduceBlocks + 32) + fft_table_bytes<T>(d) + 64 * 256;
+  return bytes;
+}
+
+// Read scal[slot] to the host (synchronises the stream).
+claire_status read_scalar(claire_ctx* c, double* dev, double* out, cudaStream_t st) {
+  CL_CUDA(c, cudaMemcpyAsync(c->hscal, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CL_CUDA(c, cudaStreamSynchronize(st));
+  *out = c->hscal[0];
+  return CLAIRE_OK;
+}
+
+// <a, b> = h1 h2 h3 sum a b over n values (FP64)
+template <class T> claire_status inner(claire_ctx* c, const T* a, const T* b, long long n, double* out, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  CL_TRY(dot_partial<T>(c, a, b, n, W.partials, st));
+  CL_TRY(reduce_final(c, W.partials, cellvol(c->d), W.scal, st));
+  return read_scalar(c, W.scal, out, st);
+}
+
+template <class T> inline T* comp(T* v, const Dims& d, int k) { return v + (long long)k * d.N; }
+template <class T> inline const T* comp(const T* v, const Dims& d, int k) { return v + (long long)k * d.N; }
+
+// ---------------------------------------------------------------------------------------------------------------
+// spectral building blocks
+template <class T> claire_status grad_spectral(claire_ctx* c, const T* f, T* out, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const Dims& d = c->d;
+  cplx<T>* S = W.spec;
+  const T inv = T(1.0 / double(d.N));
+  CL_TRY(fft_r2c<T>(c, f, S, st));
+  CL_TRY(spec_grad<T>(c, S, S + d.Ns, S + 2 * d.Ns, S + 3 * d.Ns, st));
+  for (int k = 0; k < 3; ++k) CL_TRY(fft_c2r<T>(c, S + (k + 1) * d.Ns, comp(out, d, k), inv, st));
+  return CLAIRE_OK;
+}
+
+template <class T> claire_status vec_r2c(claire_ctx* c, const T* v, cplx<T>* S, cudaStream_t st) {
+  for (int k = 0; k < 3; ++k) CL_TRY(fft_r2c<T>(c, comp(v, c->d, k), S + k * c->d.Ns, st));
+  return CLAIRE_OK;
+}
+template <class T> claire_status vec_c2r(claire_ctx* c, cplx<T>* S, T* v, cudaStream_t st) {
+  const T inv = T(1.0 / double(c->d.N));
+  for (int k = 0; k < 3; ++k) CL_TRY(fft_c2r<T>(c, S + k * c->d.Ns, comp(v, c->d, k), inv, st));
+  return CLAIRE_OK;
+}
+
+template <class T> claire_status div_spectral(claire_ctx* c, const T* v, T* out, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const Dims& d = c->d;
+  cplx<T>* S = W.spec;
+  CL_TRY(vec_r2c<T>(c, v, S, st));
+  CL_TRY(spec_div<T>(c, S, S + d.Ns, S + 2 * d.Ns, S + 3 * d.Ns, st));
+  return fft_c2r<T>(c, S + 3 * d.Ns, out, T(1.0 / double(d.N)), st);
+}
+
+template <class T> claire_status leray_inplace(claire_ctx* c, const T* v, T* out, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  cplx<T>* S = W.spec;
+  const long long Ns = c->d.Ns;
+  CL_TRY(vec_r2c<T>(c, v, S, st));
+  CL_TRY(spec_leray<T>(c, S, S + Ns, S + 2 * Ns, st));
+  return vec_c2r<T>(c, S, out, st);
+}
+
+// z = M^-1 r (Sec. 2.3.3)
+template <class T> claire_status precond_apply(claire_ctx* c, const T* r, T* z, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  CL_TRY(vec_r2c<T>(c, r, W.spec, st));
+  CL_TRY(spec_scale<T>(c, W.spec, 3, c->d.Ns, 1, c->o.beta, st));
+  return vec_c2r<T>(c, W.spec, z, st);
+}
+
+// out = beta A v + K b (the spectral tail of Eq. (5) and Eq. (7)); b is consumed
+template <class T> claire_status spectral_tail(claire_ctx* c, const T* v, const T* b, T* out, double* reg,
+                                               cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long Ns = c->d.Ns;
+  cplx<T>* V = W.spec;
+  cplx<T>* B = W.spec + 3 * Ns;
+  CL_TRY(vec_r2c<T>(c, v, V, st));
+  if (reg) {
+    // beta/2 sum_c <v_c, A v_c> by Parseval: h^3/N sum_k a(k) |v^(k)|^2
+    CL_TRY(spec_reg_partial<T>(c, V, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(c->d.N), W.scal + 1, st));
+  }
+  CL_TRY(vec_r2c<T>(c, b, B, st));
+  CL_TRY(spec_combine<T>(c, V, B, st));
+  return vec_c2r<T>(c, B, out, st);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// state solve along X into the history W.m (m^0 = mT)
+template <class T> claire_status state_history(claire_ctx* c, const T* mT, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  if (W.m != mT) CL_CUDA(c, cudaMemcpyAsync(W.m, mT, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  for (int j = 0; j < c->o.nt; ++j) CL_TRY(sl_interp<T>(c, W.m + j * N, W.dX, W.m + (j + 1) * N, st));
+  return CLAIRE_OK;
+}
+
+// the part of the linearisation that the state history does not cover: Y, grad m^j, div v
+template <class T> claire_status finish_linearization(claire_ctx* c, const T* v, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  CL_TRY(sl_departure<T>(c, v, -1, W.dY, st));
+  for (int j = 0; j <= c->o.nt; ++j) CL_TRY(grad_spectral<T>(c, W.m + j * N, W.gm + 3LL * j * N, st));
+  if (!c->o.divfree) CL_TRY(div_spectral<T>(c, v, W.rho, st));
+  c->lin_valid = true;
+  return CLAIRE_OK;
+}
+
+template <class T> claire_status linearize(claire_ctx* c, const T* mT, const T* v, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  c->lin_valid = false;
+  CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+  CL_TRY(state_history<T>(c, mT, st));
+  return finish_linearization<T>(c, v, st);
+}
+
+inline double tweight(int j, int nt) { return (j == 0 || j == nt) ? 0.5 / nt : 1.0 / nt; }
+
+// adjoint backward from lam^{nt} = mR - m^{nt}; b = sum_j w_j lam^j grad m^j (Eq. (4), (5))
+template <class T> claire_status adjoint_integral(claire_ctx* c, const T* mR, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  const int nt = c->o.nt;
+  T* lam[2] = {W.la, W.lb};
+  T* rl[2] = {W.ra, W.rb};
+  const T* rho = c->o.divfree ? nullptr : W.rho;
+  CL_TRY(sl_adjoint_terminal<T>(c, mR, W.m + nt * N, rho, lam[0], rl[0], W.b, W.gm + 3LL * nt * N,
+                                T(tweight(nt, nt)), st));
+  int cur = 0;
+  for (int j = nt - 1; j >= 0; --j) {
+    const bool store = j > 0;
+    CL_TRY(sl_adjoint_step<T>(c, lam[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? lam[1 - cur] : nullptr,
+                              (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)), st));
+    cur = 1 - cur;
+  }
+  return CLAIRE_OK;
+}
+
+// g = beta A v + K b; if J != nullptr also the objective (synchronises)
+template <class T> claire_status gradient_at_lin(claire_ctx* c, const T* mR, const T* v, T* g, double* J,
+                                                 cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  if (J) {
+    CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+  }
+  CL_TRY(adjoint_integral<T>(c, mR, st));
+  CL_TRY(spectral_tail<T>(c, v, W.b, g, J ? W.scal : nullptr, st));
+  if (J) {
+    // scal[0] mismatch, scal[1] regularisation (written by spectral_tail into scal + 1)
+    CL_CUDA(c, cudaMemcpyAsync(c->hscal, W.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CL_CUDA(c, cudaStreamSynchronize(st));
+    *J = c->hscal[0] + c->hscal[1];
+  }
+  return CLAIRE_OK;
+}
+
+// Gauss-Newton matvec at the cached linearisation (Eq. (7)-(9), lambda terms dropped)
+template <class T> claire_status hessvec_at_lin(claire_ctx* c, const T* vt, T* Hvt, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  const int nt = c->o.nt;
+  T* buf[2] = {W.la, W.lb};
+  T* rl[2] = {W.ra, W.rb};
+  const T* rho = c->o.divfree ? nullptr : W.rho;
+  int cur = 0;
+  CL_TRY(sl_incstate_init<T>(c, vt, W.gm, buf[cur], st));
+  for (int j = 0; j < nt; ++j) {
+    const bool last = j == nt - 1;
+    CL_TRY(sl_incstate_step<T>(c, buf[cur], W.dX, vt, W.gm + 3LL * (j + 1) * N, buf[1 - cur], last, rho,
+                               rl[1 - cur], W.b, T(tweight(nt, nt)), st));
+    cur = 1 - cur;
+  }
+  for (int j = nt - 1; j >= 0; --j) {
+    const bool store = j > 0;
+    CL_TRY(sl_adjoint_step<T>(c, buf[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? buf[1 - cur] : nullptr,
+                              (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)),
+                              st));
+    cur = 1 - cur;
+  }
+  return spectral_tail<T>(c, vt, W.b, Hvt, nullptr, st);
+}
+
+// state at a trial v (departure X + state history) and its objective; one PDE solve
+template <class T> claire_status evaluate(claire_ctx* c, const T* mT, const T* mR, const T* v, double* J,
+                                          cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  c->lin_valid = false;
+  CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+  CL_TRY(state_history<T>(c, mT, st));
+  CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
+  CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+  CL_TRY(vec_r2c<T>(c, v, W.spec, st));
+  CL_TRY(spec_reg_partial<T>(c, W.spec, W.partials, st));
+  CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(N), W.scal + 1, st));
+  CL_CUDA(c, cudaMemcpyAsync(c->hscal, W.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CL_CUDA(c, cudaStreamSynchronize(st));
+  *J = c->hscal[0] + c->hscal[1];
+  return CLAIRE_OK;
+}
+
+// Alg. 2: PCG for H vt = -g with M^-1 = (beta A)^-1; relative break ||r|| < eps_H ||r_0||
+template <class T> claire_status pcg(claire_ctx* c, const T* g, double eps_H, claire_report* rep, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long n3 = 3 * c->d.N;
+  CL_CUDA(c, cudaMemsetAsync(W.vt, 0, sizeof(T) * n3, st));
+  CL_TRY(scale_copy<T>(c, n3, -1.0, g, W.r, st));
+  CL_TRY(precond_apply<T>(c, W.r, W.z, st));
+  CL_CUDA(c, cudaMemcpyAsync(W.s, W.z, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+  double rz, rr0;
+  CL_TRY(inner<T>(c, W.r, W.z, n3, &rz, st));
+  CL_TRY(inner<T>(c, W.r, W.r, n3, &rr0, st));
+  const double r0 = std::sqrt(rr0);
+  if (!std::isfinite(rz) || !std::isfinite(r0)) {
+    c->set_error("non-finite PCG scalar");
+    return CLAIRE_ENAN;
+  }
+  for (int it = 0; it < c->o.max_krylov; ++it) {
+    CL_TRY(hessvec_at_lin<T>(c, W.s, W.Hs, st));
+    rep->matvecs++;
+    rep->pde_solves += 2;
+    double sHs;
+    CL_TRY(inner<T>(c, W.s, W.Hs, n3, &sHs, st));
+    if (!std::isfinite(sHs)) {
+      c->set_error("non-finite <s, Hs>");
+      return CLAIRE_ENAN;
+    }
+    if (!(sHs > 0.0)) {
+      rep->pcg_breakdowns++;
+      if (it == 0) CL_CUDA(c, cudaMemcpyAsync(W.vt, W.s, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+      break;
+    }
+    const double kappa = rz / sHs;
+    CL_TRY(pcg_update<T>(c, n3, kappa, W.s, W.Hs, W.vt, W.r, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, cellvol(c->d), W.scal, st));
+    double rr;
+    CL_TRY(read_scalar(c, W.scal, &rr, st));
+    if (std::sqrt(rr) < eps_H * r0) break;
+    CL_TRY(precond_apply<T>(c, W.r, W.z, st));
+    double rz_new;
+    CL_TRY(inner<T>(c, W.r, W.z, n3, &rz_new, st));
+    const double mu = rz_new / rz;
+    rz = rz_new;
+    CL_TRY(xpay<T>(c, n3, W.z, mu, W.s, st));
+  }
+  return CLAIRE_OK;
+}
+
+// Alg. 1 with Armijo backtracking and the stopping rules of Sec. 2.3.2
+template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
+                                              cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N, n3 = 3 * N;
+  const claire_opts& o = c->o;
+  std::memset(rep, 0, sizeof(*rep));
+  cudaEvent_t e0, e1;
+  CL_CUDA(c, cudaEventCreate(&e0));
+  CL_CUDA(c, cudaEventCreate(&e1));
+  CL_CUDA(c, cudaEventRecord(e0, st));
+  claire_status status = CLAIRE_OK;
+  do {
+    // mismatch of the template
+    CL_TRY(diffsq_partial<T>(c, mT, mR, N, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+    CL_TRY(read_scalar(c, W.scal, &rep->mismatch0, st));
+    // reference gradient at v = 0
+    double vv;
+    CL_TRY(inner<T>(c, v, v, n3, &vv, st));
+    CL_CUDA(c, cudaMemsetAsync(W.vtrial, 0, sizeof(T) * n3, st));
+    CL_TRY(linearize<T>(c, mT, W.vtrial, st));
+    double J;
+    CL_TRY(gradient_at_lin<T>(c, mR, W.vtrial, W.g, &J, st));
+    rep->pde_solves += 2;
+    double gg;
+    CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
+    rep->gnorm0 = std::sqrt(gg);
+    if (vv > 0.0) {
+      CL_TRY(linearize<T>(c, mT, v, st));
+      CL_TRY(gradient_at_lin<T>(c, mR, v, W.g, &J, st));
+      rep->pde_solves += 2;
+      CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
+    }
+    rep->J0 = J;
+    double gnorm = std::sqrt(gg);
+    if (!std::isfinite(J) || !std::isfinite(gnorm)) {
+      c->set_error("non-finite objective or gradient");
+      status = CLAIRE_ENAN;
+      break;
+    }
+    while (true) {
+      if (gnorm <= o.gtol_rel * rep->gnorm0 || gnorm <= o.gtol_abs) {
+        rep->converged = 1;
+        break;
+      }
+      if (rep->gn_iters >= o.max_gn) {
+        status = CLAIRE_ENOTCONV;
+        break;
+      }
+      const double eps_H = o.pcg_rtol > 0 ? o.pcg_rtol : std::fmin(0.5, std::sqrt(gnorm / rep->gnorm0));
+      CL_TRY(pcg<T>(c, W.g, eps_H, rep, st));
+      if (o.divfree) CL_TRY(leray_inplace<T>(c, W.vt, W.vt, st));
+      double gvt;
+      CL_TRY(inner<T>(c, W.g, W.vt, n3, &gvt, st));
+      double alpha = 1.0, Jt = 0.0;
+      bool accepted = false;
+      for (int t = 0; t < o.max_ls; ++t) {
+        CL_TRY(waxpy<T>(c, n3, v, alpha, W.vt, W.vtrial, st));
+        CL_TRY(evaluate<T>(c, mT, mR, W.vtrial, &Jt, st));
+        rep->ls_trials++;
+        rep->pde_solves++;
+        if (!std::isfinite(Jt)) {
+          c->set_error("non-finite objective in the line search");
+          status = CLAIRE_ENAN;
+          break;
+        }
+        if (Jt <= J + o.armijo_c1 * alpha * gvt) {
+          accepted = true;
+          break;
+        }
+        alpha *= 0.5;
+      }
+      if (status != CLAIRE_OK) break;
+      if (!accepted) {
+        status = CLAIRE_ELINESEARCH;
+        // restore the linearisation at the last accepted v for the report
+        CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+        CL_TRY(state_history<T>(c, mT, st));
+        break;
+      }
+      CL_CUDA(c, cudaMemcpyAsync(v, W.vtrial, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+      // the accepted trial's state history is the state at the new v; only the adjoint solve is new
+      CL_TRY(finish_linearization<T>(c, v, st));
+      CL_TRY(gradient_at_lin<T>(c, mR, v, W.g, nullptr, st));
+      rep->pde_solves += 1;
+      J = Jt;
+      CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
+      gnorm = std::sqrt(gg);
+      rep->gn_iters++;
+      if (!std::isfinite(gnorm)) {
+        c->set_error("non-finite gradient norm");
+        status = CLAIRE_ENAN;
+        break;
+      }
+    }
+    rep->J = J;
+    rep->gnorm = gnorm;
+    CL_TRY(diffsq_partial<T>(c, W.m + o.nt * N, mR, N, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+    CL_TRY(read_scalar(c, W.scal, &rep->mismatch, st));
+  } while (false);
+  CL_CUDA(c, cudaEventRecord(e1, st));
+  CL_CUDA(c, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CL_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+  rep->ms_total = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
+}
+
+template <class T> claire_status transport_dev(claire_ctx* c, const T* m0, const T* v, int dir, T* m1,
+                                               cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  const int nt = c->o.nt;
+  c->lin_valid = false;
+  T* buf[2] = {W.la, W.lb};
+  if (dir > 0) {
+    CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+    const T* src = m0;
+    int cur = 0;
+    for (int j = 0; j < nt; ++j) {
+      T* dst = buf[cur];
+      CL_TRY(sl_interp<T>(c, src, W.dX, dst, st));
+      src = dst;
+      cur = 1 - cur;
+    }
+    CL_CUDA(c, cudaMemcpyAsync(m1, src, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    return CLAIRE_OK;
+  }
+  CL_TRY(sl_departure<T>(c, v, -1, W.dY, st));
+  const T* rho = nullptr;
+  T* rl[2] = {W.ra, W.rb};
+  if (!c->o.divfree) {
+    CL_TRY(div_spectral<T>(c, v, W.rho, st));
+    rho = W.rho;
+  }
+  CL_CUDA(c, cudaMemcpyAsync(buf[0], m0, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  if (rho) CL_TRY(sl_hadamard<T>(c, rho, buf[0], rl[0], st));
+  int cur = 0;
+  for (int j = 0; j < nt; ++j) {
+    CL_TRY(sl_adjoint_step<T>(c, buf[cur], rho ? rl[cur] : nullptr, rho, W.dY, buf[1 - cur], rho ? rl[1 - cur] : nullptr,
+                              nullptr, nullptr, T(0), st));
+    cur = 1 - cur;
+  }
+  CL_CUDA(c, cudaMemcpyAsync(m1, buf[cur], sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  return CLAIRE_OK;
+}
+
+template <class T> claire_status objective_dev(claire_ctx* c, const T* m1, const T* mR, const T* v, double* J,
+                                               cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  CL_TRY(diffsq_partial<T>(c, m1, mR, N, W.partials, st));
+  CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+  CL_TRY(vec_r2c<T>(c, v, W.spec, st));
+  CL_TRY(spec_reg_partial<T>(c, W.spec, W.partials, st));
+  CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(N), W.scal + 1, st));
+  CL_CUDA(c, cudaMemcpyAsync(c->hscal, W.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CL_CUDA(c, cudaStreamSynchronize(st));
+  *J = c->hscal[0] + c->hscal[1];
+  return CLAIRE_OK;
+}
+
+template <class T> claire_status spectral_dev(claire_ctx* c, int op, const T* in, T* out, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const Dims& d = c->d;
+  cplx<T>* S = W.spec;
+  switch (op) {
+    case 0: return grad_spectral<T>(c, in, out, st);
+    case 1: return div_spectral<T>(c, in, out, st);
+    case 2: return leray_inplace<T>(c, in, out, st);
+    case 3:
+      CL_TRY(vec_r2c<T>(c, in, S, st));
+      CL_TRY(spec_scale<T>(c, S, 3, d.Ns, 0, 1.0, st));
+      return vec_c2r<T>(c, S, out, st);
+    case 4:
+      CL_TRY(fft_r2c<T>(c, in, S, st));
+      CL_TRY(spec_scale<T>(c, S, 1, d.Ns, 2, 1.0, st));
+      return fft_c2r<T>(c, S, out, T(1.0 / double(d.N)), st);
+    default: c->set_error("unknown spectral op"); return CLAIRE_EINVAL;
+  }
+}
+
+template <class T> bool is_prec(const claire_ctx* c);
+template <> bool is_prec<float>(const claire_ctx* c) { return c->o.precision == CLAIRE_F32; }
+template <> bool is_prec<double>(const claire_ctx* c) { return c->o.precision == CLAIRE_F64; }
+
+#define CHECK_CTX(ctx, T)                                                                    \
+  do {                                                                                       \
+    if (!(ctx)) return CLAIRE_EINVAL;                                                        \
+    if (!is_prec<T>(ctx)) {                                                                  \
+      (ctx)->set_error("context precision does not match the call");                         \
+      return CLAIRE_EINVAL;                                                                  \
+    }                                                                                        \
+  } while (0)
+#define CHECK_PTR(ctx, p)                                                                    \
+  do {                                                                                       \
+    if (!(p)) {                                                                              \
+      (ctx)->set_error("null pointer argument: " #p);                                        \
+      return CLAIRE_EINVAL;                                                                  \
+    }                                                                                        \
+  } while (0)
+
+template <class T> claire_status api_transport(claire_ctx* c, const T* m0, const T* v, int dir, T* m1, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, m0);
+  CHECK_PTR(c, v);
+  CHECK_PTR(c, m1);
+  if (dir != 1 && dir != -1) {
+    c->set_error("dir must be +1 or -1");
+    return CLAIRE_EINVAL;
+  }
+  return transport_dev<T>(c, m0, v, dir, m1, (cudaStream_t)s);
+}
+template <class T> claire_status api_gradient(claire_ctx* c, const T* mT, const T* mR, const T* v, T* g, double* J,
+                                              void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, mR);
+  CHECK_PTR(c, v);
+  CHECK_PTR(c, g);
+  CL_TRY(linearize<T>(c, mT, v, (cudaStream_t)s));
+  return gradient_at_lin<T>(c, mR, v, g, J, (cudaStream_t)s);
+}
+template <class T> claire_status api_linearize(claire_ctx* c, const T* mT, const T* v, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, v);
+  return linearize<T>(c, mT, v, (cudaStream_t)s);
+}
+template <class T> claire_status api_hessvec_cached(claire_ctx* c, const T* vt, T* Hvt, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, vt);
+  CHECK_PTR(c, Hvt);
+  if (!c->lin_valid) {
+    c->set_error("no cached linearisation");
+    return CLAIRE_EINVAL;
+  }
+  if ((const void*)vt == (const void*)Hvt) {
+    c->set_error("vt and Hvt must not alias");
+    return CLAIRE_EINVAL;
+  }
+  return hessvec_at_lin<T>(c, vt, Hvt, (cudaStream_t)s);
+}
+template <class T> claire_status api_hessvec(claire_ctx* c, const T* mT, const T* v, const T* vt, T* Hvt, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, v);
+  CL_TRY(linearize<T>(c, mT, v, (cudaStream_t)s));
+  return api_hessvec_cached<T>(c, vt, Hvt, s);
+}
+template <class T> claire_status api_precond(claire_ctx* c, const T* r, T* z, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, r);
+  CHECK_PTR(c, z);
+  return precond_apply<T>(c, r, z, (cudaStream_t)s);
+}
+template <class T> claire_status api_register(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
+                                              void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, mR);
+  CHECK_PTR(c, v);
+  claire_report local;
+  return register_dev<T>(c, mT, mR, v, rep ? rep : &local, (cudaStream_t)s);
+}
+template <class T> claire_status api_register_host(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
+                                                   void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, mR);
+  CHECK_PTR(c, v);
+  Work<T>& W = c->work<T>();
+  cudaStream_t st = (cudaStream_t)s;
+  const long long N = c->d.N;
+  CL_CUDA(c, cudaMemcpyAsync(W.mTdev, mT, sizeof(T) * N, cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaMemcpyAsync(W.mRdev, mR, sizeof(T) * N, cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaMemcpyAsync(W.vdev, v, sizeof(T) * 3 * N, cudaMemcpyHostToDevice, st));
+  claire_report local;
+  claire_status stat = register_dev<T>(c, W.mTdev, W.mRdev, W.vdev, rep ? rep : &local, st);
+  if (stat != CLAIRE_OK && stat != CLAIRE_ENOTCONV && stat != CLAIRE_ELINESEARCH) return stat;
+  CL_CUDA(c, cudaMemcpyAsync(v, W.vdev, sizeof(T) * 3 * N, cudaMemcpyDeviceToHost, st));
+  CL_CUDA(c, cudaStreamSynchronize(st));
+  return stat;
+}
+template <class T> claire_status api_departure(claire_ctx* c, const T* v, int dir, T* disp, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, v);
+  CHECK_PTR(c, disp);
+  if (dir != 1 && dir != -1) {
+    c->set_error("dir must be +1 or -1");
+    return CLAIRE_EINVAL;
+  }
+  return sl_departure<T>(c, v, dir, disp, (cudaStream_t)s);
+}
+template <class T> claire_status api_interp(claire_ctx* c, const T* f, const T* disp, T* out, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, f);
+  CHECK_PTR(c, disp);
+  CHECK_PTR(c, out);
+  return sl_interp<T>(c, f, disp, out, (cudaStream_t)s);
+}
+template <class T> claire_status api_spectral(claire_ctx* c, int op, const T* in, T* out, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, in);
+  CHECK_PTR(c, out);
+  return spectral_dev<T>(c, op, in, out, (cudaStream_t)s);
+}
+template <class T> claire_status api_objective(claire_ctx* c, const T* m1, const T* mR, const T* v, double* J,
+                                               void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, m1);
+  CHECK_PTR(c, mR);
+  CHECK_PTR(c, v);
+  CHECK_PTR(c, J);
+  return objective_dev<T>(c, m1, mR, v, J, (cudaStream_t)s);
+}
+template <class T> claire_status api_dot(claire_ctx* c, const T* a, const T* b, long long n, double* out, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, a);
+  CHECK_PTR(c, b);
+  CHECK_PTR(c, out);
+  if (n < 0) {
+    c->set_error("negative count");
+    return CLAIRE_EINVAL;
+  }
+  return inner<T>(c, a, b, n, out, (cudaStream_t)s);
+}
+template <class T> claire_status api_fft(claire_ctx* c, const T* f, T* spec, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, f);
+  CHECK_PTR(c, spec);
+  return fft_r2c<T>(c, f, reinterpret_cast<cplx<T>*>(spec), (cudaStream_t)s);
+}
+template <class T> claire_status api_ifft(claire_ctx* c, const T* spec, T* f, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, spec);
+  CHECK_PTR(c, f);
+  Work<T>& W = c->work<T>();
+  CL_CUDA(c, cudaMemcpyAsync(W.spec, spec, sizeof(cplx<T>) * c->d.Ns, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  return fft_c2r<T>(c, W.spec, f, T(1.0 / double(c->d.N)), (cudaStream_t)s);
+}
+
+}  // namespace
+
+// =================================================================================================================
+extern "C" {
+
+claire_status claire_default_opts(claire_opts* o, int n1, int n2, int n3, int precision) {
+  if (!o) return CLAIRE_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->n[0] = n1;
+  o->n[1] = n2;
+  o->n[2] = n3;
+  o->precision = precision;
+  o->beta = 1e-2;
+  o->nt = 4;
+  o->regnorm = 1;
+  o->divfree = 0;
+  o->gtol_rel = 5e-2;
+  o->gtol_abs = 1e-6;
+  o->max_gn = 50;
+  o->max_krylov = 100;
+  o->pcg_rtol = 0.0;
+  o->max_ls = 10;
+  o->armijo_c1 = 1e-4;
+  return CLAIRE_OK;
+}
+
+claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
+  if (!opts || !out) return CLAIRE_EINVAL;
+  *out = nullptr;
+  const claire_opts& o = *opts;
+  for (int a = 0; a < 3; ++a)
+    if (o.n[a] < 4 || (o.n[a] & 1)) return CLAIRE_EINVAL;
+  if (o.nt < 1 || !(o.beta > 0) || (o.regnorm != 1 && o.regnorm != 2) || (o.divfree != 0 && o.divfree != 1) ||
+      (o.precision != CLAIRE_F32 && o.precision != CLAIRE_F64) || o.max_gn < 0 || o.max_krylov < 1 || o.max_ls < 1)
+    return CLAIRE_EINVAL;
+  const long long N = (long long)o.n[0] * o.n[1] * o.n[2];
+  if ((long long)o.n[1] * o.n[2] > (1LL << 30) || N > (1LL << 31) - 1) return CLAIRE_EINVAL;
+  claire_ctx* c = new (std::nothrow) claire_ctx();
+  if (!c) return CLAIRE_ENOMEM;
+  c->o = o;
+  c->d.n1 = o.n[0];
+  c->d.n2 = o.n[1];
+  c->d.n3 = o.n[2];
+  c->d.n3h = o.n[2] / 2 + 1;
+  c->d.N = N;
+  c->d.Ns = (long long)o.n[0] * o.n[1] * c->d.n3h;
+  RadixPlan tmp;
+  if (!radix_plan(o.n[0], tmp) || !radix_plan(o.n[1], tmp) || !radix_plan(o.n[2] / 2, tmp)) {
+    delete c;
+    return CLAIRE_EINVAL;
+  }
+  const size_t bytes = o.precision == CLAIRE_F32 ? work_bytes<float>(o, c->d) : work_bytes<double>(o, c->d);
+  if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return CLAIRE_ENOMEM;
+  }
+  c->arena_bytes = bytes;
+  if (cudaMallocHost(&c->hscal, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->arena);
+    delete c;
+    return CLAIRE_ENOMEM;
+  }
+  claire_status s = o.precision == CLAIRE_F32 ? fft_init<float>(c) : fft_init<double>(c);
+  if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? alloc_work<float>(c) : alloc_work<double>(c);
+  if (s != CLAIRE_OK) {
+    cudaFreeHost(c->hscal);
+    cudaFree(c->arena);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return CLAIRE_OK;
+}
+
+claire_status claire_destroy(claire_ctx* c) {
+  if (!c) return CLAIRE_OK;
+  cudaDeviceSynchronize();
+  if (c->arena) cudaFree(c->arena);
+  if (c->hscal) cudaFreeHost(c->hscal);
+  delete c;
+  return CLAIRE_OK;
+}
+
+const char* claire_last_error(const claire_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t claire_workspace_bytes(const claire_ctx* c) { return c ? c->arena_bytes : 0; }
+
+claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
+  if (!c || !out) return CLAIRE_EINVAL;
+  out->launches = c->counters.launches;
+  return CLAIRE_OK;
+}
+
+claire_status claire_transport_f32(claire_ctx* c, const float* m0, const float* v, int dir, float* m1, void* s) {
+  return api_transport<float>(c, m0, v, dir, m1, s);
+}
+claire_status claire_transport_f64(claire_ctx* c, const double* m0, const double* v, int dir, double* m1, void* s) {
+  return api_transport<double>(c, m0, v, dir, m1, s);
+}
+claire_status claire_gradient_f32(claire_ctx* c, const float* mT, const float* mR, const float* v, float* g, double* J,
+                                  void* s) {
+  return api_gradient<float>(c, mT, mR, v, g, J, s);
+}
+claire_status claire_gradient_f64(claire_ctx* c, const double* mT, const double* mR, const double* v, double* g,
+                                  double* J, void* s) {
+  return api_gradient<double>(c, mT, mR, v, g, J, s);
+}
+claire_status claire_hessvec_f32(claire_ctx* c, const float* mT, const float* mR, const float* v, const float* vt,
+                                 float* Hvt, void* s) {
+  (void)mR;
+  return api_hessvec<float>(c, mT, v, vt, Hvt, s);
+}
+claire_status claire_hessvec_f64(claire_ctx* c, const double* mT, const double* mR, const double* v, const double* vt,
+                                 double* Hvt, void* s) {
+  (void)mR;
+  return api_hessvec<double>(c, mT, v, vt, Hvt, s);
+}
+claire_status claire_hessvec_cached_f32(claire_ctx* c, const float* vt, float* Hvt, void* s) {
+  return api_hessvec_cached<float>(c, vt, Hvt, s);
+}
+claire_status claire_hessvec_cached_f64(claire_ctx* c, const double* vt, double* Hvt, void* s) {
+  return api_hessvec_cached<double>(c, vt, Hvt, s);
+}
+claire_status claire_linearize_f32(claire_ctx* c, const float* mT, const float* v, void* s) {
+  return api_linearize<float>(c, mT, v, s);
+}
+claire_status claire_linearize_f64(claire_ctx* c, const double* mT, const double* v, void* s) {
+  return api_linearize<double>(c, mT, v, s);
+}
+claire_status claire_precond_f32(claire_ctx* c, const float* r, float* z, void* s) {
+  return api_precond<float>(c, r, z, s);
+}
+claire_status claire_precond_f64(claire_ctx* c, const double* r, double* z, void* s) {
+  return api_precond<double>(c, r, z, s);
+}
+claire_status claire_register_f32(claire_ctx* c, const float* mT, const float* mR, float* v, claire_report* rep,
+                                  void* s) {
+  return api_register<float>(c, mT, mR, v, rep, s);
+}
+claire_status claire_register_f64(claire_ctx* c, const double* mT, const double* mR, double* v, claire_report* rep,
+                                  void* s) {
+  return api_register<double>(c, mT, mR, v, rep, s);
+}
+claire_status claire_register_host_f32(claire_ctx* c, const float* mT, const float* mR, float* v, claire_report* rep,
+                                       void* s) {
+  return api_register_host<float>(c, mT, mR, v, rep, s);
+}
+claire_status claire_register_host_f64(claire_ctx* c, const double* mT, const double* mR, double* v,
+                                       claire_report* rep, void* s) {
+  return api_register_host<double>(c, mT, mR, v, rep, s);
+}
+claire_status claire_departure_f32(claire_ctx* c, const float* v, int dir, float* disp, void* s) {
+  return api_departure<float>(c, v, dir, disp, s);
+}
+claire_status claire_departure_f64(claire_ctx* c, const double* v, int dir, double* disp, void* s) {
+  return api_departure<double>(c, v, dir, disp, s);
+}
+claire_status claire_interp_f32(claire_ctx* c, const float* f, const float* disp, float* out, void* s) {
+  return api_interp<float>(c, f, disp, out, s);
+}
+claire_status claire_interp_f64(claire_ctx* c, const double* f, const double* disp, double* out, void* s) {
+  return api_interp<double>(c, f, disp, out, s);
+}
+claire_status claire_spectral_f32(claire_ctx* c, int op, const float* in, float* out, void* s) {
+  return api_spectral<float>(c, op, in, out, s);
+}
+claire_status claire_spectral_f64(claire_ctx* c, int op, const double* in, double* out, void* s) {
+  return api_spectral<double>(c, op, in, out, s);
+}
+claire_status claire_objective_f32(claire_ctx* c, const float* m1, const float* mR, const float* v, double* J,
+                                   void* s) {
+  return api_objective<float>(c, m1, mR, v, J, s);
+}
+claire_status claire_objective_f64(claire_ctx* c, const double* m1, const double* mR, const double* v, double* J,
+                                   void* s) {
+  return api_objective<double>(c, m1, mR, v, J, s);
+}
+claire_status claire_dot_f32(claire_ctx* c, const float* a, const float* b, long long n, double* out, void* s) {
+  return api_dot<float>(c, a, b, n, out, s);
+}
+claire_status claire_dot_f64(claire_ctx* c, const double* a, const double* b, long long n, double* out, void* s) {
+  return api_dot<double>(c, a, b, n, out, s);
+}
+claire_status claire_fft_f32(claire_ctx* c, const float* f, float* spec, void* s) { return api_fft<float>(c, f, spec, s); }
+claire_status claire_fft_f64(claire_ctx* c, const double* f, double* spec, void* s) {
+  return api_fft<double>(c, f, spec, s);
+}
+claire_status claire_ifft_f32(claire_ctx* c, const float* spec, float* f, void* s) {
+  return api_ifft<float>(c, spec, f, s);
+}
+claire_status claire_ifft_f64(claire_ctx* c, const double* spec, double* f, void* s) {
+  return api_ifft<double>(c, spec, f, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the header declares, and its host-side
+argument validation rejects bad input before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "claire.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1808_04487_gb300 import build as b
+    b.build()
+    import paper_1808_04487_gb300 as pkg
+    return pkg.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(claire_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_five_paper_calls():
+    names = declared_functions()
+    for base in ("claire_transport", "claire_gradient", "claire_hessvec", "claire_precond", "claire_register"):
+        assert base + "_f32" in names and base + "_f64" in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_default_opts_are_the_papers(L):
+    import paper_1808_04487_gb300 as pkg
+    o = pkg.Opts()
+    assert L.claire_default_opts(ctypes.byref(o), 32, 32, 32, 0) == 0
+    assert (o.nt, o.regnorm, o.divfree, o.max_gn, o.max_krylov, o.max_ls) == (4, 1, 0, 50, 100, 10)
+    assert (o.gtol_rel, o.gtol_abs, o.armijo_c1) == (5e-2, 1e-6, 1e-4)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=(31, 32, 32)), dict(n=(2, 32, 32)), dict(n=(22, 32, 32)), dict(nt=0), dict(beta=0.0), dict(beta=-1.0),
+    dict(regnorm=3), dict(divfree=2), dict(precision=5), dict(max_krylov=0), dict(max_ls=0)])
+def test_create_rejects_bad_options_before_any_device_call(L, bad):
+    import paper_1808_04487_gb300 as pkg
+    o = pkg.Opts()
+    L.claire_default_opts(ctypes.byref(o), 32, 32, 32, 0)
+    for k, val in bad.items():
+        if k == "n":
+            for a in range(3):
+                o.n[a] = val[a]
+        else:
+            setattr(o, k, val)
+    h = ctypes.c_void_p()
+    assert L.claire_create(ctypes.byref(o), ctypes.byref(h)) == 1  # CLAIRE_EINVAL
+    assert not h.value
+
+
+def test_null_context_is_rejected(L):
+    assert L.claire_transport_f32(None, None, None, 1, None, None) == 1
+    assert L.claire_register_f64(None, None, None, None, None, None) == 1
+    assert L.claire_destroy(None) == 0
+    assert L.claire_last_error(None) == b"null context"
+
+
+def test_radix_support_matches_the_batched_grids():
+    # every grid of the population-to-atlas set factors into the supported radices 2, 3, 5, 7
+    for n in (64, 96, 112, 128, 144, 160, 192, 256):
+        m = n
+        for r in (2, 3, 5, 7):
+            while m % r == 0:
+                m //= r
+        assert m == 1 and (n // 2) * 2 == n

@@ -1,0 +1,302 @@
+"""GPU (sm_103a kernels through the C-ABI) against the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances: relative L2 <= 1e-5 for FP32 and <= 1e-12 for FP64 per operator; final velocity of a full solve
+relative L2 <= 1e-3 and Gauss-Newton iteration count within +-1. Bit-exact where the method is exact (identity
+transport at v = 0).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import claire_inputs as I
+from oracle import claire_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "f64": 1e-12}
+GRIDS = [(16, 16, 16), (12, 16, 20), (40, 36, 42), (4, 4, 4), (24, 20, 14)]
+
+
+def rel(a, b):
+    a = a.detach().cpu().double().numpy() if hasattr(a, "detach") else np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def dev(x, prec):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", torch.float32 if prec == "f32" else torch.float64)
+
+
+def ctx(n, prec, **kw):
+    import paper_1808_04487_gb300 as pkg
+    return pkg.Context(n, precision=prec, **kw)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1808_04487_gb300 import build as b
+    b.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+# ------------------------------------------------------------------------------------------------------ FFT (a3)
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n", GRIDS)
+def test_fft_forward_and_inverse(n, prec):
+    f = np.random.default_rng(1).normal(size=n)
+    with ctx(n, prec) as c:
+        spec = c.fft(dev(f, prec))
+        ref = np.fft.rfftn(f)
+        got = spec[..., 0].cpu().double().numpy() + 1j * spec[..., 1].cpu().double().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < TOL[prec]
+        back = c.ifft(spec)
+        assert rel(back, f) < TOL[prec]
+        # the inverse of an arbitrary (Hermitian-consistent) spectrum
+        g = np.random.default_rng(2).normal(size=n)
+        G = np.fft.rfftn(g)
+        st = torch.from_numpy(np.stack([G.real, G.imag], -1).copy()).to(spec)
+        assert rel(c.ifft(st), g) < TOL[prec]
+
+
+# ------------------------------------------------------------------------------------------------------ spectral ops
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(16, 16, 16), (12, 16, 20), (40, 36, 42)])
+def test_spectral_operators(n, prec):
+    g = O.Grid(n)
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=n)
+    v = rng.normal(size=(3,) + n)
+    for regnorm in (1, 2):
+        with ctx(n, prec, regnorm=regnorm) as c:
+            assert rel(c.spectral("grad", dev(f, prec)), O.gradient_spectral(g, f)) < TOL[prec]
+            assert rel(c.spectral("div", dev(v, prec)), O.divergence_spectral(g, v)) < TOL[prec]
+            assert rel(c.spectral("leray", dev(v, prec)), O.leray(g, v)) < TOL[prec]
+            assert rel(c.spectral("A", dev(v, prec)), O.apply_A(g, v, regnorm)) < TOL[prec]
+            assert rel(c.spectral("lap", dev(f, prec)), O.laplacian_spectral(g, f)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("regnorm", [1, 2])
+def test_preconditioner(prec, regnorm):
+    n = (24, 20, 14)
+    g = O.Grid(n)
+    r = np.random.default_rng(4).normal(size=(3,) + n)
+    with ctx(n, prec, beta=3e-3, regnorm=regnorm) as c:
+        assert rel(c.precond(dev(r, prec)), O.precond(g, r, 3e-3, regnorm)) < TOL[prec]
+
+
+# ------------------------------------------------------------------------------------------------------ SL kernels
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n", GRIDS)
+def test_interpolation_with_wrapping_displacements(n, prec):
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=n)
+    d = rng.uniform(-6.0, 6.0, size=(3,) + n)  # crosses the periodic wrap, negative and positive
+    with ctx(n, prec) as c:
+        assert rel(c.interp(dev(f, prec), dev(d, prec)), O.interp(f, d)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(16, 16, 16), (12, 16, 20), (40, 36, 42)])
+def test_departure_points(n, prec):
+    g = O.Grid(n)
+    v = I.random_velocity(n, seed=6, kmax=3, amplitude=2.0)  # several voxels per step
+    with ctx(n, prec, nt=4) as c:
+        for sign in (+1, -1):
+            assert rel(c.departure(dev(v, prec), sign), O.departure(g, v, 4, sign)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("divfree", [False, True])
+@pytest.mark.parametrize("n", [(16, 16, 16), (12, 16, 20), (40, 36, 42)])
+def test_transport_state_and_adjoint(n, prec, divfree):
+    p = O.Problem(n, beta=1e-2, nt=4, divfree=divfree)
+    m0 = I.trig_image(n, 7)
+    v = I.random_velocity(n, seed=8, kmax=3, amplitude=0.5, divfree=divfree)
+    with ctx(n, prec, nt=4, divfree=divfree) as c:
+        for direction in (+1, -1):
+            got = c.transport(dev(m0, prec), dev(v, prec), direction)
+            assert rel(got, O.transport(p, m0, v, direction)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_identity_transport_is_bit_exact(prec):
+    n = (12, 16, 20)
+    m0 = I.trig_image(n, 9)
+    with ctx(n, prec) as c:
+        x = dev(m0, prec)
+        z = torch.zeros((3,) + n, dtype=x.dtype, device="cuda")
+        assert torch.equal(c.transport(x, z, +1), x)
+        assert torch.equal(c.transport(x, z, -1), x)
+
+
+# ------------------------------------------------------------------------------------------------------ gradient / Hessian
+CASES = [dict(regnorm=1, divfree=False, nt=4), dict(regnorm=2, divfree=True, nt=4), dict(regnorm=1, divfree=False,
+                                                                                          nt=2)]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("n", [(16, 16, 16), (12, 16, 20), (40, 36, 42)])
+def test_objective_gradient_hessvec(n, prec, case):
+    p = O.Problem(n, beta=1e-2, **case)
+    mT = I.trig_image(n, 10)
+    mR = I.trig_image(n, 11)
+    v = I.random_velocity(n, seed=12, kmax=3, amplitude=0.4, divfree=case["divfree"])
+    vt = I.random_velocity(n, seed=13, kmax=4, amplitude=1.0, divfree=case["divfree"])
+    lin = O.linearize(p, mT, v)
+    g_ref = O.reduced_gradient(p, lin, mR)
+    h_ref = O.hessvec(p, lin, vt)
+    J_ref = O.objective(p, mR, lin.m[-1], v)
+    with ctx(n, prec, beta=1e-2, **case) as c:
+        g, J = c.gradient(dev(mT, prec), dev(mR, prec), dev(v, prec), objective=True)
+        assert rel(g, g_ref) < TOL[prec]
+        assert abs(J - J_ref) <= TOL[prec] * abs(J_ref)
+        h = c.hessvec_cached(dev(vt, prec))
+        assert rel(h, h_ref) < TOL[prec]
+        h2 = c.hessvec(dev(mT, prec), dev(v, prec), dev(vt, prec))
+        assert rel(h2, h_ref) < TOL[prec]
+        assert abs(c.objective(dev(lin.m[-1], prec), dev(mR, prec), dev(v, prec)) - J_ref) <= TOL[prec] * J_ref
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_inner_product_fp64_accumulation(prec):
+    n = (40, 36, 42)
+    rng = np.random.default_rng(14)
+    a = rng.normal(size=(3,) + n)
+    b = rng.normal(size=(3,) + n)
+    g = O.Grid(n)
+    with ctx(n, prec) as c:
+        A, B = dev(a, prec), dev(b, prec)
+        ref = O.inner(g, A.cpu().double().numpy(), B.cpu().double().numpy())  # same rounded inputs
+        assert abs(c.dot(A, B) - ref) <= 1e-12 * O.norm(g, a) * O.norm(g, b)
+
+
+# ------------------------------------------------------------------------------------------------------ full solve
+def cfg0(n=(32, 32, 32)):
+    """32^3 plain method: trig image, v* |k| <= 3 amplitude 0.3, H1, beta 1e-2, nt 4, 2 GN iterations, PCG 0.1."""
+    kw = dict(beta=1e-2, nt=4, regnorm=1, divfree=False, max_gn=2, pcg_rtol=0.1)
+    p = O.Problem(n, **kw)
+    mT = I.trig_image(n, 0)
+    vstar = I.random_velocity(n, seed=0, kmax=3, amplitude=0.3)
+    mR = O.transport(p, mT, vstar, +1)
+    return p, kw, mT, mR
+
+
+@pytest.fixture(scope="module")
+def cfg0_oracle():
+    p, kw, mT, mR = cfg0()
+    v, rep = O.register(p, mT, mR)
+    return p, kw, mT, mR, v, rep
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_register_matches_oracle(cfg0_oracle, prec):
+    p, kw, mT, mR, v_ref, rep_ref = cfg0_oracle
+    with ctx(p.n, prec, **kw) as c:
+        v, rep, status = c.register(dev(mT, prec), dev(mR, prec))
+    assert rel(v, v_ref) <= (1e-10 if prec == "f64" else 1e-3)
+    assert abs(rep["gn_iters"] - rep_ref.gn_iters) <= 1
+    assert abs(rep["gnorm0"] - rep_ref.gnorm0) <= 1e-5 * rep_ref.gnorm0
+    if prec == "f64":
+        assert rep["matvecs"] == rep_ref.matvecs and rep["pde_solves"] == rep_ref.pde_solves
+    assert rep["pde_solves"] == 2 * rep["matvecs"] + rep["gn_iters"] + rep["ls_trials"] + 2
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_register_host_arrays_match_device_arrays(prec):
+    p, kw, mT, mR = cfg0(n=(16, 16, 16))
+    with ctx(p.n, prec, **kw) as c:
+        vd, _, _ = c.register(dev(mT, prec), dev(mR, prec))
+        dt = torch.float32 if prec == "f32" else torch.float64
+        vh = torch.zeros((3,) + p.n, dtype=dt).pin_memory()
+        vh, rep, _ = c.register_host(torch.from_numpy(mT).to(dt).pin_memory(),
+                                     torch.from_numpy(mR).to(dt).pin_memory(), vh)
+    assert torch.equal(vh, vd.cpu())
+
+
+def test_degenerate_identical_images_converge_immediately():
+    n = (16, 16, 16)
+    mT = I.trig_image(n, 0)
+    with ctx(n, "f64", beta=1e-2) as c:
+        v, rep, status = c.register(dev(mT, "f64"), dev(mT, "f64"))
+    assert status == "OK" and rep["gn_iters"] == 0 and rep["gnorm0"] == 0.0
+    assert float(v.abs().max()) == 0.0
+
+
+def test_divfree_register_keeps_v_divergence_free():
+    n = (24, 24, 24)
+    kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, max_gn=3, gtol_rel=1e-2)
+    p = O.Problem(n, **kw)
+    mT = I.brain_phantom(n, 0)
+    vs = I.random_velocity(n, seed=1, kmax=3, max_disp_voxels=2.0, divfree=True)
+    mR = O.transport(p, mT, vs, +1)
+    v_ref, rep_ref = O.register(p, mT, mR)
+    with ctx(n, "f64", **kw) as c:
+        v, rep, status = c.register(dev(mT, "f64"), dev(mR, "f64"))
+        div = c.spectral("div", v)
+    assert rel(v, v_ref) < 1e-10
+    assert rep["gn_iters"] == rep_ref.gn_iters
+    assert float(div.abs().max()) < 1e-10 * float(v.abs().max())
+
+
+# ------------------------------------------------------------------------------------------------------ full size
+BIG = (256, 256, 256)
+
+
+@pytest.fixture(scope="module")
+def big_inputs():
+    mT = I.brain_phantom(BIG, 0)
+    mR = I.brain_phantom(BIG, 1)
+    return mT, mR
+
+
+def test_fullsize_identity_and_constant_velocity_transport(big_inputs):
+    mT, _ = big_inputs
+    c_phys = np.array([0.011, -0.017, 0.023])  # sub-voxel shifts on the 256^3 grid
+    with ctx(BIG, "f32", nt=4) as c:
+        x = dev(mT, "f32")
+        z = torch.zeros((3,) + BIG, dtype=torch.float32, device="cuda")
+        assert torch.equal(c.transport(x, z, +1), x)
+        v = (torch.ones((3,) + BIG, dtype=torch.float64) * torch.tensor(c_phys)[:, None, None, None]).float().cuda()
+        got = c.transport(x, v, +1).cpu().double().numpy()
+    # closed form: nt applications of the fixed 4-tap periodic shift per axis, as a Fourier multiplier
+    h = 2 * math.pi / 256
+    F = np.fft.rfftn(x.cpu().double().numpy())
+    for a in range(3):
+        s = -np.float32(c_phys[a]).astype(np.float64) * 0.25 / h
+        b = math.floor(s)
+        t = s - b
+        w = O.lagrange_weights(np.array(t))
+        k = np.fft.fftfreq(256, 1 / 256) if a < 2 else np.arange(129)
+        S = sum(float(w[p]) * np.exp(2j * math.pi * k * (b + p - 1) / 256) for p in range(4)) ** 4
+        shp = [1, 1, 1]
+        shp[a] = len(k)
+        F = F * S.reshape(shp)
+    ref = np.fft.irfftn(F, s=BIG, axes=(0, 1, 2))
+    assert rel(got, ref) < 1e-5
+
+
+def test_fullsize_gradient_and_hessvec_closed_forms_at_zero(big_inputs):
+    """At v = 0: g = K[(mR - mT) grad mT] and H v~ = beta A v~ + K[(v~ . grad mT) grad mT] (H2, div v = 0)."""
+    mT, mR = big_inputs
+    g = O.Grid(BIG)
+    beta = 1e-3
+    with ctx(BIG, "f32", beta=beta, nt=4, regnorm=2, divfree=True) as c:
+        x, y = dev(mT, "f32"), dev(mR, "f32")
+        zero = torch.zeros((3,) + BIG, dtype=torch.float32, device="cuda")
+        gg = c.gradient(x, y, zero).cpu().double().numpy()
+        vt = I.random_velocity(BIG, seed=3, kmax=6, amplitude=1.0, divfree=True)
+        hv = c.hessvec_cached(dev(vt, "f32")).cpu().double().numpy()
+    mT32 = x.cpu().double().numpy()
+    mR32 = y.cpu().double().numpy()
+    gm = O.gradient_spectral(g, mT32)
+    ref_g = O.leray(g, (mR32 - mT32) * gm)
+    assert rel(gg, ref_g) < 1e-5
+    vt32 = torch.from_numpy(vt).float().double().numpy()
+    ref_h = beta * O.apply_A(g, vt32, 2) + O.leray(g, (vt32 * gm).sum(0) * gm)
+    assert rel(hv, ref_h) < 1e-5
