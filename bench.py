@@ -1,0 +1,393 @@
+"""Benchmark: time-to-solution of a 256^3 registration to relative gradient 1e-2 on the GB300 path.
+
+One step = one full inexact Gauss-Newton-Krylov solve (Alg. 1, Alg. 2) from v = 0 on the synthetic brain-like
+phantom: nested smoothed ellipsoids (0.2 / 0.5 / 0.9) + N(0, 0.01^2) noise, Gaussian sigma = 1 voxel, registered to
+itself warped by a band-limited divergence-free v* (|k| <= 6, max displacement 8 voxels); H2 regularisation,
+beta = 1e-3, div v = 0 (Leray), n_t = 4, stop at ||g|| <= 1e-2 ||g(0)||, FP32 fields with FP64 reductions.
+The warped image m_R is made by this library's own transport of m_T along v*.
+
+Prints one JSON line (see the keys below). ``--impl reference`` times the FP64 CPU oracle instead (a bounded
+sample of the same workload, extrapolated by voxel count). Under torchrun each rank runs its own replica
+(no data-path collective); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "256^3 registration sec to rel-grad 1e-2; Hessian matvec/s; HBM GB/s vs peak"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    return {"workload": "brain phantom %dx%dx%d registered to its warp by a div-free band-limited v* "
+                        "(|k|<=6, 8 voxels at 256^3), H2 beta=1e-3, div v=0, nt=4, to ||g||/||g0|| <= 1e-2"
+                        % tuple(n),
+            "n": list(n), "beta": 1e-3, "regnorm": "H2", "divfree": True, "nt": 4, "gtol_rel": 1e-2,
+            "precision": "fp32 fields, fp64 reductions",
+            "l2": "working set ~4 GB > 129 MB L2 (no flush needed)"}
+
+
+SOLVER_KW = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, gtol_rel=1e-2, max_gn=50, max_krylov=100)
+
+
+def make_inputs(n):
+    import claire_inputs as I
+    mT = I.brain_phantom(n, seed=0)
+    vstar = I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=8.0 * max(n) / 256.0, divfree=True)
+    return mT, vstar
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# Algorithmic (compulsory) bytes per grid node for each kernel, FP32 words x 4 bytes. Gathered fields count once
+# (each value is needed once; neighbours come from L1/L2). n3h-based FFT passes use the half-spectrum size.
+def algorithmic_bytes(name, n, word=4):
+    N = n[0] * n[1] * n[2]
+    Ns = n[0] * n[1] * (n[2] // 2 + 1)
+    per_node = {
+        "sl_interp": 5,                  # disp 3 + gathered field 1 + write 1
+        "sl_departure": 6,               # v 3 + write 3
+        "sl_inc_step": 11,               # disp 3 + vt 3 + grad m 3 + gathered q 1 + write 1
+        "sl_inc_step_last": 13,          # disp 3 + vt 3 + grad m 3 + q 1 + lambda 1 + b 3 (no write-back of q)
+        "sl_adj_step_store_acc": 14,     # disp 3 + lambda 1 + grad m 3 + b r/w 6 + write 1
+        "sl_adj_step_acc": 13,
+        "sl_adj_step_store": 5,
+        "sl_inc_init": 7,
+        "sl_adj_terminal": 10,
+    }
+    if name in per_node:
+        return per_node[name] * N * word
+    if name == "fft_z_r2c" or name == "fft_z_c2r":
+        return N * word + Ns * 2 * word
+    if name.startswith("fft_"):
+        return 2 * Ns * 2 * word
+    if name in ("spec_leray",):
+        return 6 * Ns * 2 * word
+    if name in ("spec_scale",):
+        return 6 * Ns * 2 * word
+    return None
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1808_04487_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel, n):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel sources."""
+    p = os.path.join(PROFILES, "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    digest = None
+    rows = {}
+    for line in open(p):
+        line = line.strip()
+        if line.startswith("# source_digest:"):
+            digest = line.split(":", 1)[1].strip()
+        elif line and not line.startswith("#"):
+            parts = line.split()
+            if len(parts) >= 3:
+                rows[(parts[0], int(parts[1]))] = float(parts[2])
+    if digest != source_digest():
+        return None
+    b = rows.get((kernel, n[0]))
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n_target, seconds_budget=30.0):
+    """Oracle (FP64 numpy, as it stands) on a bounded sample: the same problem family at 32^3, extrapolated to the
+    target grid by voxel count (the solver's work per iteration is linear in N up to the FFT's log factor, and
+    PCG/GN counts are nearly mesh independent, Sec. 4.3)."""
+    import numpy as np
+
+    import claire_inputs as I
+    from oracle import claire_oracle as O
+
+    ns = (32, 32, 32)
+    p = O.Problem(ns, beta=1e-3, nt=4, regnorm=2, divfree=True, gtol_rel=1e-2)
+    mT = I.brain_phantom(ns, seed=0)
+    vs = I.random_velocity(ns, seed=1, kmax=6, max_disp_voxels=8.0 * 32 / 256.0, divfree=True)
+    mR = O.transport(p, mT, vs, +1)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        v, rep = O.register(p, mT, mR)
+        reps += 1
+        if time.perf_counter() - t0 > seconds_budget / 3 or reps >= 3:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    scale = float(np.prod(n_target)) / float(np.prod(ns))
+    return {"value": dt * scale, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "oracle register at 32^3 of the same phantom family (same physical v*, H2 beta=1e-3, "
+                      "div-free, nt=4, rel-grad 1e-2): %.2f s/solve x %d runs, %d GN / %d matvecs, scaled by "
+                      "voxel count x%d to %s" % (dt, reps, rep.gn_iters, rep.matvecs, int(scale), list(n_target))}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n = (args.size,) * 3
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    samples = []
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(n, seconds_budget=20.0)
+        samples.append(cb["value"])
+    val = sorted(samples)[len(samples) // 2]
+    cb["value"] = val
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(n),
+            "cpu_baseline": cb, "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_1808_04487_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = (args.size,) * 3
+    mT_np, vstar_np = make_inputs(n)
+    dev = torch.device("cuda", local)
+    mT = torch.from_numpy(mT_np).float().to(dev)
+    vstar = torch.from_numpy(vstar_np).float().to(dev)
+    ctx = pkg.Context(n, precision="f32", **SOLVER_KW)
+    mR = ctx.transport(mT, vstar, +1)
+    del vstar
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        v = torch.zeros((3,) + n, dtype=torch.float32, device=dev)
+        v, rep, status = ctx.register(mT, mR, v)
+        return v, rep, status
+
+    for _ in range(max(3, args.warmup)):
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ctx.launches()
+    ctx.profile(True)
+    ctx.profile_report()  # clear
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = []
+    for _ in range(args.steps):
+        v, rep, status = solve()
+        reps.append((rep, status))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_report()
+    ctx.profile(False)
+    launches = ctx.launches() - launches0
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ms_per_step / 1e3 / world  # seconds per registration, whole job (N replicas in parallel)
+
+    # ---- Hessian matvecs/s at the converged linearisation (full matvec incl. beta A through its symbol)
+    ctx.linearize(mT, v)
+    vt = torch.randn((3,) + n, dtype=torch.float32, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    vt = ctx.spectral("leray", vt)
+    Hv = torch.empty_like(vt)
+    for _ in range(3):
+        ctx.hessvec_cached(vt, Hv)
+    times = []
+    for _ in range(20):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.hessvec_cached(vt, Hv)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    matvec_ms = times[len(times) // 2]
+
+    # ---- roofline of the dominant kernel (live CUDA-event durations over the timed region)
+    peak, peak_kind = read_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    total_kernel_ms = sum(x[1] for x in prof.values()) if prof else 0.0
+    roof = None
+    if top is not None:
+        name, (cnt, tot) = top
+        avg_ms = tot / cnt
+        byt = algorithmic_bytes(name, n)
+        achieved = byt / (avg_ms * 1e-3) / 1e9 if byt else None
+        tr = traffic_from_profiles(name, n)
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": tr,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                else "fallback 6800 GB/s",
+                "algorithmic_bytes_per_launch": byt, "avg_launch_ms": avg_ms, "launches": cnt,
+                "share_of_kernel_time": tot / total_kernel_ms if total_kernel_ms else None}
+    kernels = {k: {"launches": c, "ms": round(t, 3), "share": round(t / total_kernel_ms, 4) if total_kernel_ms else None}
+               for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}
+
+    # ---- end to end through the C-ABI with host buffers (H2D inputs + D2H solution inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        mT_h = mT.cpu().pin_memory()
+        mR_h = mR.cpu().pin_memory()
+        v_h = torch.zeros((3,) + n, dtype=torch.float32).pin_memory()
+        ctx.register_host(mT_h, mR_h, v_h.zero_())
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        k2 = max(1, min(args.steps, 2))
+        for _ in range(k2):
+            ctx.register_host(mT_h, mR_h, v_h.zero_())
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / k2
+        if dist is not None:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        N = n[0] * n[1] * n[2]
+        e2e = {"value": ems / 1e3 / world, "unit": "s", "h2d_bytes_per_step": 5 * N * 4 * world,
+               "d2h_bytes_per_step": 3 * N * 4 * world}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    rep, status = reps[-1]
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(n)
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload(n),
+        "solve": {"status": status, "gn_iters": rep["gn_iters"], "matvecs": rep["matvecs"],
+                  "pde_solves": rep["pde_solves"], "ls_trials": rep["ls_trials"], "gnorm_rel": rep["gnorm_rel"],
+                  "mismatch_rel": rep["mismatch_rel"]},
+        "hessian_matvecs_per_s": 1e3 / matvec_ms, "hessian_matvec_ms": matvec_ms,
+        "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "cpu_baseline": cb,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -137,6 +137,12 @@ claire_status claire_hessvec_f64(claire_ctx* ctx, const double* mT, const double
  * call on ctx (CLAIRE_EINVAL if there is none). This is the operator PCG applies (Alg. 2 lines 6-8). */
 claire_status claire_hessvec_cached_f32(claire_ctx* ctx, const float* vt, float* Hvt, void* stream);
 claire_status claire_hessvec_cached_f64(claire_ctx* ctx, const double* vt, double* Hvt, void* stream);
+/* Data term of the matvec alone, out = K[int_0^1 lambda~ grad m dt] (H_data of Eq. (7)), at the cached
+ * linearisation. With H_reg = beta A known in closed form this is what a caller composing its own Krylov solver or
+ * a split-preconditioned system (Sec. 2.3.3) needs; claire_register's PCG uses it with beta A s carried by
+ * recurrence. vt and out must not alias. */
+claire_status claire_hessvec_data_f32(claire_ctx* ctx, const float* vt, float* out, void* stream);
+claire_status claire_hessvec_data_f64(claire_ctx* ctx, const double* vt, double* out, void* stream);
 /* Cache the linearisation at (mT, v) without computing anything else. */
 claire_status claire_linearize_f32(claire_ctx* ctx, const float* mT, const float* v, void* stream);
 claire_status claire_linearize_f64(claire_ctx* ctx, const double* mT, const double* v, void* stream);
@@ -201,6 +207,13 @@ typedef struct {
     long long launches;
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
+
+/* Per-kernel timing (not part of the method; for measurement). While enabled, every kernel launch on ctx is
+ * bracketed by a pair of CUDA events on its stream. claire_profile_report synchronises the device, writes a JSON
+ * object {"kernel name": [launches, total_ms], ...} of everything recorded since the last report into buf
+ * (truncated to len bytes, NUL-terminated), and clears the records. Enabling adds two event records per launch. */
+claire_status claire_profile_enable(claire_ctx* ctx, int on);
+claire_status claire_profile_report(claire_ctx* ctx, char* buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -66,6 +66,7 @@ _TYPED = {
     "claire_gradient": [_VP, _VP, _VP, _VP, _PD, _VP],
     "claire_hessvec": [_VP, _VP, _VP, _VP, _VP, _VP],
     "claire_hessvec_cached": [_VP, _VP, _VP],
+    "claire_hessvec_data": [_VP, _VP, _VP],
     "claire_linearize": [_VP, _VP, _VP],
     "claire_precond": [_VP, _VP, _VP],
     "claire_register": [_VP, _VP, _VP, ctypes.POINTER(Report), _VP],
@@ -103,6 +104,10 @@ def lib():
     L.claire_workspace_bytes.restype = ctypes.c_size_t
     L.claire_get_counters.argtypes = [_VP, ctypes.POINTER(Counters)]
     L.claire_get_counters.restype = _I
+    L.claire_profile_enable.argtypes = [_VP, _I]
+    L.claire_profile_enable.restype = _I
+    L.claire_profile_report.argtypes = [_VP, ctypes.c_char_p, ctypes.c_size_t]
+    L.claire_profile_report.restype = _I
     for base, args in _TYPED.items():
         for sfx in ("_f32", "_f64"):
             f = getattr(L, base + sfx)
@@ -223,6 +228,11 @@ class Context:
         self._call("claire_hessvec_cached", self._v(vt, "vt"), self._v(out, "Hvt"), self._stream())
         return out
 
+    def hessvec_data(self, vt, out=None):
+        out = self.empty_vector() if out is None else out
+        self._call("claire_hessvec_data", self._v(vt, "vt"), self._v(out, "out"), self._stream())
+        return out
+
     def precond(self, r, out=None):
         out = self.empty_vector() if out is None else out
         self._call("claire_precond", self._v(r, "r"), self._v(out, "z"), self._stream())
@@ -298,6 +308,16 @@ class Context:
 
     def workspace_bytes(self):
         return int(lib().claire_workspace_bytes(self._h))
+
+    def profile(self, on=True):
+        lib().claire_profile_enable(self._h, 1 if on else 0)
+
+    def profile_report(self):
+        """{kernel name: (launches, total ms)} recorded since the last report."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        lib().claire_profile_report(self._h, buf, len(buf))
+        return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}
 
     def launches(self):
         c = Counters()

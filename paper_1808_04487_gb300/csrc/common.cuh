@@ -71,6 +71,7 @@ struct Counters {
 
 #define CL_LAUNCHED(ctxp)                                                                                \
   do {                                                                                                   \
+    (ctxp)->prof_end(st);                                                                                \
     (ctxp)->counters.launches++;                                                                         \
     cudaError_t e_ = cudaGetLastError();                                                                 \
     if (e_ != cudaSuccess) {                                                                             \

@@ -305,17 +305,20 @@ template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* ou
   const long long nlines = (long long)d.n1 * d.n2;
   {
     const unsigned grid = (unsigned)((nlines + p.lpc3 - 1) / p.lpc3);
+    c->prof_begin("fft_z_r2c", st);
     k_fft_z_r2c<T><<<grid, 256, smem_z<T>(d.n3, p.lpc3), st>>>(in, out, nlines, d.n3, p.ax3, p.tw3, p.lpc3);
     CL_LAUNCHED(c);
   }
   {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
+    c->prof_begin("fft_y_fwd", st);
     k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(out, d.n3h, p.ax2, p.tw2, p.ti12);
     CL_LAUNCHED(c);
   }
   {
     const long long inner = (long long)d.n2 * d.n3h;
     dim3 grid((unsigned)((inner + p.ti12 - 1) / p.ti12), 1u);
+    c->prof_begin("fft_x_fwd", st);
     k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(out, inner, p.ax1, p.tw1, p.ti12);
     CL_LAUNCHED(c);
   }
@@ -328,17 +331,20 @@ template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T
   {
     const long long inner = (long long)d.n2 * d.n3h;
     dim3 grid((unsigned)((inner + p.ti12 - 1) / p.ti12), 1u);
+    c->prof_begin("fft_x_inv", st);
     k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(spec, inner, p.ax1, p.tw1, p.ti12);
     CL_LAUNCHED(c);
   }
   {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
+    c->prof_begin("fft_y_inv", st);
     k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(spec, d.n3h, p.ax2, p.tw2, p.ti12);
     CL_LAUNCHED(c);
   }
   {
     const long long nlines = (long long)d.n1 * d.n2;
     const unsigned grid = (unsigned)((nlines + p.lpc3 - 1) / p.lpc3);
+    c->prof_begin("fft_z_c2r", st);
     k_fft_z_c2r<T><<<grid, 256, smem_z<T>(d.n3, p.lpc3), st>>>(spec, out, nlines, d.n3, p.ax3, p.tw3, p.lpc3,
                                                                 scale);
     CL_LAUNCHED(c);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -40,7 +41,11 @@ template <class T> struct Work {
   T* vdev = nullptr;    // device copy of v for the host-array API
   T* mTdev = nullptr;   // [N]
   T* mRdev = nullptr;   // [N]
-  T* m1trial = nullptr; // [N] final state of a line-search trial
+  T* m1trial = nullptr; // [N] scratch
+  T* u = nullptr;       // [3][N] beta A v, carried by recurrence through the Gauss-Newton loop
+  T* utrial = nullptr;  // [3][N] beta A v of a line-search trial
+  T* w = nullptr;       // [3][N] beta A vt, carried through PCG
+  T* q = nullptr;       // [3][N] beta A s, carried through PCG
   double* partials = nullptr;  // reduction partials
   double* scal = nullptr;      // device scalars
 };
@@ -64,6 +69,38 @@ struct claire_ctx {
   claire::Work<double> wd{};
   bool lin_valid = false;
   double* hscal = nullptr;  // pinned host mirror of Work::scal
+  // optional per-launch CUDA-event timing (off by default): one event pair per kernel launch, summed per name
+  struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  ProfRec prof_pending{};
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  cudaEvent_t prof_event() {
+    cudaEvent_t e = nullptr;
+    if (!prof_pool.empty()) {
+      e = prof_pool.back();
+      prof_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+    }
+    return e;
+  }
+  void prof_begin(const char* name, cudaStream_t st) {
+    if (!prof_on) return;
+    prof_pending.name = name;
+    prof_pending.a = prof_event();
+    prof_pending.b = prof_event();
+    if (prof_pending.a) cudaEventRecord(prof_pending.a, st);
+  }
+  void prof_end(cudaStream_t st) {
+    if (!prof_on || !prof_pending.a || !prof_pending.b) return;
+    cudaEventRecord(prof_pending.b, st);
+    prof_recs.push_back(prof_pending);
+    prof_pending = ProfRec{};
+  }
   void set_error(const std::string& s) { err = s; }
   template <class T> claire::Work<T>& work();
   template <class T> claire::FFTPlan<T>& plan();
@@ -143,5 +180,13 @@ template <class T> claire_status waxpy(claire_ctx* c, long long n, const T* x, d
 template <class T> claire_status pcg_update(claire_ctx* c, long long n, double k, const T* s, const T* Hs, T* vt, T* r,
                                             double* partials, cudaStream_t st);
 template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st);
+// sums[c] = sum of component c of a vector (FP64), c = 0, 1, 2
+template <class T> claire_status component_sums(claire_ctx* c, const T* x, double* sums, cudaStream_t st);
+// q = (r - mean_c(r)) + mu q per component, mean_c = sums[c] / N  (beta A z = r - mean(r) for z = M^-1 r)
+template <class T> claire_status q_update(claire_ctx* c, const T* r, const double* sums, double mu, T* q,
+                                          cudaStream_t st);
+// vt += k s; w += k q; r -= k Hs; partials of ||r||^2
+template <class T> claire_status pcg_update2(claire_ctx* c, long long n, double k, const T* s, const T* q, const T* Hs,
+                                             T* vt, T* w, T* r, double* partials, cudaStream_t st);
 
 }  // namespace claire

@@ -215,12 +215,14 @@ template <class T> claire_status sl_departure(claire_ctx* c, const T* v, int dir
   const double dt = 1.0 / c->o.nt;
   const double twopi = 6.283185307179586476925286766559;
   const T ih1 = T(d.n1 / twopi), ih2 = T(d.n2 / twopi), ih3 = T(d.n3 / twopi);
+  c->prof_begin("sl_departure", st);
   k_departure<T><<<blocks_for(d.N), kThreads, 0, st>>>(v, disp, T(dir * dt), ih1, ih2, ih3, d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 
 template <class T> claire_status sl_interp(claire_ctx* c, const T* f, const T* disp, T* out, cudaStream_t st) {
+  c->prof_begin("sl_interp", st);
   k_interp<T><<<blocks_for(c->d.N), kThreads, 0, st>>>(f, disp, out, c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
@@ -229,6 +231,7 @@ template <class T> claire_status sl_interp(claire_ctx* c, const T* f, const T* d
 template <class T>
 claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR, const T* m1, const T* rho, T* lam, T* rl, T* b,
                                   const T* gmj, T w, cudaStream_t st) {
+  c->prof_begin(rho ? "sl_adj_terminal_rho" : "sl_adj_terminal", st);
   if (rho)
     k_adj_terminal<T, true><<<blocks_for(c->d.N), kThreads, 0, st>>>(mR, m1, rho, lam, rl, b, gmj, w, c->d);
   else
@@ -243,6 +246,10 @@ claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next
   const T dt = T(1.0 / c->o.nt);
   const unsigned g = blocks_for(c->d.N);
   const int key = (rho ? 4 : 0) | (lam ? 2 : 0) | (b ? 1 : 0);
+  static const char* names[8] = {"sl_adj_step", "sl_adj_step_acc", "sl_adj_step_store", "sl_adj_step_store_acc",
+                                 "sl_adj_step_rho", "sl_adj_step_rho_acc", "sl_adj_step_rho_store",
+                                 "sl_adj_step_rho_store_acc"};
+  c->prof_begin(names[key], st);
 #define ADJ(R, S, A) \
   k_adj_step<T, R, S, A><<<g, kThreads, 0, st>>>(lam_next, rl_next, rho, dY, lam, rl, b, gmj, w, dt, c->d)
   switch (key) {
@@ -261,6 +268,7 @@ claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next
 }
 
 template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, const T* gm0, T* q, cudaStream_t st) {
+  c->prof_begin("sl_inc_init", st);
   k_inc_init<T><<<blocks_for(c->d.N), kThreads, 0, st>>>(vt, gm0, q, T(0.5 / c->o.nt), c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
@@ -271,6 +279,7 @@ claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* 
                                const T* rho, T* rl, T* b, T w, cudaStream_t st) {
   const T hdt = T(0.5 / c->o.nt);
   const unsigned g = blocks_for(c->d.N);
+  c->prof_begin(!last ? "sl_inc_step" : (rho ? "sl_inc_step_last_rho" : "sl_inc_step_last"), st);
   if (!last)
     k_inc_step<T, false, false><<<g, kThreads, 0, st>>>(q, dX, vt, gmj1, qout, rho, rl, b, hdt, w, c->d);
   else if (rho)
@@ -282,6 +291,7 @@ claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* 
 }
 
 template <class T> claire_status sl_hadamard(claire_ctx* c, const T* a, const T* x, T* y, cudaStream_t st) {
+  c->prof_begin("hadamard", st);
   k_hadamard<T><<<blocks_for(c->d.N), kThreads, 0, st>>>(a, x, y, c->d.N);
   CL_LAUNCHED(c);
   return CLAIRE_OK;

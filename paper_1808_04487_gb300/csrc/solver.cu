@@ -6,7 +6,9 @@
 // outer (Alg. 1) and inner (Alg. 2) loops; every scalar it needs (objective, norms, PCG scalars, Armijo test)
 // is reduced in FP64 on the device and read back once per use.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "impl.cuh"
@@ -40,7 +42,8 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
   ok &= takeT(W.b, 3 * N);
   W.spec = static_cast<cplx<T>*>(c->take(sizeof(cplx<T>) * size_t(6 * Ns)));
   ok &= W.spec != nullptr;
-  for (T** p : {&W.g, &W.vt, &W.r, &W.z, &W.s, &W.Hs, &W.vtrial, &W.vdev}) ok &= takeT(*p, 3 * N);
+  for (T** p : {&W.g, &W.vt, &W.r, &W.z, &W.s, &W.Hs, &W.vtrial, &W.vdev, &W.u, &W.utrial, &W.w, &W.q})
+    ok &= takeT(*p, 3 * N);
   ok &= takeT(W.mTdev, N);
   ok &= takeT(W.mRdev, N);
   ok &= takeT(W.m1trial, N);
@@ -57,7 +60,7 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
 template <class T> size_t work_bytes(const claire_opts& o, const Dims& d) {
   const long long N = d.N, Ns = d.Ns;
   const int nt = o.nt;
-  long long elems = 3 * N * 2 + (nt + 1) * N + 3 * (nt + 1) * N + (o.divfree ? 0 : N) + 4 * N + 3 * N + 8 * 3 * N +
+  long long elems = 3 * N * 2 + (nt + 1) * N + 3 * (nt + 1) * N + (o.divfree ? 0 : N) + 4 * N + 3 * N + 12 * 3 * N +
                     3 * N;
   size_t bytes = sizeof(T) * size_t(elems) + sizeof(cplx<T>) * size_t(6 * Ns) +
                  sizeof(double) * (kReduceBlocks + 32) + fft_table_bytes<T>(d) + 64 * 256;
@@ -221,8 +224,18 @@ template <class T> claire_status gradient_at_lin(claire_ctx* c, const T* mR, con
   return CLAIRE_OK;
 }
 
-// Gauss-Newton matvec at the cached linearisation (Eq. (7)-(9), lambda terms dropped)
-template <class T> claire_status hessvec_at_lin(claire_ctx* c, const T* vt, T* Hvt, cudaStream_t st) {
+// out = u + K b with b the time integral of the last backward sweep (u = beta A v carried by the caller)
+template <class T> claire_status add_projected_b(claire_ctx* c, const T* u, T* out, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const long long n3 = 3 * c->d.N;
+  if (c->o.divfree) {
+    CL_TRY(leray_inplace<T>(c, W.b, W.b, st));
+  }
+  return waxpy<T>(c, n3, u, 1.0, W.b, out, st);
+}
+
+// data part of the Gauss-Newton matvec at the cached linearisation: W.b = int lambda~ grad m dt (Eq. (8), (9))
+template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
   const int nt = c->o.nt;
@@ -244,11 +257,18 @@ template <class T> claire_status hessvec_at_lin(claire_ctx* c, const T* vt, T* H
                               st));
     cur = 1 - cur;
   }
-  return spectral_tail<T>(c, vt, W.b, Hvt, nullptr, st);
+  return CLAIRE_OK;
+}
+
+// Gauss-Newton matvec at the cached linearisation (Eq. (7)-(9), lambda terms dropped), applying beta A to vt
+// through its Fourier symbol (the entry point for an arbitrary vt)
+template <class T> claire_status hessvec_at_lin(claire_ctx* c, const T* vt, T* Hvt, cudaStream_t st) {
+  CL_TRY(hess_data<T>(c, vt, st));
+  return spectral_tail<T>(c, vt, c->work<T>().b, Hvt, nullptr, st);
 }
 
 // state at a trial v (departure X + state history) and its objective; one PDE solve
-template <class T> claire_status evaluate(claire_ctx* c, const T* mT, const T* mR, const T* v, double* J,
+template <class T> claire_status evaluate(claire_ctx* c, const T* mT, const T* mR, const T* v, const T* u, double* J,
                                           cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
@@ -257,23 +277,33 @@ template <class T> claire_status evaluate(claire_ctx* c, const T* mT, const T* m
   CL_TRY(state_history<T>(c, mT, st));
   CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
   CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
-  CL_TRY(vec_r2c<T>(c, v, W.spec, st));
-  CL_TRY(spec_reg_partial<T>(c, W.spec, W.partials, st));
-  CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(N), W.scal + 1, st));
+  // beta/2 sum_c <v_c, A v_c> = 1/2 <v, u>
+  CL_TRY(dot_partial<T>(c, v, u, 3 * N, W.partials, st));
+  CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal + 1, st));
   CL_CUDA(c, cudaMemcpyAsync(c->hscal, W.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CL_CUDA(c, cudaStreamSynchronize(st));
   *J = c->hscal[0] + c->hscal[1];
   return CLAIRE_OK;
 }
 
-// Alg. 2: PCG for H vt = -g with M^-1 = (beta A)^-1; relative break ||r|| < eps_H ||r_0||
+// Alg. 2: PCG for H vt = -g with M^-1 = (beta A)^-1; relative break ||r|| < eps_H ||r_0||.
+// beta A of the search direction is carried by recurrence instead of being re-applied spectrally: for
+// z = M^-1 r one has beta A z = r - mean(r) (M^-1 is (beta A)^-1 except on the constant mode, where it is 1),
+// so with s = z + mu s_old, q = beta A s = (r - mean(r)) + mu q_old, and H s = q + K[int lambda~ grad m dt].
+// The same recurrence gives w = beta A vt. This is the operator of Eq. (7) in exact arithmetic; in floating
+// point it avoids multiplying the rounding noise of a forward FFT by the symbol beta |k|^{2 regnorm}.
 template <class T> claire_status pcg(claire_ctx* c, const T* g, double eps_H, claire_report* rep, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long n3 = 3 * c->d.N;
+  double* sums = W.scal + 8;
   CL_CUDA(c, cudaMemsetAsync(W.vt, 0, sizeof(T) * n3, st));
+  CL_CUDA(c, cudaMemsetAsync(W.w, 0, sizeof(T) * n3, st));
+  CL_CUDA(c, cudaMemsetAsync(W.q, 0, sizeof(T) * n3, st));
   CL_TRY(scale_copy<T>(c, n3, -1.0, g, W.r, st));
   CL_TRY(precond_apply<T>(c, W.r, W.z, st));
   CL_CUDA(c, cudaMemcpyAsync(W.s, W.z, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+  CL_TRY(component_sums<T>(c, W.r, sums, st));
+  CL_TRY(q_update<T>(c, W.r, sums, 0.0, W.q, st));
   double rz, rr0;
   CL_TRY(inner<T>(c, W.r, W.z, n3, &rz, st));
   CL_TRY(inner<T>(c, W.r, W.r, n3, &rr0, st));
@@ -283,7 +313,8 @@ template <class T> claire_status pcg(claire_ctx* c, const T* g, double eps_H, cl
     return CLAIRE_ENAN;
   }
   for (int it = 0; it < c->o.max_krylov; ++it) {
-    CL_TRY(hessvec_at_lin<T>(c, W.s, W.Hs, st));
+    CL_TRY(hess_data<T>(c, W.s, st));
+    CL_TRY(add_projected_b<T>(c, W.q, W.Hs, st));
     rep->matvecs++;
     rep->pde_solves += 2;
     double sHs;
@@ -294,11 +325,14 @@ template <class T> claire_status pcg(claire_ctx* c, const T* g, double eps_H, cl
     }
     if (!(sHs > 0.0)) {
       rep->pcg_breakdowns++;
-      if (it == 0) CL_CUDA(c, cudaMemcpyAsync(W.vt, W.s, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+      if (it == 0) {
+        CL_CUDA(c, cudaMemcpyAsync(W.vt, W.s, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+        CL_CUDA(c, cudaMemcpyAsync(W.w, W.q, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+      }
       break;
     }
     const double kappa = rz / sHs;
-    CL_TRY(pcg_update<T>(c, n3, kappa, W.s, W.Hs, W.vt, W.r, W.partials, st));
+    CL_TRY(pcg_update2<T>(c, n3, kappa, W.s, W.q, W.Hs, W.vt, W.w, W.r, W.partials, st));
     CL_TRY(reduce_final(c, W.partials, cellvol(c->d), W.scal, st));
     double rr;
     CL_TRY(read_scalar(c, W.scal, &rr, st));
@@ -309,11 +343,23 @@ template <class T> claire_status pcg(claire_ctx* c, const T* g, double eps_H, cl
     const double mu = rz_new / rz;
     rz = rz_new;
     CL_TRY(xpay<T>(c, n3, W.z, mu, W.s, st));
+    CL_TRY(component_sums<T>(c, W.r, sums, st));
+    CL_TRY(q_update<T>(c, W.r, sums, mu, W.q, st));
   }
   return CLAIRE_OK;
 }
 
-// Alg. 1 with Armijo backtracking and the stopping rules of Sec. 2.3.2
+// u = beta A v through the spectral symbol (used once, for a nonzero initial guess)
+template <class T> claire_status apply_betaA(claire_ctx* c, const T* v, T* u, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  CL_TRY(vec_r2c<T>(c, v, W.spec, st));
+  CL_TRY(spec_scale<T>(c, W.spec, 3, c->d.Ns, 0, c->o.beta, st));
+  return vec_c2r<T>(c, W.spec, u, st);
+}
+
+// Alg. 1 with Armijo backtracking and the stopping rules of Sec. 2.3.2. u = beta A v is carried along with v
+// (u_{k+1} = u_k + alpha beta A vt_k, the latter from PCG), so the gradient g = u + K b and the objective
+// J = mismatch + 1/2 <v, u> never apply the regularisation symbol to a rounded field.
 template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
                                               cudaStream_t st) {
   Work<T>& W = c->work<T>();
@@ -326,26 +372,35 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
   CL_CUDA(c, cudaEventRecord(e0, st));
   claire_status status = CLAIRE_OK;
   do {
-    // mismatch of the template
     CL_TRY(diffsq_partial<T>(c, mT, mR, N, W.partials, st));
     CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
     CL_TRY(read_scalar(c, W.scal, &rep->mismatch0, st));
-    // reference gradient at v = 0
+    // reference gradient at v = 0 (Sec. 2.3.2): g_0 = K[int lambda grad m dt] with m = m_T
     double vv;
     CL_TRY(inner<T>(c, v, v, n3, &vv, st));
     CL_CUDA(c, cudaMemsetAsync(W.vtrial, 0, sizeof(T) * n3, st));
+    CL_CUDA(c, cudaMemsetAsync(W.u, 0, sizeof(T) * n3, st));
     CL_TRY(linearize<T>(c, mT, W.vtrial, st));
-    double J;
-    CL_TRY(gradient_at_lin<T>(c, mR, W.vtrial, W.g, &J, st));
+    CL_TRY(adjoint_integral<T>(c, mR, st));
+    CL_TRY(add_projected_b<T>(c, W.u, W.g, st));
     rep->pde_solves += 2;
     double gg;
     CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
     rep->gnorm0 = std::sqrt(gg);
+    double J = rep->mismatch0;
     if (vv > 0.0) {
+      CL_TRY(apply_betaA<T>(c, v, W.u, st));
       CL_TRY(linearize<T>(c, mT, v, st));
-      CL_TRY(gradient_at_lin<T>(c, mR, v, W.g, &J, st));
+      CL_TRY(adjoint_integral<T>(c, mR, st));
+      CL_TRY(add_projected_b<T>(c, W.u, W.g, st));
       rep->pde_solves += 2;
       CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
+      double mism, reg;
+      CL_TRY(diffsq_partial<T>(c, W.m + o.nt * N, mR, N, W.partials, st));
+      CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+      CL_TRY(read_scalar(c, W.scal, &mism, st));
+      CL_TRY(inner<T>(c, v, W.u, n3, &reg, st));
+      J = mism + 0.5 * reg;
     }
     rep->J0 = J;
     double gnorm = std::sqrt(gg);
@@ -365,14 +420,19 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
       }
       const double eps_H = o.pcg_rtol > 0 ? o.pcg_rtol : std::fmin(0.5, std::sqrt(gnorm / rep->gnorm0));
       CL_TRY(pcg<T>(c, W.g, eps_H, rep, st));
-      if (o.divfree) CL_TRY(leray_inplace<T>(c, W.vt, W.vt, st));
+      if (o.divfree) {
+        // re-project the step (idempotent in exact arithmetic; removes rounding drift); K commutes with A
+        CL_TRY(leray_inplace<T>(c, W.vt, W.vt, st));
+        CL_TRY(leray_inplace<T>(c, W.w, W.w, st));
+      }
       double gvt;
       CL_TRY(inner<T>(c, W.g, W.vt, n3, &gvt, st));
       double alpha = 1.0, Jt = 0.0;
       bool accepted = false;
       for (int t = 0; t < o.max_ls; ++t) {
         CL_TRY(waxpy<T>(c, n3, v, alpha, W.vt, W.vtrial, st));
-        CL_TRY(evaluate<T>(c, mT, mR, W.vtrial, &Jt, st));
+        CL_TRY(waxpy<T>(c, n3, W.u, alpha, W.w, W.utrial, st));
+        CL_TRY(evaluate<T>(c, mT, mR, W.vtrial, W.utrial, &Jt, st));
         rep->ls_trials++;
         rep->pde_solves++;
         if (!std::isfinite(Jt)) {
@@ -389,15 +449,17 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
       if (status != CLAIRE_OK) break;
       if (!accepted) {
         status = CLAIRE_ELINESEARCH;
-        // restore the linearisation at the last accepted v for the report
+        // restore the state at the last accepted v for the report
         CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
         CL_TRY(state_history<T>(c, mT, st));
         break;
       }
       CL_CUDA(c, cudaMemcpyAsync(v, W.vtrial, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
+      CL_CUDA(c, cudaMemcpyAsync(W.u, W.utrial, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
       // the accepted trial's state history is the state at the new v; only the adjoint solve is new
       CL_TRY(finish_linearization<T>(c, v, st));
-      CL_TRY(gradient_at_lin<T>(c, mR, v, W.g, nullptr, st));
+      CL_TRY(adjoint_integral<T>(c, mR, st));
+      CL_TRY(add_projected_b<T>(c, W.u, W.g, st));
       rep->pde_solves += 1;
       J = Jt;
       CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
@@ -559,6 +621,23 @@ template <class T> claire_status api_hessvec_cached(claire_ctx* c, const T* vt, 
     return CLAIRE_EINVAL;
   }
   return hessvec_at_lin<T>(c, vt, Hvt, (cudaStream_t)s);
+}
+template <class T> claire_status api_hessvec_data(claire_ctx* c, const T* vt, T* out, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, vt);
+  CHECK_PTR(c, out);
+  if (!c->lin_valid) {
+    c->set_error("no cached linearisation");
+    return CLAIRE_EINVAL;
+  }
+  if ((const void*)vt == (const void*)out) {
+    c->set_error("vt and out must not alias");
+    return CLAIRE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)s;
+  CL_CUDA(c, cudaMemsetAsync(out, 0, sizeof(T) * 3 * c->d.N, st));
+  CL_TRY(hess_data<T>(c, vt, st));
+  return add_projected_b<T>(c, out, out, st);
 }
 template <class T> claire_status api_hessvec(claire_ctx* c, const T* mT, const T* v, const T* vt, T* Hvt, void* s) {
   CHECK_CTX(c, T);
@@ -735,9 +814,49 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   return CLAIRE_OK;
 }
 
+claire_status claire_profile_enable(claire_ctx* c, int on) {
+  if (!c) return CLAIRE_EINVAL;
+  c->prof_on = on != 0;
+  return CLAIRE_OK;
+}
+
+claire_status claire_profile_report(claire_ctx* c, char* buf, size_t len) {
+  if (!c || !buf || len == 0) return CLAIRE_EINVAL;
+  CL_CUDA(c, cudaDeviceSynchronize());
+  std::map<std::string, std::pair<long long, double>> agg;
+  for (auto& r : c->prof_recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) ms = 0.f;
+    auto& e = agg[r.name];
+    e.first += 1;
+    e.second += ms;
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    char tmp[256];
+    std::snprintf(tmp, sizeof(tmp), "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
+                  kv.second.second);
+    out += tmp;
+    first = false;
+  }
+  out += "}";
+  std::strncpy(buf, out.c_str(), len - 1);
+  buf[len - 1] = 0;
+  return CLAIRE_OK;
+}
+
 claire_status claire_destroy(claire_ctx* c) {
   if (!c) return CLAIRE_OK;
   cudaDeviceSynchronize();
+  for (auto& r : c->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
   if (c->arena) cudaFree(c->arena);
   if (c->hscal) cudaFreeHost(c->hscal);
   delete c;
@@ -783,6 +902,12 @@ claire_status claire_hessvec_cached_f32(claire_ctx* c, const float* vt, float* H
 }
 claire_status claire_hessvec_cached_f64(claire_ctx* c, const double* vt, double* Hvt, void* s) {
   return api_hessvec_cached<double>(c, vt, Hvt, s);
+}
+claire_status claire_hessvec_data_f32(claire_ctx* c, const float* vt, float* out, void* s) {
+  return api_hessvec_data<float>(c, vt, out, s);
+}
+claire_status claire_hessvec_data_f64(claire_ctx* c, const double* vt, double* out, void* s) {
+  return api_hessvec_data<double>(c, vt, out, s);
 }
 claire_status claire_linearize_f32(claire_ctx* c, const float* mT, const float* v, void* s) {
   return api_linearize<float>(c, mT, v, s);

@@ -152,6 +152,7 @@ static inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads
 
 template <class T>
 claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G1, cplx<T>* G2, cudaStream_t st) {
+  c->prof_begin("spec_grad", st);
   k_spec_grad<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(F, G0, G1, G2, c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
@@ -159,11 +160,13 @@ claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G
 template <class T>
 claire_status spec_div(claire_ctx* c, const cplx<T>* V0, const cplx<T>* V1, const cplx<T>* V2, cplx<T>* D,
                        cudaStream_t st) {
+  c->prof_begin("spec_div", st);
   k_spec_div<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V0, V1, V2, D, c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T> claire_status spec_leray(claire_ctx* c, cplx<T>* V0, cplx<T>* V1, cplx<T>* V2, cudaStream_t st) {
+  c->prof_begin("spec_leray", st);
   k_spec_leray<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V0, V1, V2, c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
@@ -171,16 +174,19 @@ template <class T> claire_status spec_leray(claire_ctx* c, cplx<T>* V0, cplx<T>*
 template <class T>
 claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp, long long cstride, int mode, double beta,
                          cudaStream_t st) {
+  c->prof_begin("spec_scale", st);
   k_spec_scale<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V, ncomp, cstride, mode, c->o.regnorm, T(beta), c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T> claire_status spec_combine(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st) {
+  c->prof_begin("spec_combine", st);
   k_spec_combine<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V, B, c->o.regnorm, c->o.divfree, T(c->o.beta), c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T> claire_status spec_reg_partial(claire_ctx* c, const cplx<T>* V, double* partials, cudaStream_t st) {
+  c->prof_begin("spec_reg_partial", st);
   k_spec_reg_partial<T><<<kReduceBlocks, 256, 0, st>>>(V, c->o.regnorm, c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
