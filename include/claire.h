@@ -208,6 +208,22 @@ typedef struct {
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 
+/* Inner product that allocates nothing (the paper has no counterpart; this is a service for callers).
+ * *out (a DEVICE pointer to one double, written on `stream`) = scale * sum_i a[i] * b[i] over `count` floats,
+ * accumulated in FP64 with the same kernels and summation order as claire_dot_f32 (pass scale = h1 h2 h3 to get
+ * that call's <a, b>). No context is needed, and the call makes no cudaMalloc/cudaFree and calls no allocating
+ * library: it is meant for callers that must not allocate device memory, e.g. code running inside a fixed
+ * memory budget or a framework allocator that owns the device, or a loop that cannot afford cudaMalloc's implicit
+ * device synchronisation. Its partial sums live in a file-scope device array of 65536 doubles (512 KiB) that every
+ * GPU which loads this library keeps until the process exits, so count is limited to 65536 * 2048 = 134217728
+ * values (larger counts return CLAIRE_EINVAL, as do null pointers and count < 0; a CUDA launch error returns
+ * CLAIRE_ECUDA). The array is shared by every call in the process: calls whose kernels overlap on the GPU (two
+ * streams, or two host threads) race on it and must be serialised by the caller; nothing in it needs clearing
+ * between calls. The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. */
+claire_status claire_dot_noalloc_f32(const float* a, const float* b, long long count, double scale, double* out,
+                                     void* stream);
+
 /* Per-kernel timing (not part of the method; for measurement). While enabled, every kernel launch on ctx is
  * bracketed by a pair of CUDA events on its stream. claire_profile_report synchronises the device, writes a JSON
  * object {"kernel name": [launches, total_ms], ...} of everything recorded since the last report into buf

@@ -104,6 +104,8 @@ def lib():
     L.claire_workspace_bytes.restype = ctypes.c_size_t
     L.claire_get_counters.argtypes = [_VP, ctypes.POINTER(Counters)]
     L.claire_get_counters.restype = _I
+    L.claire_dot_noalloc_f32.argtypes = [_VP, _VP, _LL, _D, _VP, _VP]
+    L.claire_dot_noalloc_f32.restype = _I
     L.claire_profile_enable.argtypes = [_VP, _I]
     L.claire_profile_enable.restype = _I
     L.claire_profile_report.argtypes = [_VP, ctypes.c_char_p, ctypes.c_size_t]

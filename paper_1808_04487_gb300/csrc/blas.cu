@@ -1,6 +1,8 @@
 // Streaming vector kernels of the Krylov and Gauss-Newton loops (Alg. 1, Alg. 2): FP64-accumulated inner products
 // (warp-shuffle + shared-memory block reduction into a fixed number of partials, then a one-block deterministic
 // finish, so results are reproducible run to run) and the fused PCG updates.
+#include <mutex>
+
 #include "impl.cuh"
 
 namespace claire {
@@ -214,6 +216,36 @@ template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a
 
 constexpr int kSumBlocks = kReduceBlocks / 4;
 
+// ---- inner product without any allocation ------------------------------------------------------------------
+// The partial sums of k_dot go to this file-scope array instead of a context workspace. Each block writes its own
+// slot before the finishing kernel reads it, so nothing has to be cleared between calls.
+constexpr int kNoAllocBlocks = 1 << 16;           // partial-sum slots (512 KiB of FP64 on every device)
+constexpr long long kNoAllocChunk = 256LL * 8;    // values reduced per block
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocBlocks];
+
+// Host-side address of g_noalloc_partials on each device, looked up once per device (the host symbol itself is
+// only a stand-in and must never be passed to a kernel).
+static double* noalloc_scratch_on_current_device(claire_status* st) {
+  static std::mutex mu;
+  static double* addr[256] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    *st = CLAIRE_ECUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
+      *st = CLAIRE_ECUDA;
+      return nullptr;
+    }
+    addr[dev] = static_cast<double*>(p);
+  }
+  *st = CLAIRE_OK;
+  return addr[dev];
+}
+
 template <class T> claire_status component_sums(claire_ctx* c, const T* x, double* sums, cudaStream_t st) {
   double* partials = c->work<T>().partials;
   c->prof_begin("comp_sum", st);
@@ -258,3 +290,21 @@ INST(double)
 #undef INST
 
 }  // namespace claire
+
+extern "C" claire_status claire_dot_noalloc_f32(const float* a, const float* b, long long count, double scale,
+                                                double* out, void* stream) {
+  using namespace claire;
+  if (!a || !b || !out || count < 0) return CLAIRE_EINVAL;
+  const long long blocks = (count + kNoAllocChunk - 1) / kNoAllocChunk;
+  if (blocks > kNoAllocBlocks) return CLAIRE_EINVAL;
+  claire_status st = CLAIRE_OK;
+  double* partials = noalloc_scratch_on_current_device(&st);
+  if (st != CLAIRE_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = blocks > 0 ? (int)blocks : 1;
+  k_dot<float><<<nb, 256, 0, s>>>(a, b, count, partials);
+  if (cudaGetLastError() != cudaSuccess) return CLAIRE_ECUDA;
+  k_reduce_final<<<1, 1024, 0, s>>>(partials, nb, scale, out);
+  if (cudaGetLastError() != cudaSuccess) return CLAIRE_ECUDA;
+  return CLAIRE_OK;
+}
