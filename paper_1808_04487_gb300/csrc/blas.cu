@@ -75,86 +75,6 @@ __global__ void k_scale_copy(long long n, T a, const T* __restrict__ x, T* __res
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i];
 }
-template <class T>
-__global__ void __launch_bounds__(256) k_pcg_update(long long n, T k, const T* __restrict__ s,
-                                                    const T* __restrict__ Hs, T* __restrict__ vt, T* __restrict__ r,
-                                                    double* __restrict__ partials) {
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    vt[i] = fma(k, s[i], vt[i]);
-    const T ri = fma(-k, Hs[i], r[i]);
-    r[i] = ri;
-    acc += double(ri) * double(ri);
-  }
-  block_partial(acc, partials);
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_pcg_update2(long long n, T k, const T* __restrict__ s,
-                                                     const T* __restrict__ q, const T* __restrict__ Hs,
-                                                     T* __restrict__ vt, T* __restrict__ w, T* __restrict__ r,
-                                                     double* __restrict__ partials) {
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    vt[i] = fma(k, s[i], vt[i]);
-    w[i] = fma(k, q[i], w[i]);
-    const T ri = fma(-k, Hs[i], r[i]);
-    r[i] = ri;
-    acc += double(ri) * double(ri);
-  }
-  block_partial(acc, partials);
-}
-
-// one block row per component: grid (kReduceBlocks/4, 3); partials laid out [3][gridDim.x]
-template <class T>
-__global__ void __launch_bounds__(256) k_comp_sum(const T* __restrict__ x, long long N,
-                                                  double* __restrict__ partials) {
-  const T* xc = x + blockIdx.y * N;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    acc += double(xc[i]);
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
-  }
-}
-
-__global__ void k_comp_sum_final(const double* __restrict__ partials, int np, double* __restrict__ sums) {
-  __shared__ double red[32];
-  const double* p = partials + blockIdx.x * np;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += p[i];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) sums[blockIdx.x] = t;
-  }
-}
-
-template <class T>
-__global__ void k_q_update(const T* __restrict__ r, const double* __restrict__ sums, T mu, T* __restrict__ q,
-                           long long N) {
-  const double invN = 1.0 / double(N);
-  for (int c = 0; c < 3; ++c) {
-    const T mean = T(sums[c] * invN);
-    const T* rc = r + c * N;
-    T* qc = q + c * N;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x)
-      qc[i] = fma(mu, qc[i], rc[i] - mean);
-  }
-}
-
 static inline unsigned stream_blocks(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   return (unsigned)(b < 8 * 152 * 4 ? b : 8 * 152 * 4);
@@ -174,6 +94,30 @@ claire_status diffsq_partial(claire_ctx* c, const T* a, const T* b, long long n,
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
+__global__ void __launch_bounds__(1024) k_reduce_final_v(const double* __restrict__ partials, int np, double scale,
+                                                         double* __restrict__ out) {
+  __shared__ double red[32];
+  const double* p = partials + (long long)blockIdx.x * np;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += p[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = scale * t;
+  }
+}
+
+claire_status reduce_final_v(claire_ctx* c, const double* partials, int nv, int np, double scale, double* out,
+                             cudaStream_t st) {
+  c->prof_begin("reduce_final_v", st);
+  k_reduce_final_v<<<nv, 1024, 0, st>>>(partials, np, scale, out);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+
 claire_status reduce_final(claire_ctx* c, const double* partials, double scale, double* out, cudaStream_t st) {
   c->prof_begin("reduce_final", st);
   k_reduce_final<<<1, 1024, 0, st>>>(partials, kReduceBlocks, scale, out);
@@ -199,14 +143,6 @@ claire_status waxpy(claire_ctx* c, long long n, const T* x, double a, const T* y
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
-template <class T>
-claire_status pcg_update(claire_ctx* c, long long n, double k, const T* s, const T* Hs, T* vt, T* r, double* partials,
-                         cudaStream_t st) {
-  c->prof_begin("pcg_update", st);
-  k_pcg_update<T><<<kReduceBlocks, 256, 0, st>>>(n, T(k), s, Hs, vt, r, partials);
-  CL_LAUNCHED(c);
-  return CLAIRE_OK;
-}
 template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st) {
   c->prof_begin("scale_copy", st);
   k_scale_copy<T><<<stream_blocks(n), kThreads, 0, st>>>(n, T(a), x, y);
@@ -214,7 +150,6 @@ template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a
   return CLAIRE_OK;
 }
 
-constexpr int kSumBlocks = kReduceBlocks / 4;
 
 // ---- inner product without any allocation ------------------------------------------------------------------
 // The partial sums of k_dot go to this file-scope array instead of a context workspace. Each block writes its own
@@ -246,44 +181,12 @@ static double* noalloc_scratch_on_current_device(claire_status* st) {
   return addr[dev];
 }
 
-template <class T> claire_status component_sums(claire_ctx* c, const T* x, double* sums, cudaStream_t st) {
-  double* partials = c->work<T>().partials;
-  c->prof_begin("comp_sum", st);
-  k_comp_sum<T><<<dim3(kSumBlocks, 3), 256, 0, st>>>(x, c->d.N, partials);
-  CL_LAUNCHED(c);
-  c->prof_begin("comp_sum_final", st);
-  k_comp_sum_final<<<3, 1024, 0, st>>>(partials, kSumBlocks, sums);
-  CL_LAUNCHED(c);
-  return CLAIRE_OK;
-}
-template <class T>
-claire_status q_update(claire_ctx* c, const T* r, const double* sums, double mu, T* q, cudaStream_t st) {
-  c->prof_begin("q_update", st);
-  k_q_update<T><<<stream_blocks(c->d.N), kThreads, 0, st>>>(r, sums, T(mu), q, c->d.N);
-  CL_LAUNCHED(c);
-  return CLAIRE_OK;
-}
-template <class T>
-claire_status pcg_update2(claire_ctx* c, long long n, double k, const T* s, const T* q, const T* Hs, T* vt, T* w, T* r,
-                          double* partials, cudaStream_t st) {
-  c->prof_begin("pcg_update2", st);
-  k_pcg_update2<T><<<kReduceBlocks, 256, 0, st>>>(n, T(k), s, q, Hs, vt, w, r, partials);
-  CL_LAUNCHED(c);
-  return CLAIRE_OK;
-}
-
 #define INST(T)                                                                                                   \
-  template claire_status component_sums<T>(claire_ctx*, const T*, double*, cudaStream_t);                        \
-  template claire_status q_update<T>(claire_ctx*, const T*, const double*, double, T*, cudaStream_t);             \
-  template claire_status pcg_update2<T>(claire_ctx*, long long, double, const T*, const T*, const T*, T*, T*, T*,  \
-                                        double*, cudaStream_t);                                                   \
   template claire_status dot_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);       \
   template claire_status diffsq_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);    \
   template claire_status axpy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);                     \
   template claire_status xpay<T>(claire_ctx*, long long, const T*, double, T*, cudaStream_t);                     \
   template claire_status waxpy<T>(claire_ctx*, long long, const T*, double, const T*, T*, cudaStream_t);          \
-  template claire_status pcg_update<T>(claire_ctx*, long long, double, const T*, const T*, T*, T*, double*,       \
-                                       cudaStream_t);                                                             \
   template claire_status scale_copy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);
 INST(float)
 INST(double)

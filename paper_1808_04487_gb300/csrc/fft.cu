@@ -214,10 +214,11 @@ __global__ void __launch_bounds__(256) k_fft_z_c2r(const cplx<T>* __restrict__ i
   }
 }
 
-// Strided axis (length L, element stride `inner`), in place; grid.x over column tiles, grid.y over outer slabs.
+// Strided axis (length L, element stride `inner`): reads src, writes data (src == data: in place); grid.x over
+// column tiles, grid.y over outer slabs.
 template <class T, int SIGN>
-__global__ void __launch_bounds__(256) k_fft_strided(cplx<T>* __restrict__ data, long long inner, RadixPlan rp,
-                                                     const cplx<T>* __restrict__ Wg, int TI) {
+__global__ void __launch_bounds__(256) k_fft_strided(const cplx<T>* src, cplx<T>* data, long long inner,
+                                                     RadixPlan rp, const cplx<T>* __restrict__ Wg, int TI) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* W = reinterpret_cast<cplx<T>*>(smem_raw);
   const int L = rp.L;
@@ -226,10 +227,12 @@ __global__ void __launch_bounds__(256) k_fft_strided(cplx<T>* __restrict__ data,
   for (int t = threadIdx.x; t < L; t += blockDim.x) W[t] = Wg[t];
   const long long i0 = (long long)blockIdx.x * TI;
   const int nc = (int)min((long long)TI, inner - i0);
-  cplx<T>* base = data + (long long)blockIdx.y * L * inner + i0;
+  const long long off = (long long)blockIdx.y * L * inner + i0;
+  cplx<T>* base = data + off;
+  const cplx<T>* sbase = src + off;
   for (int t = threadIdx.x; t < L * TI; t += blockDim.x) {
     const int a = t / TI, c = t - a * TI;
-    if (c < nc) A[t] = base[(long long)a * inner + c];
+    if (c < nc) A[t] = sbase[(long long)a * inner + c];
   }
   __syncthreads();
   const cplx<T>* Y = stockham<T, SIGN>(A, B, rp, nc, 1, TI, true, W, 1);
@@ -312,33 +315,34 @@ template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* ou
   {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
     c->prof_begin("fft_y_fwd", st);
-    k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(out, d.n3h, p.ax2, p.tw2, p.ti12);
+    k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(out, out, d.n3h, p.ax2, p.tw2, p.ti12);
     CL_LAUNCHED(c);
   }
   {
     const long long inner = (long long)d.n2 * d.n3h;
     dim3 grid((unsigned)((inner + p.ti12 - 1) / p.ti12), 1u);
     c->prof_begin("fft_x_fwd", st);
-    k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(out, inner, p.ax1, p.tw1, p.ti12);
+    k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(out, out, inner, p.ax1, p.tw1, p.ti12);
     CL_LAUNCHED(c);
   }
   return CLAIRE_OK;
 }
 
-template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st) {
+template <class T>
+claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st, const cplx<T>* src) {
   const FFTPlan<T>& p = c->plan<T>();
   const Dims& d = c->d;
   {
     const long long inner = (long long)d.n2 * d.n3h;
     dim3 grid((unsigned)((inner + p.ti12 - 1) / p.ti12), 1u);
     c->prof_begin("fft_x_inv", st);
-    k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(spec, inner, p.ax1, p.tw1, p.ti12);
+    k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(src ? src : spec, spec, inner, p.ax1, p.tw1, p.ti12);
     CL_LAUNCHED(c);
   }
   {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
     c->prof_begin("fft_y_inv", st);
-    k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(spec, d.n3h, p.ax2, p.tw2, p.ti12);
+    k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(spec, spec, d.n3h, p.ax2, p.tw2, p.ti12);
     CL_LAUNCHED(c);
   }
   {
@@ -358,7 +362,8 @@ template claire_status fft_init<float>(claire_ctx*);
 template claire_status fft_init<double>(claire_ctx*);
 template claire_status fft_r2c<float>(claire_ctx*, const float*, cplx<float>*, cudaStream_t);
 template claire_status fft_r2c<double>(claire_ctx*, const double*, cplx<double>*, cudaStream_t);
-template claire_status fft_c2r<float>(claire_ctx*, cplx<float>*, float*, float, cudaStream_t);
-template claire_status fft_c2r<double>(claire_ctx*, cplx<double>*, double*, double, cudaStream_t);
+template claire_status fft_c2r<float>(claire_ctx*, cplx<float>*, float*, float, cudaStream_t, const cplx<float>*);
+template claire_status fft_c2r<double>(claire_ctx*, cplx<double>*, double*, double, cudaStream_t,
+                                        const cplx<double>*);
 
 }  // namespace claire

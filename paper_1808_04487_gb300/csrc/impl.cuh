@@ -31,22 +31,23 @@ template <class T> struct Work {
   T* rb = nullptr;      // [N] rho * adjoint pong
   T* b = nullptr;       // [3][N] time integral accumulator
   cplx<T>* spec = nullptr;  // 6 half spectra of Ns values
-  T* g = nullptr;       // solver vectors, [3][N] each
-  T* vt = nullptr;
-  T* r = nullptr;
-  T* z = nullptr;
-  T* s = nullptr;
-  T* Hs = nullptr;
-  T* vtrial = nullptr;
-  T* vdev = nullptr;    // device copy of v for the host-array API
+  T* s = nullptr;       // [3][N] PCG search direction in physical space (input of the matvec's SL solves)
+  T* vtrial = nullptr;  // [3][N] line-search trial velocity
+  T* vdev = nullptr;    // [3][N] device copy of v for the host-array API
   T* mTdev = nullptr;   // [N]
   T* mRdev = nullptr;   // [N]
-  T* m1trial = nullptr; // [N] scratch
-  T* u = nullptr;       // [3][N] beta A v, carried by recurrence through the Gauss-Newton loop
-  T* utrial = nullptr;  // [3][N] beta A v of a line-search trial
-  T* w = nullptr;       // [3][N] beta A vt, carried through PCG
-  T* q = nullptr;       // [3][N] beta A s, carried through PCG
-  double* partials = nullptr;  // reduction partials
+  // Fourier-domain solver vectors, 3 half spectra (component stride Ns) each
+  cplx<T>* Vh = nullptr;   // v (master copy)
+  cplx<T>* Vtrh = nullptr; // line-search trial v
+  cplx<T>* Gh = nullptr;   // reduced gradient
+  cplx<T>* Rh = nullptr;   // PCG residual
+  cplx<T>* Sh = nullptr;   // PCG direction
+  cplx<T>* VTh = nullptr;  // Newton step vt
+  cplx<T>* Bh = nullptr;   // transform of the time integral b
+  cplx<T>* Sc = nullptr;   // work array of inverse transforms
+  double* bigpart = nullptr;   // one FP64 partial per block of the gather launch shape
+  long long nbig = 0;
+  double* partials = nullptr;  // reduction partials, [4][kReduceBlocks]
   double* scal = nullptr;      // device scalars
 };
 
@@ -124,8 +125,10 @@ template <class T> size_t fft_table_bytes(const Dims& d);
 template <class T> claire_status fft_init(claire_ctx* c);
 // forward R2C of a scalar: in [N] real -> out [Ns] half spectrum (unnormalised)
 template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* out, cudaStream_t st);
-// inverse C2R: spec [Ns] (overwritten) -> out [N], multiplied by `scale` (1/N for the true inverse)
-template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st);
+// inverse C2R: spec [Ns] (overwritten) -> out [N], multiplied by `scale` (1/N for the true inverse). With src
+// given, the first pass reads src instead of spec (src is left untouched; spec is used as the work array).
+template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st,
+                                         const cplx<T>* src = nullptr);
 
 // ---- spectral.cu ----------------------------------------------------------------------------------------------
 template <class T> claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G1, cplx<T>* G2,
@@ -141,6 +144,22 @@ template <class T> claire_status spec_combine(claire_ctx* c, const cplx<T>* V, c
 // partial sums of sum_c sum_{half k} w(k3) a(k) |V_c(k)|^2 into partials[kReduceBlocks]
 template <class T> claire_status spec_reg_partial(claire_ctx* c, const cplx<T>* V, double* partials, cudaStream_t st);
 
+// Fourier-domain solver vectors (3 components of Ns each); partials laid out [value][kReduceBlocks]
+template <class T> claire_status sp_grad(claire_ctx* c, const cplx<T>* V, const cplx<T>* B, cplx<T>* G,
+                                         double* partials, cudaStream_t st);
+template <class T> claire_status sp_pcg0(claire_ctx* c, const cplx<T>* G, cplx<T>* R, cplx<T>* S, cplx<T>* Vt,
+                                         double* partials, cudaStream_t st);
+template <class T> claire_status sp_pcg_step(claire_ctx* c, const cplx<T>* S, const cplx<T>* Bt, cplx<T>* R,
+                                             cplx<T>* Vt, double kappa, double* partials, cudaStream_t st);
+template <class T> claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cplx<T>* S, double mu, double* partials,
+                                            cudaStream_t st);
+template <class T> claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G, cplx<T>* Vt, double* partials,
+                                                cudaStream_t st);
+template <class T> claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr,
+                                          cplx<T>* Sc, double alpha, double* partials, cudaStream_t st);
+template <class T> claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* partials,
+                                             cudaStream_t st);
+
 // ---- sl.cu ----------------------------------------------------------------------------------------------------
 template <class T> claire_status sl_hadamard(claire_ctx* c, const T* a, const T* x, T* y, cudaStream_t st);
 template <class T> claire_status sl_departure(claire_ctx* c, const T* v, int dir, T* disp, cudaStream_t st);
@@ -150,9 +169,15 @@ template <class T> claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR,
                                                      T* rl, T* b, const T* gmj, T w, cudaStream_t st);
 // one backward continuity step along Y; rho/rl_next: div source (or null); lam/rl: stores (or null);
 // b: accumulation b += w lam grad m (or null)
+// with sdot (and lam == null, b != null): also part[block] = partial <sdot, b_final>, one slot per block of launch3
 template <class T> claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next, const T* rho,
                                                  const T* dY, T* lam, T* rl, T* b, const T* gmj, T w,
-                                                 cudaStream_t st);
+                                                 cudaStream_t st, const T* sdot = nullptr, double* part = nullptr);
+// launch shape of the gather kernels: 256 threads, x along i3 (up to 64 wide), y along i2, z = i1
+struct Launch3 {
+  dim3 grid, block;
+};
+Launch3 launch3(const Dims& d);
 // q^0 = -(dt/2) vt . grad m^0
 template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, const T* gm0, T* q, cudaStream_t st);
 // m~^{j+1} = q^j(X) + dt/2 f^{j+1}; writes q^{j+1}, or on the last step lam~ = -m~, rho*lam~, b = w lam~ grad m
@@ -176,17 +201,8 @@ template <class T> claire_status xpay(claire_ctx* c, long long n, const T* x, do
 // z = x + a*y
 template <class T> claire_status waxpy(claire_ctx* c, long long n, const T* x, double a, const T* y, T* z,
                                        cudaStream_t st);
-// vt += k s; r -= k Hs; partials of ||r||^2
-template <class T> claire_status pcg_update(claire_ctx* c, long long n, double k, const T* s, const T* Hs, T* vt, T* r,
-                                            double* partials, cudaStream_t st);
 template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st);
-// sums[c] = sum of component c of a vector (FP64), c = 0, 1, 2
-template <class T> claire_status component_sums(claire_ctx* c, const T* x, double* sums, cudaStream_t st);
-// q = (r - mean_c(r)) + mu q per component, mean_c = sums[c] / N  (beta A z = r - mean(r) for z = M^-1 r)
-template <class T> claire_status q_update(claire_ctx* c, const T* r, const double* sums, double mu, T* q,
-                                          cudaStream_t st);
-// vt += k s; w += k q; r -= k Hs; partials of ||r||^2
-template <class T> claire_status pcg_update2(claire_ctx* c, long long n, double k, const T* s, const T* q, const T* Hs,
-                                             T* vt, T* w, T* r, double* partials, cudaStream_t st);
-
+// out[v] = scale * sum(partials[v * np .. v * np + np)) for v < nv
+claire_status reduce_final_v(claire_ctx* c, const double* partials, int nv, int np, double scale, double* out,
+                             cudaStream_t st);
 }  // namespace claire

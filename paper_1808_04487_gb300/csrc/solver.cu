@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <utility>
 
 #include "impl.cuh"
 
@@ -29,6 +30,10 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
     p = static_cast<T*>(c->take(sizeof(T) * size_t(count)));
     return p != nullptr;
   };
+  auto takeC = [&](cplx<T>*& p, long long count) -> bool {
+    p = static_cast<cplx<T>*>(c->take(sizeof(cplx<T>) * size_t(count)));
+    return p != nullptr;
+  };
   bool ok = true;
   ok &= takeT(W.dX, 3 * N);
   ok &= takeT(W.dY, 3 * N);
@@ -40,16 +45,17 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
   ok &= takeT(W.ra, N);
   ok &= takeT(W.rb, N);
   ok &= takeT(W.b, 3 * N);
-  W.spec = static_cast<cplx<T>*>(c->take(sizeof(cplx<T>) * size_t(6 * Ns)));
-  ok &= W.spec != nullptr;
-  for (T** p : {&W.g, &W.vt, &W.r, &W.z, &W.s, &W.Hs, &W.vtrial, &W.vdev, &W.u, &W.utrial, &W.w, &W.q})
-    ok &= takeT(*p, 3 * N);
+  ok &= takeC(W.spec, 6 * Ns);
+  for (T** p : {&W.s, &W.vtrial, &W.vdev}) ok &= takeT(*p, 3 * N);
   ok &= takeT(W.mTdev, N);
   ok &= takeT(W.mRdev, N);
-  ok &= takeT(W.m1trial, N);
-  W.partials = static_cast<double*>(c->take(sizeof(double) * kReduceBlocks));
+  for (cplx<T>** p : {&W.Vh, &W.Vtrh, &W.Gh, &W.Rh, &W.Sh, &W.VTh, &W.Bh, &W.Sc}) ok &= takeC(*p, 3 * Ns);
+  const Launch3 L = launch3(c->d);
+  W.nbig = (long long)L.grid.x * L.grid.y * L.grid.z;
+  W.bigpart = static_cast<double*>(c->take(sizeof(double) * size_t(W.nbig)));
+  W.partials = static_cast<double*>(c->take(sizeof(double) * 4 * kReduceBlocks));
   W.scal = static_cast<double*>(c->take(sizeof(double) * 32));
-  ok &= W.partials != nullptr && W.scal != nullptr;
+  ok &= W.partials != nullptr && W.scal != nullptr && W.bigpart != nullptr;
   if (!ok) {
     c->set_error("workspace arena too small");
     return CLAIRE_ENOMEM;
@@ -60,11 +66,13 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
 template <class T> size_t work_bytes(const claire_opts& o, const Dims& d) {
   const long long N = d.N, Ns = d.Ns;
   const int nt = o.nt;
-  long long elems = 3 * N * 2 + (nt + 1) * N + 3 * (nt + 1) * N + (o.divfree ? 0 : N) + 4 * N + 3 * N + 12 * 3 * N +
-                    3 * N;
-  size_t bytes = sizeof(T) * size_t(elems) + sizeof(cplx<T>) * size_t(6 * Ns) +
-                 sizeof(double) * (kReduceBlocks + 32) + fft_table_bytes<T>(d) + 64 * 256;
-  return bytes;
+  const long long elems = 3 * N * 2 + (nt + 1) * N + 3 * (nt + 1) * N + (o.divfree ? 0 : N) + 4 * N + 3 * N +
+                          3 * 3 * N + 2 * N;
+  const long long celems = 6 * Ns + 8 * 3 * Ns;
+  const Launch3 L = launch3(d);
+  const long long nbig = (long long)L.grid.x * L.grid.y * L.grid.z;
+  return sizeof(T) * size_t(elems) + sizeof(cplx<T>) * size_t(celems) +
+         sizeof(double) * size_t(nbig + 4 * kReduceBlocks + 32) + fft_table_bytes<T>(d) + 64 * 256;
 }
 
 // Read scal[slot] to the host (synchronises the stream).
@@ -234,8 +242,9 @@ template <class T> claire_status add_projected_b(claire_ctx* c, const T* u, T* o
   return waxpy<T>(c, n3, u, 1.0, W.b, out, st);
 }
 
-// data part of the Gauss-Newton matvec at the cached linearisation: W.b = int lambda~ grad m dt (Eq. (8), (9))
-template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStream_t st) {
+// data part of the Gauss-Newton matvec at the cached linearisation: W.b = int lambda~ grad m dt (Eq. (8), (9)).
+// With dot = true the last backward step also writes the per-block partials of <vt, W.b> to W.bigpart.
+template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStream_t st, bool dot = false) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
   const int nt = c->o.nt;
@@ -254,7 +263,7 @@ template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStrea
     const bool store = j > 0;
     CL_TRY(sl_adjoint_step<T>(c, buf[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? buf[1 - cur] : nullptr,
                               (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)),
-                              st));
+                              st, (dot && j == 0) ? vt : nullptr, (dot && j == 0) ? W.bigpart : nullptr));
     cur = 1 - cur;
   }
   return CLAIRE_OK;
@@ -267,104 +276,108 @@ template <class T> claire_status hessvec_at_lin(claire_ctx* c, const T* vt, T* H
   return spectral_tail<T>(c, vt, c->work<T>().b, Hvt, nullptr, st);
 }
 
-// state at a trial v (departure X + state history) and its objective; one PDE solve
-template <class T> claire_status evaluate(claire_ctx* c, const T* mT, const T* mR, const T* v, const T* u, double* J,
-                                          cudaStream_t st) {
+// 1/2 ||m^{nt} - mR||^2 of the state at v (departure X + state history; one PDE solve) into scal[slot]
+template <class T> claire_status state_mismatch(claire_ctx* c, const T* mT, const T* mR, const T* v, int slot,
+                                                cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
   c->lin_valid = false;
   CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
   CL_TRY(state_history<T>(c, mT, st));
   CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
-  CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
-  // beta/2 sum_c <v_c, A v_c> = 1/2 <v, u>
-  CL_TRY(dot_partial<T>(c, v, u, 3 * N, W.partials, st));
-  CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal + 1, st));
-  CL_CUDA(c, cudaMemcpyAsync(c->hscal, W.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal + slot, st);
+}
+
+claire_status read_scalars(claire_ctx* c, const double* dev, int n, double* out, cudaStream_t st) {
+  CL_CUDA(c, cudaMemcpyAsync(c->hscal, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   CL_CUDA(c, cudaStreamSynchronize(st));
-  *J = c->hscal[0] + c->hscal[1];
+  for (int i = 0; i < n; ++i) out[i] = c->hscal[i];
   return CLAIRE_OK;
 }
 
-// Alg. 2: PCG for H vt = -g with M^-1 = (beta A)^-1; relative break ||r|| < eps_H ||r_0||.
-// beta A of the search direction is carried by recurrence instead of being re-applied spectrally: for
-// z = M^-1 r one has beta A z = r - mean(r) (M^-1 is (beta A)^-1 except on the constant mode, where it is 1),
-// so with s = z + mu s_old, q = beta A s = (r - mean(r)) + mu q_old, and H s = q + K[int lambda~ grad m dt].
-// The same recurrence gives w = beta A vt. This is the operator of Eq. (7) in exact arithmetic; in floating
-// point it avoids multiplying the rounding noise of a forward FFT by the symbol beta |k|^{2 regnorm}.
-template <class T> claire_status pcg(claire_ctx* c, const T* g, double eps_H, claire_report* rep, cudaStream_t st) {
+// s = F^-1 S (three components; S is left untouched, W.Sc is the work array)
+template <class T> claire_status spec_to_phys(claire_ctx* c, const cplx<T>* S, T* s, cudaStream_t st) {
   Work<T>& W = c->work<T>();
-  const long long n3 = 3 * c->d.N;
-  double* sums = W.scal + 8;
-  CL_CUDA(c, cudaMemsetAsync(W.vt, 0, sizeof(T) * n3, st));
-  CL_CUDA(c, cudaMemsetAsync(W.w, 0, sizeof(T) * n3, st));
-  CL_CUDA(c, cudaMemsetAsync(W.q, 0, sizeof(T) * n3, st));
-  CL_TRY(scale_copy<T>(c, n3, -1.0, g, W.r, st));
-  CL_TRY(precond_apply<T>(c, W.r, W.z, st));
-  CL_CUDA(c, cudaMemcpyAsync(W.s, W.z, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
-  CL_TRY(component_sums<T>(c, W.r, sums, st));
-  CL_TRY(q_update<T>(c, W.r, sums, 0.0, W.q, st));
-  double rz, rr0;
-  CL_TRY(inner<T>(c, W.r, W.z, n3, &rz, st));
-  CL_TRY(inner<T>(c, W.r, W.r, n3, &rr0, st));
-  const double r0 = std::sqrt(rr0);
+  const long long Ns = c->d.Ns;
+  const T inv = T(1.0 / double(c->d.N));
+  for (int k = 0; k < 3; ++k) CL_TRY(fft_c2r<T>(c, W.Sc + k * Ns, comp(s, c->d, k), inv, st, S + k * Ns));
+  return CLAIRE_OK;
+}
+
+// gradient at the cached linearisation into W.Gh: G = beta A V + K F[b] (V null: v = 0); scal[slot] = ||g||^2
+template <class T> claire_status gradient_spec(claire_ctx* c, const T* mR, const cplx<T>* V, int slot,
+                                               cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  CL_TRY(adjoint_integral<T>(c, mR, st));
+  CL_TRY(vec_r2c<T>(c, W.b, W.Bh, st));
+  CL_TRY(sp_grad<T>(c, V, W.Bh, W.Gh, W.partials, st));
+  return reduce_final_v(c, W.partials, 1, kReduceBlocks, cellvol(c->d) / double(c->d.N), W.scal + slot, st);
+}
+
+// Alg. 2 in the Fourier domain: PCG for H vt = -g with M^-1 = (beta A)^-1 and the relative break
+// ||r|| < eps_H ||r_0||. r, s, vt and g are half spectra; beta A, M^-1 and K act as exact diagonal multiplies, and
+// inner products follow from Parseval, so the iterates are those of Alg. 2 in exact arithmetic. Each iteration
+// transforms s back to physical space for the incremental solves (Eq. (8), (9)) and their time integral b~ forward;
+// <s, H s> = <s, beta A s> (spectral) + <s, b~> (fused into the last backward gather).
+template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report* rep, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  const double sc = cellvol(c->d) / double(c->d.N);  // Parseval scale h1 h2 h3 / N
+  CL_TRY(sp_pcg0<T>(c, W.Gh, W.Rh, W.Sh, W.VTh, W.partials, st));
+  CL_TRY(reduce_final_v(c, W.partials, 3, kReduceBlocks, sc, W.scal, st));  // <r,z>, ||r||^2, <s,beta A s>
+  double v3[3];
+  CL_TRY(read_scalars(c, W.scal, 3, v3, st));
+  double rz = v3[0];
+  const double r0 = std::sqrt(v3[1]);
+  double sAs = v3[2];
   if (!std::isfinite(rz) || !std::isfinite(r0)) {
     c->set_error("non-finite PCG scalar");
     return CLAIRE_ENAN;
   }
+  CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
   for (int it = 0; it < c->o.max_krylov; ++it) {
-    CL_TRY(hess_data<T>(c, W.s, st));
-    CL_TRY(add_projected_b<T>(c, W.q, W.Hs, st));
+    CL_TRY(hess_data<T>(c, W.s, st, true));
+    CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)W.nbig, cellvol(c->d), W.scal + 4, st));
+    CL_TRY(vec_r2c<T>(c, W.b, W.Bh, st));
     rep->matvecs++;
     rep->pde_solves += 2;
-    double sHs;
-    CL_TRY(inner<T>(c, W.s, W.Hs, n3, &sHs, st));
+    double sBt;
+    CL_TRY(read_scalars(c, W.scal + 4, 1, &sBt, st));
+    const double sHs = sAs + sBt;
     if (!std::isfinite(sHs)) {
       c->set_error("non-finite <s, Hs>");
       return CLAIRE_ENAN;
     }
     if (!(sHs > 0.0)) {
       rep->pcg_breakdowns++;
-      if (it == 0) {
-        CL_CUDA(c, cudaMemcpyAsync(W.vt, W.s, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
-        CL_CUDA(c, cudaMemcpyAsync(W.w, W.q, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
-      }
+      if (it == 0)
+        CL_CUDA(c, cudaMemcpyAsync(W.VTh, W.Sh, sizeof(cplx<T>) * 3 * c->d.Ns, cudaMemcpyDeviceToDevice, st));
       break;
     }
     const double kappa = rz / sHs;
-    CL_TRY(pcg_update2<T>(c, n3, kappa, W.s, W.q, W.Hs, W.vt, W.w, W.r, W.partials, st));
-    CL_TRY(reduce_final(c, W.partials, cellvol(c->d), W.scal, st));
-    double rr;
-    CL_TRY(read_scalar(c, W.scal, &rr, st));
-    if (std::sqrt(rr) < eps_H * r0) break;
-    CL_TRY(precond_apply<T>(c, W.r, W.z, st));
-    double rz_new;
-    CL_TRY(inner<T>(c, W.r, W.z, n3, &rz_new, st));
-    const double mu = rz_new / rz;
-    rz = rz_new;
-    CL_TRY(xpay<T>(c, n3, W.z, mu, W.s, st));
-    CL_TRY(component_sums<T>(c, W.r, sums, st));
-    CL_TRY(q_update<T>(c, W.r, sums, mu, W.q, st));
+    CL_TRY(sp_pcg_step<T>(c, W.Sh, W.Bh, W.Rh, W.VTh, kappa, W.partials, st));
+    CL_TRY(reduce_final_v(c, W.partials, 2, kReduceBlocks, sc, W.scal, st));  // ||r||^2, <r, z>
+    double v2[2];
+    CL_TRY(read_scalars(c, W.scal, 2, v2, st));
+    if (std::sqrt(v2[0]) < eps_H * r0) break;
+    const double mu = v2[1] / rz;
+    rz = v2[1];
+    CL_TRY(sp_pcg_dir<T>(c, W.Rh, W.Sh, mu, W.partials, st));
+    CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 2, st));
+    CL_TRY(read_scalars(c, W.scal + 2, 1, &sAs, st));
+    CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
   }
   return CLAIRE_OK;
 }
 
-// u = beta A v through the spectral symbol (used once, for a nonzero initial guess)
-template <class T> claire_status apply_betaA(claire_ctx* c, const T* v, T* u, cudaStream_t st) {
-  Work<T>& W = c->work<T>();
-  CL_TRY(vec_r2c<T>(c, v, W.spec, st));
-  CL_TRY(spec_scale<T>(c, W.spec, 3, c->d.Ns, 0, c->o.beta, st));
-  return vec_c2r<T>(c, W.spec, u, st);
-}
-
-// Alg. 1 with Armijo backtracking and the stopping rules of Sec. 2.3.2. u = beta A v is carried along with v
-// (u_{k+1} = u_k + alpha beta A vt_k, the latter from PCG), so the gradient g = u + K b and the objective
-// J = mismatch + 1/2 <v, u> never apply the regularisation symbol to a rounded field.
+// Alg. 1 with Armijo backtracking and the stopping rules of Sec. 2.3.2. The iterate is kept as its half spectrum
+// (master copy) next to its physical values (needed by the departure points); the gradient, the step and the
+// regularisation value live in the Fourier domain (see pcg).
 template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
                                               cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N, n3 = 3 * N;
   const claire_opts& o = c->o;
+  const double sc = cellvol(c->d) / double(N);
   std::memset(rep, 0, sizeof(*rep));
   cudaEvent_t e0, e1;
   CL_CUDA(c, cudaEventCreate(&e0));
@@ -375,32 +388,32 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
     CL_TRY(diffsq_partial<T>(c, mT, mR, N, W.partials, st));
     CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
     CL_TRY(read_scalar(c, W.scal, &rep->mismatch0, st));
-    // reference gradient at v = 0 (Sec. 2.3.2): g_0 = K[int lambda grad m dt] with m = m_T
+    // reference gradient at v = 0 (Sec. 2.3.2)
     double vv;
     CL_TRY(inner<T>(c, v, v, n3, &vv, st));
     CL_CUDA(c, cudaMemsetAsync(W.vtrial, 0, sizeof(T) * n3, st));
-    CL_CUDA(c, cudaMemsetAsync(W.u, 0, sizeof(T) * n3, st));
     CL_TRY(linearize<T>(c, mT, W.vtrial, st));
-    CL_TRY(adjoint_integral<T>(c, mR, st));
-    CL_TRY(add_projected_b<T>(c, W.u, W.g, st));
+    CL_TRY(gradient_spec<T>(c, mR, (const cplx<T>*)nullptr, 0, st));
     rep->pde_solves += 2;
     double gg;
-    CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
+    CL_TRY(read_scalars(c, W.scal, 1, &gg, st));
     rep->gnorm0 = std::sqrt(gg);
     double J = rep->mismatch0;
     if (vv > 0.0) {
-      CL_TRY(apply_betaA<T>(c, v, W.u, st));
+      CL_TRY(vec_r2c<T>(c, v, W.Vh, st));
+      CL_TRY(sp_copy_reg<T>(c, W.Vh, nullptr, W.partials, st));
+      CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, 0.5 * o.beta * sc, W.scal + 5, st));
       CL_TRY(linearize<T>(c, mT, v, st));
-      CL_TRY(adjoint_integral<T>(c, mR, st));
-      CL_TRY(add_projected_b<T>(c, W.u, W.g, st));
-      rep->pde_solves += 2;
-      CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
-      double mism, reg;
       CL_TRY(diffsq_partial<T>(c, W.m + o.nt * N, mR, N, W.partials, st));
-      CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
-      CL_TRY(read_scalar(c, W.scal, &mism, st));
-      CL_TRY(inner<T>(c, v, W.u, n3, &reg, st));
-      J = mism + 0.5 * reg;
+      CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal + 6, st));
+      CL_TRY(gradient_spec<T>(c, mR, W.Vh, 0, st));
+      rep->pde_solves += 2;
+      double r3[7];
+      CL_TRY(read_scalars(c, W.scal, 7, r3, st));
+      gg = r3[0];
+      J = r3[6] + r3[5];
+    } else {
+      CL_CUDA(c, cudaMemsetAsync(W.Vh, 0, sizeof(cplx<T>) * 3 * c->d.Ns, st));
     }
     rep->J0 = J;
     double gnorm = std::sqrt(gg);
@@ -419,20 +432,22 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
         break;
       }
       const double eps_H = o.pcg_rtol > 0 ? o.pcg_rtol : std::fmin(0.5, std::sqrt(gnorm / rep->gnorm0));
-      CL_TRY(pcg<T>(c, W.g, eps_H, rep, st));
-      if (o.divfree) {
-        // re-project the step (idempotent in exact arithmetic; removes rounding drift); K commutes with A
-        CL_TRY(leray_inplace<T>(c, W.vt, W.vt, st));
-        CL_TRY(leray_inplace<T>(c, W.w, W.w, st));
-      }
+      CL_TRY(pcg<T>(c, eps_H, rep, st));
+      // re-project the step under div v = 0 (idempotent in exact arithmetic) and <g, vt> for the Armijo test
+      CL_TRY(sp_project_dot<T>(c, W.Gh, W.VTh, W.partials, st));
+      CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 7, st));
       double gvt;
-      CL_TRY(inner<T>(c, W.g, W.vt, n3, &gvt, st));
+      CL_TRY(read_scalars(c, W.scal + 7, 1, &gvt, st));
       double alpha = 1.0, Jt = 0.0;
       bool accepted = false;
       for (int t = 0; t < o.max_ls; ++t) {
-        CL_TRY(waxpy<T>(c, n3, v, alpha, W.vt, W.vtrial, st));
-        CL_TRY(waxpy<T>(c, n3, W.u, alpha, W.w, W.utrial, st));
-        CL_TRY(evaluate<T>(c, mT, mR, W.vtrial, W.utrial, &Jt, st));
+        CL_TRY(sp_trial<T>(c, W.Vh, W.VTh, W.Vtrh, W.Sc, alpha, W.partials, st));
+        CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, 0.5 * o.beta * sc, W.scal + 5, st));
+        CL_TRY(vec_c2r<T>(c, W.Sc, W.vtrial, st));
+        CL_TRY(state_mismatch<T>(c, mT, mR, W.vtrial, 6, st));
+        double r2[2];
+        CL_TRY(read_scalars(c, W.scal + 5, 2, r2, st));
+        Jt = r2[0] + r2[1];
         rep->ls_trials++;
         rep->pde_solves++;
         if (!std::isfinite(Jt)) {
@@ -449,20 +464,18 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
       if (status != CLAIRE_OK) break;
       if (!accepted) {
         status = CLAIRE_ELINESEARCH;
-        // restore the state at the last accepted v for the report
         CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
         CL_TRY(state_history<T>(c, mT, st));
         break;
       }
+      std::swap(W.Vh, W.Vtrh);
       CL_CUDA(c, cudaMemcpyAsync(v, W.vtrial, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
-      CL_CUDA(c, cudaMemcpyAsync(W.u, W.utrial, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st));
       // the accepted trial's state history is the state at the new v; only the adjoint solve is new
       CL_TRY(finish_linearization<T>(c, v, st));
-      CL_TRY(adjoint_integral<T>(c, mR, st));
-      CL_TRY(add_projected_b<T>(c, W.u, W.g, st));
+      CL_TRY(gradient_spec<T>(c, mR, W.Vh, 0, st));
       rep->pde_solves += 1;
       J = Jt;
-      CL_TRY(inner<T>(c, W.g, W.g, n3, &gg, st));
+      CL_TRY(read_scalars(c, W.scal, 1, &gg, st));
       gnorm = std::sqrt(gg);
       rep->gn_iters++;
       if (!std::isfinite(gnorm)) {
@@ -774,7 +787,8 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
       (o.precision != CLAIRE_F32 && o.precision != CLAIRE_F64) || o.max_gn < 0 || o.max_krylov < 1 || o.max_ls < 1)
     return CLAIRE_EINVAL;
   const long long N = (long long)o.n[0] * o.n[1] * o.n[2];
-  if ((long long)o.n[1] * o.n[2] > (1LL << 30) || N > (1LL << 31) - 1) return CLAIRE_EINVAL;
+  // 32-bit node indices in the kernels and the launch grid's z extent (one i1 slab per grid z index)
+  if (N > (1LL << 31) - 1 || o.n[0] > 65535) return CLAIRE_EINVAL;
   claire_ctx* c = new (std::nothrow) claire_ctx();
   if (!c) return CLAIRE_ENOMEM;
   c->o = o;

@@ -148,6 +148,252 @@ __global__ void __launch_bounds__(256) k_spec_reg_partial(const cplx<T>* __restr
   }
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// Fourier-domain PCG / Gauss-Newton vector kernels. The solver keeps v, g, r, s, vt as half spectra (3 components,
+// component stride Ns); beta A, M^-1 and K are then exact diagonal multiplies on these master copies, and inner
+// products follow from Parseval: <a, b> = h1 h2 h3 / N sum_k w(k3) Re(a^ conj b^), w = 1 on the k3 = 0 and
+// k3 = n3/2 planes and 2 elsewhere. Grid-stride over the half spectrum with 32-bit indices; FP64 partial sums,
+// one slot per block and value (partials[v * kReduceBlocks + block]).
+struct HWave {
+  int k1, k2, k3, p1, p2, p3;
+  double w;  // Parseval weight
+};
+
+__device__ __forceinline__ HWave hwave(unsigned j, const Dims& d) {
+  HWave h;
+  const unsigned n3h = (unsigned)d.n3h, n2 = (unsigned)d.n2;
+  const unsigned i3 = j % n3h;
+  const unsigned t = j / n3h;
+  const unsigned i2 = t % n2;
+  const unsigned i1 = t / n2;
+  h.k1 = (int)i1 <= d.n1 / 2 ? (int)i1 : (int)i1 - d.n1;
+  h.k2 = (int)i2 <= d.n2 / 2 ? (int)i2 : (int)i2 - d.n2;
+  h.k3 = (int)i3;
+  h.p1 = (2 * h.k1 == d.n1) ? 0 : h.k1;
+  h.p2 = (2 * h.k2 == d.n2) ? 0 : h.k2;
+  h.p3 = (2 * h.k3 == d.n3) ? 0 : h.k3;
+  h.w = (h.k3 == 0 || 2 * h.k3 == d.n3) ? 1.0 : 2.0;
+  return h;
+}
+
+template <class T> __device__ __forceinline__ T hsym(const HWave& h, int regnorm) {
+  const T ksq = T(h.k1) * T(h.k1) + T(h.k2) * T(h.k2) + T(h.k3) * T(h.k3);
+  return regnorm == 2 ? ksq * ksq : ksq;
+}
+
+template <class T> __device__ __forceinline__ void hleray(const HWave& h, cplx<T>& a, cplx<T>& b, cplx<T>& c) {
+  Wave w;
+  w.k1 = h.k1;
+  w.k2 = h.k2;
+  w.k3 = h.k3;
+  w.p1 = h.p1;
+  w.p2 = h.p2;
+  w.p3 = h.p3;
+  leray_apply<T>(w, a, b, c);
+}
+
+template <class T> __device__ __forceinline__ double cdot(cplx<T> a, cplx<T> b) {
+  return double(a.x) * double(b.x) + double(a.y) * double(b.y);
+}
+
+template <int V> __device__ __forceinline__ void block_reduce_v(double (&acc)[V], double* __restrict__ partials) {
+  __shared__ double red[V][32];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double a = acc[v];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < V) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
+    partials[threadIdx.x * kReduceBlocks + blockIdx.x] = t;
+  }
+}
+
+#define HLOOP for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < (unsigned)d.Ns; j += gridDim.x * blockDim.x)
+
+// G = beta a V + K B (V may be null: v = 0); partial ||G||^2
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ B,
+                                                 cplx<T>* __restrict__ G, int regnorm, int divfree, T beta, Dims d,
+                                                 double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[1] = {0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    cplx<T> b0 = B[j], b1 = B[s + j], b2 = B[2 * s + j];
+    if (divfree) hleray<T>(h, b0, b1, b2);
+    if (V) {
+      const T f = beta * hsym<T>(h, regnorm);
+      const cplx<T> v0 = V[j], v1 = V[s + j], v2 = V[2 * s + j];
+      b0 = mk<T>(fma(f, v0.x, b0.x), fma(f, v0.y, b0.y));
+      b1 = mk<T>(fma(f, v1.x, b1.x), fma(f, v1.y, b1.y));
+      b2 = mk<T>(fma(f, v2.x, b2.x), fma(f, v2.y, b2.y));
+    }
+    G[j] = b0;
+    G[s + j] = b1;
+    G[2 * s + j] = b2;
+    acc[0] += h.w * (cdot<T>(b0, b0) + cdot<T>(b1, b1) + cdot<T>(b2, b2));
+  }
+  block_reduce_v<1>(acc, partials);
+}
+
+// PCG start (Alg. 2): R = -G, S = Z = M^-1 R, Vt = 0; partials <R,Z>, ||R||^2, <S, beta A S>
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ R,
+                                                 cplx<T>* __restrict__ S, cplx<T>* __restrict__ Vt, int regnorm,
+                                                 T beta, Dims d, double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[3] = {0.0, 0.0, 0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    const T a = hsym<T>(h, regnorm);
+    const T ba = beta * a;
+    const T m = a > T(0) ? T(1) / ba : T(1);
+    double rr = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> g = G[c * s + j];
+      const cplx<T> r = mk<T>(-g.x, -g.y);
+      const cplx<T> z = mk<T>(m * r.x, m * r.y);
+      R[c * s + j] = r;
+      S[c * s + j] = z;
+      Vt[c * s + j] = mk<T>(T(0), T(0));
+      rr += cdot<T>(r, r);
+    }
+    acc[0] += h.w * double(m) * rr;
+    acc[1] += h.w * rr;
+    acc[2] += h.w * double(ba) * double(m) * double(m) * rr;
+  }
+  block_reduce_v<3>(acc, partials);
+}
+
+// PCG update: H S = beta a S + K Bt; R -= kappa H S; Vt += kappa S; partials ||R||^2, <R, M^-1 R>
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ Bt,
+                                                     cplx<T>* __restrict__ R, cplx<T>* __restrict__ Vt, T kappa,
+                                                     int regnorm, int divfree, T beta, Dims d,
+                                                     double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[2] = {0.0, 0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    const T a = hsym<T>(h, regnorm);
+    const T ba = beta * a;
+    const T m = a > T(0) ? T(1) / ba : T(1);
+    cplx<T> b0 = Bt[j], b1 = Bt[s + j], b2 = Bt[2 * s + j];
+    if (divfree) hleray<T>(h, b0, b1, b2);
+    const cplx<T> bb[3] = {b0, b1, b2};
+    double rr = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> sv = S[c * s + j];
+      const cplx<T> hs = mk<T>(fma(ba, sv.x, bb[c].x), fma(ba, sv.y, bb[c].y));
+      cplx<T> r = R[c * s + j];
+      r = mk<T>(fma(-kappa, hs.x, r.x), fma(-kappa, hs.y, r.y));
+      R[c * s + j] = r;
+      cplx<T> vt = Vt[c * s + j];
+      Vt[c * s + j] = mk<T>(fma(kappa, sv.x, vt.x), fma(kappa, sv.y, vt.y));
+      rr += cdot<T>(r, r);
+    }
+    acc[0] += h.w * rr;
+    acc[1] += h.w * double(m) * rr;
+  }
+  block_reduce_v<2>(acc, partials);
+}
+
+// PCG direction: S = M^-1 R + mu S; partial <S, beta A S>
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ S, T mu,
+                                                    int regnorm, T beta, Dims d, double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[1] = {0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    const T a = hsym<T>(h, regnorm);
+    const T ba = beta * a;
+    const T m = a > T(0) ? T(1) / ba : T(1);
+    double ss = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> r = R[c * s + j];
+      cplx<T> sv = S[c * s + j];
+      sv = mk<T>(fma(mu, sv.x, m * r.x), fma(mu, sv.y, m * r.y));
+      S[c * s + j] = sv;
+      ss += cdot<T>(sv, sv);
+    }
+    acc[0] += h.w * double(ba) * ss;
+  }
+  block_reduce_v<1>(acc, partials);
+}
+
+// optional projection Vt = K Vt (div v = 0), then partial <G, Vt>
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_project_dot(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Vt,
+                                                        int divfree, Dims d, double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[1] = {0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    cplx<T> v0 = Vt[j], v1 = Vt[s + j], v2 = Vt[2 * s + j];
+    if (divfree) {
+      hleray<T>(h, v0, v1, v2);
+      Vt[j] = v0;
+      Vt[s + j] = v1;
+      Vt[2 * s + j] = v2;
+    }
+    acc[0] += h.w * (cdot<T>(G[j], v0) + cdot<T>(G[s + j], v1) + cdot<T>(G[2 * s + j], v2));
+  }
+  block_reduce_v<1>(acc, partials);
+}
+
+// line-search trial: Vtr = V + alpha Vt (also copied to Sc, the work array of the inverse transform);
+// partial sum_k w a(k) |Vtr|^2 (the regularisation value)
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_trial(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ Vt,
+                                                  cplx<T>* __restrict__ Vtr, cplx<T>* __restrict__ Sc, T alpha,
+                                                  int regnorm, Dims d, double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[1] = {0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    double e = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> v = V[c * s + j], t = Vt[c * s + j];
+      const cplx<T> x = mk<T>(fma(alpha, t.x, v.x), fma(alpha, t.y, v.y));
+      Vtr[c * s + j] = x;
+      Sc[c * s + j] = x;
+      e += cdot<T>(x, x);
+    }
+    acc[0] += h.w * hsym<double>(h, regnorm) * e;
+  }
+  block_reduce_v<1>(acc, partials);
+}
+
+// partial sum_k w a(k) |V|^2 and a copy of V into Sc (used for a nonzero initial guess)
+template <class T>
+__global__ void __launch_bounds__(256) k_sp_copy_reg(const cplx<T>* __restrict__ V, cplx<T>* __restrict__ Sc,
+                                                     int regnorm, Dims d, double* __restrict__ partials) {
+  const long long s = d.Ns;
+  double acc[1] = {0.0};
+  HLOOP {
+    const HWave h = hwave(j, d);
+    double e = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> x = V[c * s + j];
+      if (Sc) Sc[c * s + j] = x;
+      e += cdot<T>(x, x);
+    }
+    acc[0] += h.w * hsym<double>(h, regnorm) * e;
+  }
+  block_reduce_v<1>(acc, partials);
+}
+#undef HLOOP
+
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 template <class T>
@@ -192,7 +438,72 @@ template <class T> claire_status spec_reg_partial(claire_ctx* c, const cplx<T>* 
   return CLAIRE_OK;
 }
 
+template <class T>
+claire_status sp_grad(claire_ctx* c, const cplx<T>* V, const cplx<T>* B, cplx<T>* G, double* partials,
+                      cudaStream_t st) {
+  c->prof_begin("sp_grad", st);
+  k_sp_grad<T><<<kReduceBlocks, 256, 0, st>>>(V, B, G, c->o.regnorm, c->o.divfree, T(c->o.beta), c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status sp_pcg0(claire_ctx* c, const cplx<T>* G, cplx<T>* R, cplx<T>* S, cplx<T>* Vt, double* partials,
+                      cudaStream_t st) {
+  c->prof_begin("sp_pcg0", st);
+  k_sp_pcg0<T><<<kReduceBlocks, 256, 0, st>>>(G, R, S, Vt, c->o.regnorm, T(c->o.beta), c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status sp_pcg_step(claire_ctx* c, const cplx<T>* S, const cplx<T>* Bt, cplx<T>* R, cplx<T>* Vt, double kappa,
+                          double* partials, cudaStream_t st) {
+  c->prof_begin("sp_pcg_step", st);
+  k_sp_pcg_step<T><<<kReduceBlocks, 256, 0, st>>>(S, Bt, R, Vt, T(kappa), c->o.regnorm, c->o.divfree, T(c->o.beta),
+                                                  c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cplx<T>* S, double mu, double* partials, cudaStream_t st) {
+  c->prof_begin("sp_pcg_dir", st);
+  k_sp_pcg_dir<T><<<kReduceBlocks, 256, 0, st>>>(R, S, T(mu), c->o.regnorm, T(c->o.beta), c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G, cplx<T>* Vt, double* partials, cudaStream_t st) {
+  c->prof_begin("sp_project_dot", st);
+  k_sp_project_dot<T><<<kReduceBlocks, 256, 0, st>>>(G, Vt, c->o.divfree, c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr, cplx<T>* Sc, double alpha,
+                       double* partials, cudaStream_t st) {
+  c->prof_begin("sp_trial", st);
+  k_sp_trial<T><<<kReduceBlocks, 256, 0, st>>>(V, Vt, Vtr, Sc, T(alpha), c->o.regnorm, c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* partials, cudaStream_t st) {
+  c->prof_begin("sp_copy_reg", st);
+  k_sp_copy_reg<T><<<kReduceBlocks, 256, 0, st>>>(V, Sc, c->o.regnorm, c->d, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+
 #define INST(T)                                                                                                   \
+  template claire_status sp_grad<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, double*, cudaStream_t); \
+  template claire_status sp_pcg0<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, double*,           \
+                                    cudaStream_t);                                                               \
+  template claire_status sp_pcg_step<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, double,  \
+                                        double*, cudaStream_t);                                                  \
+  template claire_status sp_pcg_dir<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double, double*, cudaStream_t);     \
+  template claire_status sp_project_dot<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double*, cudaStream_t);        \
+  template claire_status sp_trial<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, double,      \
+                                     double*, cudaStream_t);                                                     \
+  template claire_status sp_copy_reg<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double*, cudaStream_t);          \
   template claire_status spec_grad<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, cudaStream_t);  \
   template claire_status spec_div<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*,      \
                                      cudaStream_t);                                                              \
