@@ -22,22 +22,22 @@ __device__ __forceinline__ void block_partial(double acc, double* __restrict__ p
 template <class T>
 __global__ void __launch_bounds__(256) k_dot(const T* __restrict__ a, const T* __restrict__ b, long long n,
                                              double* __restrict__ partials) {
-  double acc = 0.0;
+  Acc<T> acc;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    acc += double(a[i]) * double(b[i]);
-  block_partial(acc, partials);
+    acc.add_prod(a[i], b[i]);
+  block_partial(acc.value(), partials);
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_diffsq(const T* __restrict__ a, const T* __restrict__ b, long long n,
                                                 double* __restrict__ partials) {
-  double acc = 0.0;
+  Acc<T> acc;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double e = double(a[i]) - double(b[i]);
-    acc += e * e;
+    const T e = a[i] - b[i];
+    acc.add_prod(e, e);
   }
-  block_partial(acc, partials);
+  block_partial(acc.value(), partials);
 }
 
 __global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partials, int np, double scale,

@@ -306,25 +306,25 @@ template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* ou
   const FFTPlan<T>& p = c->plan<T>();
   const Dims& d = c->d;
   const long long nlines = (long long)d.n1 * d.n2;
-  {
+  const long long inner1 = (long long)d.n2 * d.n3h;
+  c->prof_begin("fft_z_r2c", st);
+  if (!fft2_z<T>(d.n3 / 2, -1, in, out, nlines, p.tw3, T(1), st)) {
     const unsigned grid = (unsigned)((nlines + p.lpc3 - 1) / p.lpc3);
-    c->prof_begin("fft_z_r2c", st);
     k_fft_z_r2c<T><<<grid, 256, smem_z<T>(d.n3, p.lpc3), st>>>(in, out, nlines, d.n3, p.ax3, p.tw3, p.lpc3);
-    CL_LAUNCHED(c);
   }
-  {
+  CL_LAUNCHED(c);
+  c->prof_begin("fft_y_fwd", st);
+  if (!fft2_strided<T>(d.n2, -1, out, out, d.n3h, d.n1, p.tw2, st)) {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
-    c->prof_begin("fft_y_fwd", st);
     k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(out, out, d.n3h, p.ax2, p.tw2, p.ti12);
-    CL_LAUNCHED(c);
   }
-  {
-    const long long inner = (long long)d.n2 * d.n3h;
-    dim3 grid((unsigned)((inner + p.ti12 - 1) / p.ti12), 1u);
-    c->prof_begin("fft_x_fwd", st);
-    k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(out, out, inner, p.ax1, p.tw1, p.ti12);
-    CL_LAUNCHED(c);
+  CL_LAUNCHED(c);
+  c->prof_begin("fft_x_fwd", st);
+  if (!fft2_strided<T>(d.n1, -1, out, out, inner1, 1, p.tw1, st)) {
+    dim3 grid((unsigned)((inner1 + p.ti12 - 1) / p.ti12), 1u);
+    k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(out, out, inner1, p.ax1, p.tw1, p.ti12);
   }
+  CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 
@@ -332,27 +332,28 @@ template <class T>
 claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st, const cplx<T>* src) {
   const FFTPlan<T>& p = c->plan<T>();
   const Dims& d = c->d;
-  {
-    const long long inner = (long long)d.n2 * d.n3h;
-    dim3 grid((unsigned)((inner + p.ti12 - 1) / p.ti12), 1u);
-    c->prof_begin("fft_x_inv", st);
-    k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(src ? src : spec, spec, inner, p.ax1, p.tw1, p.ti12);
-    CL_LAUNCHED(c);
+  const long long nlines = (long long)d.n1 * d.n2;
+  const long long inner1 = (long long)d.n2 * d.n3h;
+  const cplx<T>* first = src ? src : spec;
+  c->prof_begin("fft_x_inv", st);
+  if (!fft2_strided<T>(d.n1, +1, first, spec, inner1, 1, p.tw1, st)) {
+    dim3 grid((unsigned)((inner1 + p.ti12 - 1) / p.ti12), 1u);
+    k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(first, spec, inner1, p.ax1, p.tw1, p.ti12);
   }
-  {
+  CL_LAUNCHED(c);
+  c->prof_begin("fft_y_inv", st);
+  if (!fft2_strided<T>(d.n2, +1, spec, spec, d.n3h, d.n1, p.tw2, st)) {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
-    c->prof_begin("fft_y_inv", st);
     k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(spec, spec, d.n3h, p.ax2, p.tw2, p.ti12);
-    CL_LAUNCHED(c);
   }
-  {
-    const long long nlines = (long long)d.n1 * d.n2;
+  CL_LAUNCHED(c);
+  c->prof_begin("fft_z_c2r", st);
+  if (!fft2_z<T>(d.n3 / 2, +1, spec, out, nlines, p.tw3, scale, st)) {
     const unsigned grid = (unsigned)((nlines + p.lpc3 - 1) / p.lpc3);
-    c->prof_begin("fft_z_c2r", st);
     k_fft_z_c2r<T><<<grid, 256, smem_z<T>(d.n3, p.lpc3), st>>>(spec, out, nlines, d.n3, p.ax3, p.tw3, p.lpc3,
                                                                 scale);
-    CL_LAUNCHED(c);
   }
+  CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 

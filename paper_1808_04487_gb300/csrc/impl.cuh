@@ -130,6 +130,12 @@ template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* ou
 template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_t st,
                                          const cplx<T>* src = nullptr);
 
+// ---- fft2.cu: length-specialised passes (false: no specialisation for L) ----
+template <class T> bool fft2_strided(int L, int sign, const cplx<T>* src, cplx<T>* dst, long long inner, int outer,
+                                     const cplx<T>* W, cudaStream_t st);
+template <class T> bool fft2_z(int L, int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3,
+                               T scale, cudaStream_t st);
+
 // ---- spectral.cu ----------------------------------------------------------------------------------------------
 template <class T> claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G1, cplx<T>* G2,
                                            cudaStream_t st);

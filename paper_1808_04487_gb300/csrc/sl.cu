@@ -10,8 +10,9 @@
 
 namespace claire {
 
-// Per-axis part of a stencil: the four cubic Lagrange weights and the unwrapped index of the first node, b - 1.
-template <class T> __device__ __forceinline__ int axis_setup(int i, T disp, T* w) {
+// Per-axis part of a stencil: the four cubic Lagrange weights and the first stencil node b - 1, reduced into
+// [0, n) by a periodic shift when it lies outside [-n, n) (only for displacements beyond one period).
+template <class T> __device__ __forceinline__ int axis_setup(int i, T disp, int n, T* w) {
   const T fd = floor(disp);
   const T t = disp - fd;
   const T tp1 = t + T(1), tm1 = t - T(1), tm2 = t - T(2);
@@ -19,27 +20,35 @@ template <class T> __device__ __forceinline__ int axis_setup(int i, T disp, T* w
   w[1] = (tp1 * tm1 * tm2) * T(0.5);
   w[2] = -(tp1 * t * tm2) * T(0.5);
   w[3] = (tp1 * t * tm1) * T(1.0 / 6.0);
-  return i + (int)fd - 1;
+  int b = i + (int)fd - 1;
+  if (b < -n || b >= n) {
+    b %= n;
+    if (b < 0) b += n;
+  }
+  return b;
 }
 
-__device__ __forceinline__ int wrap(int q, int n) {
-  q %= n;
-  return q < 0 ? q + n : q;
+// q in [-n, 2n) -> [0, n)
+__device__ __forceinline__ int wrapc(int q, int n) {
+  q = q < 0 ? q + n : q;
+  return q >= n ? q - n : q;
 }
 
 template <class T> struct Stencil {
   T w1[4], w2[4], w3[4];
-  int b1, b2, b3;  // unwrapped first stencil node per axis
-  bool inside;     // all 4 x 4 x 4 nodes inside the box: no periodic wrap needed
+  int b1, b2, b3;  // first stencil node per axis, in [-n, n)
+  bool inside;     // the whole warp's stencils lie inside the box: no periodic wrap needed
 };
 
 template <class T>
 __device__ __forceinline__ void stencil_at(int i1, int i2, int i3, T d1, T d2, T d3, const Dims& d, Stencil<T>& s) {
-  s.b1 = axis_setup<T>(i1, d1, s.w1);
-  s.b2 = axis_setup<T>(i2, d2, s.w2);
-  s.b3 = axis_setup<T>(i3, d3, s.w3);
-  s.inside = (unsigned)s.b1 <= (unsigned)(d.n1 - 4) && (unsigned)s.b2 <= (unsigned)(d.n2 - 4) &&
-             (unsigned)s.b3 <= (unsigned)(d.n3 - 4);
+  s.b1 = axis_setup<T>(i1, d1, d.n1, s.w1);
+  s.b2 = axis_setup<T>(i2, d2, d.n2, s.w2);
+  s.b3 = axis_setup<T>(i3, d3, d.n3, s.w3);
+  const bool in = (unsigned)s.b1 <= (unsigned)(d.n1 - 4) && (unsigned)s.b2 <= (unsigned)(d.n2 - 4) &&
+                  (unsigned)s.b3 <= (unsigned)(d.n3 - 4);
+  // one path per warp: a warp with any wrapping lane takes the wrapping path for all its lanes
+  s.inside = __all_sync(__activemask(), in);
 }
 
 // sum_{p,q,r} w1[p] w2[q] w3[r] f[row(p,q) + col(r)], evaluated as 16 four-tap sums along i3, then i2, then i1.
@@ -67,9 +76,9 @@ template <class T> __device__ __forceinline__ T gather(const T* __restrict__ f, 
     int o1[4], o2[4], o3[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      o1[p] = wrap(s.b1 + p, d.n1) * s1;
-      o2[p] = wrap(s.b2 + p, d.n2) * s2;
-      o3[p] = wrap(s.b3 + p, d.n3);
+      o1[p] = wrapc(s.b1 + p, d.n1) * s1;
+      o2[p] = wrapc(s.b2 + p, d.n2) * s2;
+      o3[p] = wrapc(s.b3 + p, d.n3);
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const T* __restrict__ lam_next
                                                   const T* __restrict__ gm, T w, T dt, Dims d,
                                                   const T* __restrict__ sv, double* __restrict__ part) {
   const Node x = node3d(d);
-  double contrib = 0.0;
+  Acc<T> contrib;
   if (x.valid) {
     const int idx = x.idx;
     const long long N = d.N;
@@ -191,14 +200,19 @@ __global__ void __launch_bounds__(256) k_adj_step(const T* __restrict__ lam_next
       b[N + idx] = b1;
       b[2 * N + idx] = b2;
       // <s, b>: the final time integral against a vector s, for PCG's <s, H s> (Alg. 2)
-      if (DOT) contrib = double(sv[idx]) * b0 + double(sv[N + idx]) * b1 + double(sv[2 * N + idx]) * b2;
+      if (DOT) {
+        contrib.add_prod(sv[idx], b0);
+        contrib.add_prod(sv[N + idx], b1);
+        contrib.add_prod(sv[2 * N + idx], b2);
+      }
     }
   }
   if (DOT) {
     __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
+    double cs = contrib.value();
+    for (int o = 16; o > 0; o >>= 1) cs += __shfl_down_sync(0xffffffffu, cs, o);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if ((tid & 31) == 0) red[tid >> 5] = contrib;
+    if ((tid & 31) == 0) red[tid >> 5] = cs;
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;

@@ -798,6 +798,8 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   c->d.n3h = o.n[2] / 2 + 1;
   c->d.N = N;
   c->d.Ns = (long long)o.n[0] * o.n[1] * c->d.n3h;
+  c->d.by_n3h = FastDiv((unsigned)c->d.n3h);
+  c->d.by_n2 = FastDiv((unsigned)o.n[1]);
   RadixPlan tmp;
   if (!radix_plan(o.n[0], tmp) || !radix_plan(o.n[1], tmp) || !radix_plan(o.n[2] / 2, tmp)) {
     delete c;

@@ -14,13 +14,14 @@ struct Wave {
 
 __device__ __forceinline__ Wave wavenumbers(long long idx, const Dims& d) {
   Wave w;
-  const int i3 = (int)(idx % d.n3h);
-  const long long t = idx / d.n3h;
-  const int i2 = (int)(t % d.n2);
-  const int i1 = (int)(t / d.n2);
-  w.k1 = i1 <= d.n1 / 2 ? i1 : i1 - d.n1;
-  w.k2 = i2 <= d.n2 / 2 ? i2 : i2 - d.n2;
-  w.k3 = i3;
+  const unsigned j = (unsigned)idx;
+  const unsigned t = d.by_n3h.div(j);
+  const unsigned i3 = j - t * (unsigned)d.n3h;
+  const unsigned i1 = d.by_n2.div(t);
+  const unsigned i2 = t - i1 * (unsigned)d.n2;
+  w.k1 = (int)i1 <= d.n1 / 2 ? (int)i1 : (int)i1 - d.n1;
+  w.k2 = (int)i2 <= d.n2 / 2 ? (int)i2 : (int)i2 - d.n2;
+  w.k3 = (int)i3;
   w.p1 = (2 * w.k1 == d.n1) ? 0 : w.k1;
   w.p2 = (2 * w.k2 == d.n2) ? 0 : w.k2;
   w.p3 = (2 * w.k3 == d.n3) ? 0 : w.k3;
@@ -123,23 +124,21 @@ __global__ void k_spec_combine(const cplx<T>* __restrict__ V, cplx<T>* __restric
 template <class T>
 __global__ void __launch_bounds__(256) k_spec_reg_partial(const cplx<T>* __restrict__ V, int regnorm, Dims d,
                                                           double* __restrict__ partials) {
-  double acc = 0.0;
+  Acc<T> acc;
   const long long s = d.Ns;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < s;
        idx += (long long)gridDim.x * blockDim.x) {
     const Wave w = wavenumbers(idx, d);
-    const double a = reg_symbol<double>(w, regnorm);
-    const double wt = (w.k3 == 0 || 2 * w.k3 == d.n3) ? 1.0 : 2.0;
-    double e = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      const cplx<T> x = V[c * s + idx];
-      e += double(x.x) * double(x.x) + double(x.y) * double(x.y);
-    }
-    acc += wt * a * e;
+    const T a = reg_symbol<T>(w, regnorm);
+    const T wt = (w.k3 == 0 || 2 * w.k3 == d.n3) ? T(1) : T(2);
+    T e = T(0);
+    for (int c = 0; c < 3; ++c) e += V[c * s + idx].x * V[c * s + idx].x + V[c * s + idx].y * V[c * s + idx].y;
+    acc.add(wt * a * e);
   }
   __shared__ double red[256 / 32];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  double t0 = acc.value();
+  for (int o = 16; o > 0; o >>= 1) t0 += __shfl_down_sync(0xffffffffu, t0, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t0;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -161,11 +160,10 @@ struct HWave {
 
 __device__ __forceinline__ HWave hwave(unsigned j, const Dims& d) {
   HWave h;
-  const unsigned n3h = (unsigned)d.n3h, n2 = (unsigned)d.n2;
-  const unsigned i3 = j % n3h;
-  const unsigned t = j / n3h;
-  const unsigned i2 = t % n2;
-  const unsigned i1 = t / n2;
+  const unsigned t = d.by_n3h.div(j);
+  const unsigned i3 = j - t * (unsigned)d.n3h;
+  const unsigned i1 = d.by_n2.div(t);
+  const unsigned i2 = t - i1 * (unsigned)d.n2;
   h.k1 = (int)i1 <= d.n1 / 2 ? (int)i1 : (int)i1 - d.n1;
   h.k2 = (int)i2 <= d.n2 / 2 ? (int)i2 : (int)i2 - d.n2;
   h.k3 = (int)i3;
@@ -192,15 +190,19 @@ template <class T> __device__ __forceinline__ void hleray(const HWave& h, cplx<T
   leray_apply<T>(w, a, b, c);
 }
 
-template <class T> __device__ __forceinline__ double cdot(cplx<T> a, cplx<T> b) {
-  return double(a.x) * double(b.x) + double(a.y) * double(b.y);
-}
+template <class T> __device__ __forceinline__ T csq(cplx<T> a) { return a.x * a.x + a.y * a.y; }
+template <class T> __device__ __forceinline__ T cre(cplx<T> a, cplx<T> b) { return a.x * b.x + a.y * b.y; }
 
-template <int V> __device__ __forceinline__ void block_reduce_v(double (&acc)[V], double* __restrict__ partials) {
+// M^-1 symbol 1/(beta a) (1 where a = 0); FP32 uses the correctly rounded reciprocal intrinsic
+__device__ __forceinline__ float precond_sym(float ba, float a) { return a > 0.f ? __frcp_rn(ba) : 1.f; }
+__device__ __forceinline__ double precond_sym(double ba, double a) { return a > 0.0 ? 1.0 / ba : 1.0; }
+
+template <class T, int V>
+__device__ __forceinline__ void block_reduce_v(const Acc<T> (&accs)[V], double* __restrict__ partials) {
   __shared__ double red[V][32];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    double a = acc[v];
+    double a = accs[v].value();
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = a;
   }
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, 
                                                  cplx<T>* __restrict__ G, int regnorm, int divfree, T beta, Dims d,
                                                  double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[1] = {0.0};
+  Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
     cplx<T> b0 = B[j], b1 = B[s + j], b2 = B[2 * s + j];
@@ -235,9 +237,9 @@ __global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, 
     G[j] = b0;
     G[s + j] = b1;
     G[2 * s + j] = b2;
-    acc[0] += h.w * (cdot<T>(b0, b0) + cdot<T>(b1, b1) + cdot<T>(b2, b2));
+    acc[0].add(T(h.w) * (csq<T>(b0) + csq<T>(b1) + csq<T>(b2)));
   }
-  block_reduce_v<1>(acc, partials);
+  block_reduce_v<T, 1>(acc, partials);
 }
 
 // PCG start (Alg. 2): R = -G, S = Z = M^-1 R, Vt = 0; partials <R,Z>, ||R||^2, <S, beta A S>
@@ -246,13 +248,13 @@ __global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, 
                                                  cplx<T>* __restrict__ S, cplx<T>* __restrict__ Vt, int regnorm,
                                                  T beta, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[3] = {0.0, 0.0, 0.0};
+  Acc<T> acc[3];
   HLOOP {
     const HWave h = hwave(j, d);
     const T a = hsym<T>(h, regnorm);
     const T ba = beta * a;
-    const T m = a > T(0) ? T(1) / ba : T(1);
-    double rr = 0.0;
+    const T m = precond_sym(ba, a);
+    T rr = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> g = G[c * s + j];
@@ -261,13 +263,14 @@ __global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, 
       R[c * s + j] = r;
       S[c * s + j] = z;
       Vt[c * s + j] = mk<T>(T(0), T(0));
-      rr += cdot<T>(r, r);
+      rr += csq<T>(r);
     }
-    acc[0] += h.w * double(m) * rr;
-    acc[1] += h.w * rr;
-    acc[2] += h.w * double(ba) * double(m) * double(m) * rr;
+    const T wrr = T(h.w) * rr;
+    acc[0].add(m * wrr);
+    acc[1].add(wrr);
+    acc[2].add(ba * m * m * wrr);
   }
-  block_reduce_v<3>(acc, partials);
+  block_reduce_v<T, 3>(acc, partials);
 }
 
 // PCG update: H S = beta a S + K Bt; R -= kappa H S; Vt += kappa S; partials ||R||^2, <R, M^-1 R>
@@ -277,16 +280,16 @@ __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__
                                                      int regnorm, int divfree, T beta, Dims d,
                                                      double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[2] = {0.0, 0.0};
+  Acc<T> acc[2];
   HLOOP {
     const HWave h = hwave(j, d);
     const T a = hsym<T>(h, regnorm);
     const T ba = beta * a;
-    const T m = a > T(0) ? T(1) / ba : T(1);
+    const T m = precond_sym(ba, a);
     cplx<T> b0 = Bt[j], b1 = Bt[s + j], b2 = Bt[2 * s + j];
     if (divfree) hleray<T>(h, b0, b1, b2);
     const cplx<T> bb[3] = {b0, b1, b2};
-    double rr = 0.0;
+    T rr = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> sv = S[c * s + j];
@@ -296,12 +299,13 @@ __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__
       R[c * s + j] = r;
       cplx<T> vt = Vt[c * s + j];
       Vt[c * s + j] = mk<T>(fma(kappa, sv.x, vt.x), fma(kappa, sv.y, vt.y));
-      rr += cdot<T>(r, r);
+      rr += csq<T>(r);
     }
-    acc[0] += h.w * rr;
-    acc[1] += h.w * double(m) * rr;
+    const T wrr = T(h.w) * rr;
+    acc[0].add(wrr);
+    acc[1].add(m * wrr);
   }
-  block_reduce_v<2>(acc, partials);
+  block_reduce_v<T, 2>(acc, partials);
 }
 
 // PCG direction: S = M^-1 R + mu S; partial <S, beta A S>
@@ -309,24 +313,24 @@ template <class T>
 __global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ S, T mu,
                                                     int regnorm, T beta, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[1] = {0.0};
+  Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
     const T a = hsym<T>(h, regnorm);
     const T ba = beta * a;
-    const T m = a > T(0) ? T(1) / ba : T(1);
-    double ss = 0.0;
+    const T m = precond_sym(ba, a);
+    T ss = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> r = R[c * s + j];
       cplx<T> sv = S[c * s + j];
       sv = mk<T>(fma(mu, sv.x, m * r.x), fma(mu, sv.y, m * r.y));
       S[c * s + j] = sv;
-      ss += cdot<T>(sv, sv);
+      ss += csq<T>(sv);
     }
-    acc[0] += h.w * double(ba) * ss;
+    acc[0].add(T(h.w) * ba * ss);
   }
-  block_reduce_v<1>(acc, partials);
+  block_reduce_v<T, 1>(acc, partials);
 }
 
 // optional projection Vt = K Vt (div v = 0), then partial <G, Vt>
@@ -334,7 +338,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_sp_project_dot(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Vt,
                                                         int divfree, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[1] = {0.0};
+  Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
     cplx<T> v0 = Vt[j], v1 = Vt[s + j], v2 = Vt[2 * s + j];
@@ -344,9 +348,9 @@ __global__ void __launch_bounds__(256) k_sp_project_dot(const cplx<T>* __restric
       Vt[s + j] = v1;
       Vt[2 * s + j] = v2;
     }
-    acc[0] += h.w * (cdot<T>(G[j], v0) + cdot<T>(G[s + j], v1) + cdot<T>(G[2 * s + j], v2));
+    acc[0].add(T(h.w) * (cre<T>(G[j], v0) + cre<T>(G[s + j], v1) + cre<T>(G[2 * s + j], v2)));
   }
-  block_reduce_v<1>(acc, partials);
+  block_reduce_v<T, 1>(acc, partials);
 }
 
 // line-search trial: Vtr = V + alpha Vt (also copied to Sc, the work array of the inverse transform);
@@ -356,21 +360,21 @@ __global__ void __launch_bounds__(256) k_sp_trial(const cplx<T>* __restrict__ V,
                                                   cplx<T>* __restrict__ Vtr, cplx<T>* __restrict__ Sc, T alpha,
                                                   int regnorm, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[1] = {0.0};
+  Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
-    double e = 0.0;
+    T e = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> v = V[c * s + j], t = Vt[c * s + j];
       const cplx<T> x = mk<T>(fma(alpha, t.x, v.x), fma(alpha, t.y, v.y));
       Vtr[c * s + j] = x;
       Sc[c * s + j] = x;
-      e += cdot<T>(x, x);
+      e += csq<T>(x);
     }
-    acc[0] += h.w * hsym<double>(h, regnorm) * e;
+    acc[0].add(T(h.w) * hsym<T>(h, regnorm) * e);
   }
-  block_reduce_v<1>(acc, partials);
+  block_reduce_v<T, 1>(acc, partials);
 }
 
 // partial sum_k w a(k) |V|^2 and a copy of V into Sc (used for a nonzero initial guess)
@@ -378,19 +382,19 @@ template <class T>
 __global__ void __launch_bounds__(256) k_sp_copy_reg(const cplx<T>* __restrict__ V, cplx<T>* __restrict__ Sc,
                                                      int regnorm, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
-  double acc[1] = {0.0};
+  Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
-    double e = 0.0;
+    T e = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> x = V[c * s + j];
       if (Sc) Sc[c * s + j] = x;
-      e += cdot<T>(x, x);
+      e += csq<T>(x);
     }
-    acc[0] += h.w * hsym<double>(h, regnorm) * e;
+    acc[0].add(T(h.w) * hsym<T>(h, regnorm) * e);
   }
-  block_reduce_v<1>(acc, partials);
+  block_reduce_v<T, 1>(acc, partials);
 }
 #undef HLOOP
 

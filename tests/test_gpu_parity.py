@@ -78,6 +78,20 @@ def test_fft_forward_and_inverse(n, prec):
         assert rel(c.ifft(st), g) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(64, 96, 128), (112, 48, 160), (144, 160, 112), (192, 256, 144), (256, 32, 256),
+                               (96, 112, 96), (160, 192, 144)])
+def test_fft_length_specialised_passes(n, prec):
+    """Every length with a compile-time specialised pass (the population grids 64..256) against numpy."""
+    f = np.random.default_rng(11).normal(size=n)
+    with ctx(n, prec) as c:
+        spec = c.fft(dev(f, prec))
+        ref = np.fft.rfftn(f)
+        got = spec[..., 0].cpu().double().numpy() + 1j * spec[..., 1].cpu().double().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < TOL[prec]
+        assert rel(c.ifft(spec), f) < TOL[prec]
+
+
 # ------------------------------------------------------------------------------------------------------ spectral ops
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("n", [(16, 16, 16), (12, 16, 20), (40, 36, 42)])
