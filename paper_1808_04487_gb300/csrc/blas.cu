@@ -56,6 +56,38 @@ __global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict_
 }
 
 template <class T>
+__global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ a, long long n, double* __restrict__ partials) {
+  T m = T(0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(a[i]));
+  __shared__ double red[32];
+  double v = double(m);
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, red[i]);
+    partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_max_final(const double* __restrict__ partials, int np,
+                                                    double* __restrict__ out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) v = fmax(v, partials[i]);
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, red[i]);
+    *out = t;
+  }
+}
+
+template <class T>
 __global__ void k_axpy(long long n, T a, const T* __restrict__ x, T* __restrict__ y) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = fma(a, x[i], y[i]);
@@ -124,6 +156,20 @@ claire_status reduce_final(claire_ctx* c, const double* partials, double scale, 
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
+template <class T>
+claire_status absmax_partial(claire_ctx* c, const T* a, long long n, double* partials, cudaStream_t st) {
+  c->prof_begin("absmax", st);
+  k_absmax<T><<<kReduceBlocks, 256, 0, st>>>(a, n, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+claire_status max_final(claire_ctx* c, const double* partials, int np, double* out, cudaStream_t st) {
+  c->prof_begin("max_final", st);
+  k_max_final<<<1, 1024, 0, st>>>(partials, np, out);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+
 template <class T> claire_status axpy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st) {
   c->prof_begin("axpy", st);
   k_axpy<T><<<stream_blocks(n), kThreads, 0, st>>>(n, T(a), x, y);
@@ -182,6 +228,7 @@ static double* noalloc_scratch_on_current_device(claire_status* st) {
 }
 
 #define INST(T)                                                                                                   \
+  template claire_status absmax_partial<T>(claire_ctx*, const T*, long long, double*, cudaStream_t);              \
   template claire_status dot_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);       \
   template claire_status diffsq_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);    \
   template claire_status axpy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);                     \

@@ -69,6 +69,8 @@ struct claire_ctx {
   claire::Work<float> wf{};
   claire::Work<double> wd{};
   bool lin_valid = false;
+  int haloX = -1, haloY = -1;  // brick halo of the cached departure points (-1: unknown, plain gathers)
+  long long dot_blocks = 0;    // partials written by the last dot-fused adjoint step
   double* hscal = nullptr;  // pinned host mirror of Work::scal
   // optional per-launch CUDA-event timing (off by default): one event pair per kernel launch, summed per name
   struct ProfRec {
@@ -169,7 +171,10 @@ template <class T> claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cp
 // ---- sl.cu ----------------------------------------------------------------------------------------------------
 template <class T> claire_status sl_hadamard(claire_ctx* c, const T* a, const T* x, T* y, cudaStream_t st);
 template <class T> claire_status sl_departure(claire_ctx* c, const T* v, int dir, T* disp, cudaStream_t st);
-template <class T> claire_status sl_interp(claire_ctx* c, const T* f, const T* disp, T* out, cudaStream_t st);
+// H >= 0: brick-tiled gathers for displacements bounded by H - 1 voxels; H < 0: plain global gathers
+template <class T> claire_status sl_init(claire_ctx* c);
+template <class T> claire_status sl_interp(claire_ctx* c, const T* f, const T* disp, T* out, cudaStream_t st,
+                                           int H = -1);
 // lam = mR - m1; optionally rl = rho*lam; b = w * lam * gm  (terminal condition of the adjoint, Eq. (4))
 template <class T> claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR, const T* m1, const T* rho, T* lam,
                                                      T* rl, T* b, const T* gmj, T w, cudaStream_t st);
@@ -178,7 +183,8 @@ template <class T> claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR,
 // with sdot (and lam == null, b != null): also part[block] = partial <sdot, b_final>, one slot per block of launch3
 template <class T> claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next, const T* rho,
                                                  const T* dY, T* lam, T* rl, T* b, const T* gmj, T w,
-                                                 cudaStream_t st, const T* sdot = nullptr, double* part = nullptr);
+                                                 cudaStream_t st, const T* sdot = nullptr, double* part = nullptr,
+                                                 int H = -1);
 // launch shape of the gather kernels: 256 threads, x along i3 (up to 64 wide), y along i2, z = i1
 struct Launch3 {
   dim3 grid, block;
@@ -189,12 +195,17 @@ template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, co
 // m~^{j+1} = q^j(X) + dt/2 f^{j+1}; writes q^{j+1}, or on the last step lam~ = -m~, rho*lam~, b = w lam~ grad m
 template <class T> claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* vt, const T* gmj1,
                                                   T* qout, bool last, const T* rho, T* rl, T* b, T w,
-                                                  cudaStream_t st);
+                                                  cudaStream_t st, int H = -1);
 
 // ---- blas.cu --------------------------------------------------------------------------------------------------
 // partials[kReduceBlocks] of sum a*b (FP64 accumulation); a == b allowed
 template <class T> claire_status dot_partial(claire_ctx* c, const T* a, const T* b, long long n, double* partials,
                                              cudaStream_t st);
+// partials[kReduceBlocks] of max |a_i| (as double)
+template <class T> claire_status absmax_partial(claire_ctx* c, const T* a, long long n, double* partials,
+                                                cudaStream_t st);
+// out = max(partials[0..np))
+claire_status max_final(claire_ctx* c, const double* partials, int np, double* out, cudaStream_t st);
 // partials of sum (a - b)^2
 template <class T> claire_status diffsq_partial(claire_ctx* c, const T* a, const T* b, long long n, double* partials,
                                                 cudaStream_t st);

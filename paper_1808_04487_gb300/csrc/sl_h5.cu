@@ -1,0 +1,6 @@
+// Brick-tiled FP32 semi-Lagrangian launchers for halo 5 (see sl_kernels.cuh).
+#include "sl_kernels.cuh"
+
+namespace claire {
+CLAIRE_SL_LAUNCHERS(, float, 5)
+}  // namespace claire

@@ -161,13 +161,24 @@ template <class T> claire_status spectral_tail(claire_ctx* c, const T* v, const 
   return vec_c2r<T>(c, B, out, st);
 }
 
+// Brick halo for the tiled gathers: max |displacement| D in voxels over the field -> H = ceil(D) + 1
+template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* halo, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  CL_TRY(absmax_partial<T>(c, disp, 3 * c->d.N, W.partials, st));
+  CL_TRY(max_final(c, W.partials, kReduceBlocks, W.scal + 12, st));
+  double D;
+  CL_TRY(read_scalar(c, W.scal + 12, &D, st));
+  *halo = (std::isfinite(D) && D < 64.0) ? (int)std::ceil(D + 1e-3) + 1 : -1;
+  return CLAIRE_OK;
+}
+
 // ---------------------------------------------------------------------------------------------------------------
 // state solve along X into the history W.m (m^0 = mT)
 template <class T> claire_status state_history(claire_ctx* c, const T* mT, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
   if (W.m != mT) CL_CUDA(c, cudaMemcpyAsync(W.m, mT, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
-  for (int j = 0; j < c->o.nt; ++j) CL_TRY(sl_interp<T>(c, W.m + j * N, W.dX, W.m + (j + 1) * N, st));
+  for (int j = 0; j < c->o.nt; ++j) CL_TRY(sl_interp<T>(c, W.m + j * N, W.dX, W.m + (j + 1) * N, st, c->haloX));
   return CLAIRE_OK;
 }
 
@@ -176,6 +187,7 @@ template <class T> claire_status finish_linearization(claire_ctx* c, const T* v,
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
   CL_TRY(sl_departure<T>(c, v, -1, W.dY, st));
+  CL_TRY(update_halo<T>(c, W.dY, &c->haloY, st));
   for (int j = 0; j <= c->o.nt; ++j) CL_TRY(grad_spectral<T>(c, W.m + j * N, W.gm + 3LL * j * N, st));
   if (!c->o.divfree) CL_TRY(div_spectral<T>(c, v, W.rho, st));
   c->lin_valid = true;
@@ -186,6 +198,7 @@ template <class T> claire_status linearize(claire_ctx* c, const T* mT, const T* 
   Work<T>& W = c->work<T>();
   c->lin_valid = false;
   CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+  CL_TRY(update_halo<T>(c, W.dX, &c->haloX, st));
   CL_TRY(state_history<T>(c, mT, st));
   return finish_linearization<T>(c, v, st);
 }
@@ -206,7 +219,8 @@ template <class T> claire_status adjoint_integral(claire_ctx* c, const T* mR, cu
   for (int j = nt - 1; j >= 0; --j) {
     const bool store = j > 0;
     CL_TRY(sl_adjoint_step<T>(c, lam[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? lam[1 - cur] : nullptr,
-                              (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)), st));
+                              (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)), st,
+                              nullptr, nullptr, c->haloY));
     cur = 1 - cur;
   }
   return CLAIRE_OK;
@@ -256,14 +270,15 @@ template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStrea
   for (int j = 0; j < nt; ++j) {
     const bool last = j == nt - 1;
     CL_TRY(sl_incstate_step<T>(c, buf[cur], W.dX, vt, W.gm + 3LL * (j + 1) * N, buf[1 - cur], last, rho,
-                               rl[1 - cur], W.b, T(tweight(nt, nt)), st));
+                               rl[1 - cur], W.b, T(tweight(nt, nt)), st, c->haloX));
     cur = 1 - cur;
   }
   for (int j = nt - 1; j >= 0; --j) {
     const bool store = j > 0;
     CL_TRY(sl_adjoint_step<T>(c, buf[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? buf[1 - cur] : nullptr,
                               (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)),
-                              st, (dot && j == 0) ? vt : nullptr, (dot && j == 0) ? W.bigpart : nullptr));
+                              st, (dot && j == 0) ? vt : nullptr, (dot && j == 0) ? W.bigpart : nullptr,
+                              c->haloY));
     cur = 1 - cur;
   }
   return CLAIRE_OK;
@@ -283,6 +298,7 @@ template <class T> claire_status state_mismatch(claire_ctx* c, const T* mT, cons
   const long long N = c->d.N;
   c->lin_valid = false;
   CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+  CL_TRY(update_halo<T>(c, W.dX, &c->haloX, st));
   CL_TRY(state_history<T>(c, mT, st));
   CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
   return reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal + slot, st);
@@ -336,7 +352,7 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
   CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
   for (int it = 0; it < c->o.max_krylov; ++it) {
     CL_TRY(hess_data<T>(c, W.s, st, true));
-    CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)W.nbig, cellvol(c->d), W.scal + 4, st));
+    CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)c->dot_blocks, cellvol(c->d), W.scal + 4, st));
     CL_TRY(vec_r2c<T>(c, W.b, W.Bh, st));
     rep->matvecs++;
     rep->pde_solves += 2;
@@ -465,6 +481,7 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
       if (!accepted) {
         status = CLAIRE_ELINESEARCH;
         CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
+        CL_TRY(update_halo<T>(c, W.dX, &c->haloX, st));
         CL_TRY(state_history<T>(c, mT, st));
         break;
       }
@@ -506,6 +523,7 @@ template <class T> claire_status transport_dev(claire_ctx* c, const T* m0, const
   const long long N = c->d.N;
   const int nt = c->o.nt;
   c->lin_valid = false;
+  c->haloX = c->haloY = -1;
   T* buf[2] = {W.la, W.lb};
   if (dir > 0) {
     CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
@@ -819,6 +837,7 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
     return CLAIRE_ENOMEM;
   }
   claire_status s = o.precision == CLAIRE_F32 ? fft_init<float>(c) : fft_init<double>(c);
+  if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? sl_init<float>(c) : sl_init<double>(c);
   if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? alloc_work<float>(c) : alloc_work<double>(c);
   if (s != CLAIRE_OK) {
     cudaFreeHost(c->hscal);
