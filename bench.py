@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--study", default=None, choices=[None, "precision"],
+                    help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path (own JSON line)")
     return ap.parse_args()
 
 
@@ -229,8 +231,94 @@ def run_reference(args, rank, world):
     return 0
 
 
+def precision_study(args):
+    """Per-operator errors (transport, reduced gradient, GN matvec data term) of the FP32 path and of the FP32 path
+    with a BF16 gradient history, against the FP64 path of this library (itself held to 1e-12 of the FP64 oracle by
+    the parity tests), plus matvecs/s and full solves (time, GN/PCG counts, final mismatch) for all three."""
+    import numpy as np
+    import torch
+
+    import paper_1808_04487_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    n = (args.size,) * 3
+    mT_np, vstar_np = make_inputs(n)
+    dev = torch.device("cuda", 0)
+    res = {}
+    ctx64 = pkg.Context(n, precision="f64", **SOLVER_KW)
+    mT64 = torch.from_numpy(mT_np).to(dev)
+    vs64 = torch.from_numpy(vstar_np).to(dev)
+    mR64 = ctx64.transport(mT64, vs64, +1)
+    # operators at v = v*/2 (a generic linearisation point) with a div-free direction
+    g = torch.Generator(dev).manual_seed(5)
+    vt64 = ctx64.spectral("leray", torch.randn((3,) + n, dtype=torch.float64, device=dev, generator=g))
+    v64 = 0.5 * vs64
+    ref = {"transport": ctx64.transport(mT64, v64, +1)}
+    ctx64.linearize(mT64, v64)
+    ref["hessvec_data"] = ctx64.hessvec_data(vt64)
+    ref["gradient"] = ctx64.gradient(mT64, mR64, v64)
+    # data term K[int lambda grad m dt] of the gradient: the part the solver's Fourier-domain gradient inherits from
+    # the physical-space solves (its beta A v is exact on the master spectrum)
+    ref["gradient_data"] = ref["gradient"] - ctx64.spectral("A", v64) * SOLVER_KW["beta"]
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a.double() - b) / torch.linalg.vector_norm(b))
+
+    def timed_register(ctx, mT, mR, dtype):
+        v = torch.zeros((3,) + n, dtype=dtype, device=dev)
+        ctx.register(mT, mR, v)  # warm-up
+        v.zero_()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        v, rep, status = ctx.register(mT, mR, v)
+        t1.record()
+        torch.cuda.synchronize()
+        return v, rep, status, t0.elapsed_time(t1) / 1e3
+
+    v_ref, rep64, st64, sec64 = timed_register(ctx64, mT64, mR64, torch.float64)
+    res["f64"] = {"seconds": sec64, "gn_iters": rep64["gn_iters"], "matvecs": rep64["matvecs"],
+                  "mismatch_rel": rep64["mismatch_rel"], "gnorm_rel": rep64["gnorm_rel"], "status": st64}
+    ctx64.close()
+    for name, mask in (("f32", 0), ("f32_bf16grad", 1)):
+        c = pkg.Context(n, precision="f32", bf16_mask=mask, **SOLVER_KW)
+        mT = mT64.float()
+        mR = mR64.float()
+        v = v64.float()
+        vt = vt64.float()
+        e = {"transport": rel(c.transport(mT, v, +1), ref["transport"])}
+        c.linearize(mT, v)
+        e["hessvec_data"] = rel(c.hessvec_data(vt), ref["hessvec_data"])
+        gv = c.gradient(mT, mR, v)
+        e["gradient_api"] = rel(gv, ref["gradient"])
+        e["gradient_data"] = rel(gv - c.spectral("A", v) * SOLVER_KW["beta"], ref["gradient_data"])
+        c.linearize(mT, v)
+        out = torch.empty_like(vt)
+        for _ in range(3):
+            c.hessvec_cached(vt, out)
+        ts = []
+        for _ in range(10):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            c.hessvec_cached(vt, out)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        vv, rep, st, sec = timed_register(c, mT, mR, torch.float32)
+        res[name] = {"errors_vs_f64": e, "hessian_matvecs_per_s": 1e3 / sorted(ts)[len(ts) // 2], "seconds": sec,
+                     "gn_iters": rep["gn_iters"], "matvecs": rep["matvecs"], "mismatch_rel": rep["mismatch_rel"],
+                     "gnorm_rel": rep["gnorm_rel"], "status": st, "v_rel_err_vs_f64": rel(vv, v_ref),
+                     "speedup_vs_f64_solve": sec64 / sec}
+        c.close()
+    print(json.dumps({"study": "precision", "config": workload(n), "results": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.study == "precision":
+        return precision_study(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

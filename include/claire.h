@@ -71,6 +71,10 @@ typedef struct {
     double pcg_rtol;     /* > 0: fixed relative PCG tolerance; <= 0: eps_H = min(0.5, sqrt(||g_k||/||g_0||)) (Alg. 2) */
     int max_ls;          /* Armijo trials (default 10); alpha starts at 1 and is halved */
     double armijo_c1;    /* sufficient-decrease constant (default 1e-4) */
+    int bf16_mask;       /* reduced-precision storage (FP32 contexts only; default 0): bit 0 stores the spectral
+                            gradients of the state history, grad m^j, in BF16 (read by every incremental state and
+                            adjoint step; arithmetic stays FP32, reductions FP64). The error this adds is measured,
+                            not bounded by the FP32 tolerance. */
 } claire_opts;
 
 /* What claire_register reports (the quantities of Table 3 plus timing). Host struct, filled on return. */

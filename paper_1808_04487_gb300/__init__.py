@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
                 ("nt", ctypes.c_int), ("regnorm", ctypes.c_int), ("divfree", ctypes.c_int),
                 ("gtol_rel", ctypes.c_double), ("gtol_abs", ctypes.c_double), ("max_gn", ctypes.c_int),
                 ("max_krylov", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("max_ls", ctypes.c_int),
-                ("armijo_c1", ctypes.c_double)]
+                ("armijo_c1", ctypes.c_double), ("bf16_mask", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -128,7 +128,7 @@ class Context:
     """One registration problem setup (grid, precision, beta, n_t, norm, constraint) and its device workspace."""
 
     def __init__(self, n, precision="f32", beta=1e-2, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2,
-                 gtol_abs=1e-6, max_gn=50, max_krylov=100, pcg_rtol=0.0, max_ls=10, armijo_c1=1e-4):
+                 gtol_abs=1e-6, max_gn=50, max_krylov=100, pcg_rtol=0.0, max_ls=10, armijo_c1=1e-4, bf16_mask=0):
         L = lib()
         torch = _torch()
         if not torch.cuda.is_available():
@@ -142,6 +142,7 @@ class Context:
         o.beta, o.nt, o.regnorm, o.divfree = float(beta), int(nt), int(regnorm), int(bool(divfree))
         o.gtol_rel, o.gtol_abs, o.max_gn, o.max_krylov = float(gtol_rel), float(gtol_abs), int(max_gn), int(max_krylov)
         o.pcg_rtol, o.max_ls, o.armijo_c1 = float(pcg_rtol), int(max_ls), float(armijo_c1)
+        o.bf16_mask = int(bf16_mask)
         self.opts = o
         torch.cuda.init()
         h = _VP()

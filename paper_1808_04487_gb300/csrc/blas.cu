@@ -1,6 +1,8 @@
 // Streaming vector kernels of the Krylov and Gauss-Newton loops (Alg. 1, Alg. 2): FP64-accumulated inner products
 // (warp-shuffle + shared-memory block reduction into a fixed number of partials, then a one-block deterministic
 // finish, so results are reproducible run to run) and the fused PCG updates.
+#include <cuda_bf16.h>
+
 #include <mutex>
 
 #include "impl.cuh"
@@ -87,6 +89,11 @@ __global__ void __launch_bounds__(1024) k_max_final(const double* __restrict__ p
   }
 }
 
+__global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
 template <class T>
 __global__ void k_axpy(long long n, T a, const T* __restrict__ x, T* __restrict__ y) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -166,6 +173,13 @@ claire_status absmax_partial(claire_ctx* c, const T* a, long long n, double* par
 claire_status max_final(claire_ctx* c, const double* partials, int np, double* out, cudaStream_t st) {
   c->prof_begin("max_final", st);
   k_max_final<<<1, 1024, 0, st>>>(partials, np, out);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+
+claire_status to_bf16(claire_ctx* c, const float* x, void* y, long long n, cudaStream_t st) {
+  c->prof_begin("to_bf16", st);
+  k_to_bf16<<<stream_blocks(n), kThreads, 0, st>>>(x, static_cast<__nv_bfloat16*>(y), n);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }

@@ -24,6 +24,7 @@ template <class T> struct Work {
   T* dY = nullptr;      // [3][N] adjoint departure displacement
   T* m = nullptr;       // [nt+1][N] state history
   T* gm = nullptr;      // [nt+1][3][N] spectral gradients of the state history
+  void* gm16 = nullptr; // [nt+1][3][N] the same history in BF16 (reduced-storage mode, FP32 only)
   T* rho = nullptr;     // [N] div v (only without the div v = 0 constraint)
   T* la = nullptr;      // [N] adjoint ping
   T* lb = nullptr;      // [N] adjoint pong
@@ -69,6 +70,7 @@ struct claire_ctx {
   claire::Work<float> wf{};
   claire::Work<double> wd{};
   bool lin_valid = false;
+  bool gm16_on = false;        // gradient history stored in BF16 (claire_opts.bf16_mask bit 0)
   int haloX = -1, haloY = -1;  // brick halo of the cached departure points (-1: unknown, plain gathers)
   long long dot_blocks = 0;    // partials written by the last dot-fused adjoint step
   double* hscal = nullptr;  // pinned host mirror of Work::scal
@@ -176,13 +178,14 @@ template <class T> claire_status sl_init(claire_ctx* c);
 template <class T> claire_status sl_interp(claire_ctx* c, const T* f, const T* disp, T* out, cudaStream_t st,
                                            int H = -1);
 // lam = mR - m1; optionally rl = rho*lam; b = w * lam * gm  (terminal condition of the adjoint, Eq. (4))
+// gm arguments point to a gradient history slice of type T, or BF16 when g16 (FP32 only)
 template <class T> claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR, const T* m1, const T* rho, T* lam,
-                                                     T* rl, T* b, const T* gmj, T w, cudaStream_t st);
+                                                     T* rl, T* b, const void* gmj, bool g16, T w, cudaStream_t st);
 // one backward continuity step along Y; rho/rl_next: div source (or null); lam/rl: stores (or null);
 // b: accumulation b += w lam grad m (or null)
 // with sdot (and lam == null, b != null): also part[block] = partial <sdot, b_final>, one slot per block of launch3
 template <class T> claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next, const T* rho,
-                                                 const T* dY, T* lam, T* rl, T* b, const T* gmj, T w,
+                                                 const T* dY, T* lam, T* rl, T* b, const void* gmj, bool g16, T w,
                                                  cudaStream_t st, const T* sdot = nullptr, double* part = nullptr,
                                                  int H = -1);
 // launch shape of the gather kernels: 256 threads, x along i3 (up to 64 wide), y along i2, z = i1
@@ -191,11 +194,12 @@ struct Launch3 {
 };
 Launch3 launch3(const Dims& d);
 // q^0 = -(dt/2) vt . grad m^0
-template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, const T* gm0, T* q, cudaStream_t st);
+template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, const void* gm0, bool g16, T* q,
+                                                  cudaStream_t st);
 // m~^{j+1} = q^j(X) + dt/2 f^{j+1}; writes q^{j+1}, or on the last step lam~ = -m~, rho*lam~, b = w lam~ grad m
-template <class T> claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* vt, const T* gmj1,
-                                                  T* qout, bool last, const T* rho, T* rl, T* b, T w,
-                                                  cudaStream_t st, int H = -1);
+template <class T> claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* vt,
+                                                  const void* gmj1, bool g16, T* qout, bool last, const T* rho, T* rl,
+                                                  T* b, T w, cudaStream_t st, int H = -1);
 
 // ---- blas.cu --------------------------------------------------------------------------------------------------
 // partials[kReduceBlocks] of sum a*b (FP64 accumulation); a == b allowed
@@ -211,6 +215,8 @@ template <class T> claire_status diffsq_partial(claire_ctx* c, const T* a, const
                                                 cudaStream_t st);
 // out[slot] = scale * sum(partials[0..kReduceBlocks))
 claire_status reduce_final(claire_ctx* c, const double* partials, double scale, double* out, cudaStream_t st);
+// y = x rounded to BF16 (round to nearest even)
+claire_status to_bf16(claire_ctx* c, const float* x, void* y, long long n, cudaStream_t st);
 // y = a*x + y
 template <class T> claire_status axpy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st);
 // y = x + a*y

@@ -10,11 +10,26 @@
 
 namespace claire {
 
-// the tiled FP32 launchers live in sl_h<H>.cu
+// the tiled FP32 launchers live in sl_h<H>.cu (FP32 gradient history) and sl_h<H>_bf16.cu (BF16 history)
 CLAIRE_SL_LAUNCHERS(extern, float, 2)
 CLAIRE_SL_LAUNCHERS(extern, float, 3)
 CLAIRE_SL_LAUNCHERS(extern, float, 4)
 CLAIRE_SL_LAUNCHERS(extern, float, 5)
+CLAIRE_SL_LAUNCHERS_G(extern, float, 2, __nv_bfloat16)
+CLAIRE_SL_LAUNCHERS_G(extern, float, 3, __nv_bfloat16)
+CLAIRE_SL_LAUNCHERS_G(extern, float, 4, __nv_bfloat16)
+CLAIRE_SL_LAUNCHERS_G(extern, float, 5, __nv_bfloat16)
+
+// Calls f(g) with g a typed pointer to the gradient history: T, or BF16 when g16 (FP32 only).
+template <class T, class F> static void with_gm(const void* gm, bool g16, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    if (g16) {
+      f(static_cast<const __nv_bfloat16*>(gm));
+      return;
+    }
+  }
+  f(static_cast<const T*>(gm));
+}
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
@@ -66,19 +81,23 @@ claire_status sl_interp(claire_ctx* c, const T* f, const T* disp, T* out, cudaSt
 
 template <class T>
 claire_status sl_adjoint_terminal(claire_ctx* c, const T* mR, const T* m1, const T* rho, T* lam, T* rl, T* b,
-                                  const T* gmj, T w, cudaStream_t st) {
+                                  const void* gmj, bool g16, T w, cudaStream_t st) {
   c->prof_begin(rho ? "sl_adj_terminal_rho" : "sl_adj_terminal", st);
-  if (rho)
-    k_adj_terminal<T, true><<<blocks_for(c->d.N), kThreads, 0, st>>>(mR, m1, rho, lam, rl, b, gmj, w, c->d);
-  else
-    k_adj_terminal<T, false><<<blocks_for(c->d.N), kThreads, 0, st>>>(mR, m1, rho, lam, rl, b, gmj, w, c->d);
+  with_gm<T>(gmj, g16, [&](auto g) {
+    using G = std::remove_const_t<std::remove_pointer_t<decltype(g)>>;
+    if (rho)
+      k_adj_terminal<T, true, G><<<blocks_for(c->d.N), kThreads, 0, st>>>(mR, m1, rho, lam, rl, b, g, w, c->d);
+    else
+      k_adj_terminal<T, false, G><<<blocks_for(c->d.N), kThreads, 0, st>>>(mR, m1, rho, lam, rl, b, g, w, c->d);
+  });
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 
 template <class T>
 claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next, const T* rho, const T* dY, T* lam,
-                              T* rl, T* b, const T* gmj, T w, cudaStream_t st, const T* sdot, double* part, int H) {
+                              T* rl, T* b, const void* gmj, bool g16, T w, cudaStream_t st, const T* sdot, double* part,
+                              int H) {
   const T dt = T(1.0 / c->o.nt);
   const bool dot = sdot != nullptr && b != nullptr && lam == nullptr;
   const int key = (rho ? 4 : 0) | (lam ? 2 : 0) | (b ? 1 : 0);
@@ -91,8 +110,8 @@ claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next
     dim3 grid, block;
     tiled_shape<-1>(c->d, grid, block);
 #define ADJ_PLAIN(R, S)                                                                                          \
-  k_adj_step<T, R, S, false, false, -1><<<grid, block, 0, st>>>(lam_next, rl_next, rho, dY, lam, rl, b, gmj, w, dt, \
-                                                                c->d, sdot, part)
+  k_adj_step<T, R, S, false, false, -1, T><<<grid, block, 0, st>>>(lam_next, rl_next, rho, dY, lam, rl, b,       \
+                                                                   (const T*)nullptr, w, dt, c->d, sdot, part)
     if (rho) {
       if (lam)
         ADJ_PLAIN(true, true);
@@ -108,32 +127,42 @@ claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next
   } else {
     const int h = tile_halo<T>(H);
     with_halo<T>(h, [&](auto hc) {
-      const long long nb = sl_launch_adj<T, decltype(hc)::value>(rho != nullptr, lam != nullptr, dot, lam_next,
-                                                                 rl_next, rho, dY, lam, rl, b, gmj, w, dt, c->d,
-                                                                 sdot, part, st);
-      if (dot) c->dot_blocks = nb;
+      with_gm<T>(gmj, g16, [&](auto g) {
+        using G = std::remove_const_t<std::remove_pointer_t<decltype(g)>>;
+        const long long nb = sl_launch_adj<T, decltype(hc)::value, G>(rho != nullptr, lam != nullptr, dot, lam_next,
+                                                                      rl_next, rho, dY, lam, rl, b, g, w, dt, c->d,
+                                                                      sdot, part, st);
+        if (dot) c->dot_blocks = nb;
+      });
     });
   }
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 
-template <class T> claire_status sl_incstate_init(claire_ctx* c, const T* vt, const T* gm0, T* q, cudaStream_t st) {
+template <class T>
+claire_status sl_incstate_init(claire_ctx* c, const T* vt, const void* gm0, bool g16, T* q, cudaStream_t st) {
   c->prof_begin("sl_inc_init", st);
-  k_inc_init<T><<<blocks_for(c->d.N), kThreads, 0, st>>>(vt, gm0, q, T(0.5 / c->o.nt), c->d);
+  with_gm<T>(gm0, g16, [&](auto g) {
+    using G = std::remove_const_t<std::remove_pointer_t<decltype(g)>>;
+    k_inc_init<T, G><<<blocks_for(c->d.N), kThreads, 0, st>>>(vt, g, q, T(0.5 / c->o.nt), c->d);
+  });
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 
 template <class T>
-claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* vt, const T* gmj1, T* qout, bool last,
-                               const T* rho, T* rl, T* b, T w, cudaStream_t st, int H) {
+claire_status sl_incstate_step(claire_ctx* c, const T* q, const T* dX, const T* vt, const void* gmj1, bool g16,
+                               T* qout, bool last, const T* rho, T* rl, T* b, T w, cudaStream_t st, int H) {
   const T hdt = T(0.5 / c->o.nt);
   c->prof_begin(!last ? "sl_inc_step" : (rho ? "sl_inc_step_last_rho" : "sl_inc_step_last"), st);
   const int variant = !last ? 0 : (rho ? 2 : 1);
   const int h = tile_halo<T>(H);
   with_halo<T>(h, [&](auto hc) {
-    sl_launch_inc<T, decltype(hc)::value>(variant, q, dX, vt, gmj1, qout, rho, rl, b, hdt, w, c->d, st);
+    with_gm<T>(gmj1, g16, [&](auto g) {
+      using G = std::remove_const_t<std::remove_pointer_t<decltype(g)>>;
+      sl_launch_inc<T, decltype(hc)::value, G>(variant, q, dX, vt, g, qout, rho, rl, b, hdt, w, c->d, st);
+    });
   });
   CL_LAUNCHED(c);
   return CLAIRE_OK;
@@ -167,13 +196,13 @@ template <class T> claire_status sl_hadamard(claire_ctx* c, const T* a, const T*
   template claire_status sl_departure<T>(claire_ctx*, const T*, int, T*, cudaStream_t);                         \
   template claire_status sl_init<T>(claire_ctx*);                                                                \
   template claire_status sl_interp<T>(claire_ctx*, const T*, const T*, T*, cudaStream_t, int);                  \
-  template claire_status sl_adjoint_terminal<T>(claire_ctx*, const T*, const T*, const T*, T*, T*, T*, const T*, \
-                                                T, cudaStream_t);                                               \
+  template claire_status sl_adjoint_terminal<T>(claire_ctx*, const T*, const T*, const T*, T*, T*, T*,           \
+                                                const void*, bool, T, cudaStream_t);                            \
   template claire_status sl_adjoint_step<T>(claire_ctx*, const T*, const T*, const T*, const T*, T*, T*, T*,     \
-                                            const T*, T, cudaStream_t, const T*, double*, int);                 \
-  template claire_status sl_incstate_init<T>(claire_ctx*, const T*, const T*, T*, cudaStream_t);                \
-  template claire_status sl_incstate_step<T>(claire_ctx*, const T*, const T*, const T*, const T*, T*, bool,     \
-                                             const T*, T*, T*, T, cudaStream_t, int);
+                                            const void*, bool, T, cudaStream_t, const T*, double*, int);        \
+  template claire_status sl_incstate_init<T>(claire_ctx*, const T*, const void*, bool, T*, cudaStream_t);      \
+  template claire_status sl_incstate_step<T>(claire_ctx*, const T*, const T*, const T*, const void*, bool, T*,  \
+                                             bool, const T*, T*, T*, T, cudaStream_t, int);
 INST(float)
 INST(double)
 #undef INST

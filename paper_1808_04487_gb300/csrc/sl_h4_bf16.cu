@@ -1,0 +1,6 @@
+// Brick-tiled FP32 semi-Lagrangian launchers with a BF16 gradient history, halo 4 (see sl_kernels.cuh).
+#include "sl_kernels.cuh"
+
+namespace claire {
+CLAIRE_SL_LAUNCHERS_G(, float, 4, __nv_bfloat16)
+}  // namespace claire

@@ -1,11 +1,22 @@
 // Semi-Lagrangian device code shared by sl.cu and the per-halo units sl_h<H>.cu (internal).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "impl.cuh"
 
 namespace claire {
+
+// Element of a gradient history stored as G (the compute type T, or BF16 for the reduced-storage mode)
+template <class T, class G> __device__ __forceinline__ T ldg_as(const G* p) {
+  if constexpr (std::is_same<G, __nv_bfloat16>::value) {
+    return T(__bfloat162float(p[0]));
+  } else {
+    return __ldg(p);
+  }
+}
 
 // Per-axis part of a stencil: the four cubic Lagrange weights and the unwrapped first stencil node b - 1.
 template <class T> __device__ __forceinline__ int axis_setup(int i, T disp, T* w) {
@@ -300,11 +311,11 @@ __global__ void __launch_bounds__(256) k_interp(const T* __restrict__ f, const T
 }
 
 // lam = mR - m1 (Eq. (4) final condition), rl = rho lam, b = w lam grad m^{nt}
-template <class T, bool RHO>
+template <class T, bool RHO, class G>
 __global__ void __launch_bounds__(256) k_adj_terminal(const T* __restrict__ mR, const T* __restrict__ m1,
                                                       const T* __restrict__ rho, T* __restrict__ lam,
                                                       T* __restrict__ rl, T* __restrict__ b,
-                                                      const T* __restrict__ gm, T w, Dims d) {
+                                                      const G* __restrict__ gm, T w, Dims d) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= d.N) return;
   const long long N = d.N;
@@ -312,19 +323,19 @@ __global__ void __launch_bounds__(256) k_adj_terminal(const T* __restrict__ mR, 
   lam[idx] = l;
   if (RHO) rl[idx] = rho[idx] * l;
   const T wl = w * l;
-  b[idx] = wl * gm[idx];
-  b[N + idx] = wl * gm[N + idx];
-  b[2 * N + idx] = wl * gm[2 * N + idx];
+  b[idx] = wl * ldg_as<T, G>(gm + idx);
+  b[N + idx] = wl * ldg_as<T, G>(gm + N + idx);
+  b[2 * N + idx] = wl * ldg_as<T, G>(gm + 2 * N + idx);
 }
 
 // One backward step of -d_t lam - div(lam v) = 0 along Y (Eq. (4), (9)):
 //   a = lam^{j+1}(Y); with the div source: c = (rho lam^{j+1})(Y), lam^j = a + dt/2 (c + rho(x)(a + dt c)).
 // Epilogue: optional store of lam^j and rho lam^j, and b += w_j lam^j grad m^j.
-template <class T, bool RHO, bool STORE, bool ACC, bool DOT, int H>
+template <class T, bool RHO, bool STORE, bool ACC, bool DOT, int H, class G>
 __global__ void __launch_bounds__(256) k_adj_step(const T* __restrict__ lam_next, const T* __restrict__ rl_next,
                                                   const T* __restrict__ rho, const T* __restrict__ dY,
                                                   T* __restrict__ lam, T* __restrict__ rl, T* __restrict__ b,
-                                                  const T* __restrict__ gm, T w, T dt, Dims d,
+                                                  const G* __restrict__ gm, T w, T dt, Dims d,
                                                   const T* __restrict__ sv, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
@@ -351,9 +362,9 @@ __global__ void __launch_bounds__(256) k_adj_step(const T* __restrict__ lam_next
     }
     if (ACC) {
       const T wl = w * l;
-      const T b0 = fma(wl, gm[idx], b[idx]);
-      const T b1 = fma(wl, gm[N + idx], b[N + idx]);
-      const T b2 = fma(wl, gm[2 * N + idx], b[2 * N + idx]);
+      const T b0 = fma(wl, ldg_as<T, G>(gm + idx), b[idx]);
+      const T b1 = fma(wl, ldg_as<T, G>(gm + N + idx), b[N + idx]);
+      const T b2 = fma(wl, ldg_as<T, G>(gm + 2 * N + idx), b[2 * N + idx]);
       b[idx] = b0;
       b[N + idx] = b1;
       b[2 * N + idx] = b2;
@@ -381,21 +392,22 @@ __global__ void __launch_bounds__(256) k_adj_step(const T* __restrict__ lam_next
 }
 
 // q^0 = m~^0 + dt/2 f^0 with m~^0 = 0, f = -vt . grad m (Eq. (8))
-template <class T>
-__global__ void __launch_bounds__(256) k_inc_init(const T* __restrict__ vt, const T* __restrict__ gm,
+template <class T, class G>
+__global__ void __launch_bounds__(256) k_inc_init(const T* __restrict__ vt, const G* __restrict__ gm,
                                                   T* __restrict__ q, T hdt, Dims d) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= d.N) return;
   const long long N = d.N;
-  const T f = -(vt[idx] * gm[idx] + vt[N + idx] * gm[N + idx] + vt[2 * N + idx] * gm[2 * N + idx]);
+  const T f = -(vt[idx] * ldg_as<T, G>(gm + idx) + vt[N + idx] * ldg_as<T, G>(gm + N + idx) +
+                vt[2 * N + idx] * ldg_as<T, G>(gm + 2 * N + idx));
   q[idx] = hdt * f;
 }
 
 // m~^{j+1}(x) = q^j(X) + dt/2 f^{j+1}(x); not last: q^{j+1} = m~^{j+1} + dt/2 f^{j+1}.
 // last: lam~ = -m~(1) (Eq. (9) final condition), rl = rho lam~, b = w lam~ grad m^{nt}.
-template <class T, bool LAST, bool RHO, int H>
+template <class T, bool LAST, bool RHO, int H, class G>
 __global__ void __launch_bounds__(256) k_inc_step(const T* __restrict__ q, const T* __restrict__ dX,
-                                                  const T* __restrict__ vt, const T* __restrict__ gm,
+                                                  const T* __restrict__ vt, const G* __restrict__ gm,
                                                   T* __restrict__ qout, const T* __restrict__ rho,
                                                   T* __restrict__ rl, T* __restrict__ b, T hdt, T w, Dims d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(256) k_inc_step(const T* __restrict__ q, const
   for_nodes<H>(d, tl, [&](int i1, int i2, int i3, int idx) {
     Stencil<T> s;
     stencil_at<T>(i1, i2, i3, dX[idx], dX[N + idx], dX[2 * N + idx], d, s);
-    const T g1 = gm[idx], g2 = gm[N + idx], g3 = gm[2 * N + idx];
+    const T g1 = ldg_as<T, G>(gm + idx), g2 = ldg_as<T, G>(gm + N + idx), g3 = ldg_as<T, G>(gm + 2 * N + idx);
     const T f = -(vt[idx] * g1 + vt[N + idx] * g2 + vt[2 * N + idx] * g3);
     const T mt = sample<T, H>(q, sm, 0, tl, s, d) + hdt * f;
     if (!LAST) {
@@ -470,30 +482,30 @@ void sl_launch_interp(const T* f, const T* disp, T* out, const Dims& d, cudaStre
 }
 
 // variant: 0 inner step, 1 last step, 2 last step with the div source
-template <class T, int HC>
-void sl_launch_inc(int variant, const T* q, const T* dX, const T* vt, const T* gm, T* qout, const T* rho, T* rl, T* b,
+template <class T, int HC, class G>
+void sl_launch_inc(int variant, const T* q, const T* dX, const T* vt, const G* gm, T* qout, const T* rho, T* rl, T* b,
                    T hdt, T w, const Dims& d, cudaStream_t st) {
   dim3 grid, block;
   tiled_shape<HC>(d, grid, block);
   const size_t sm = tiled_smem<T, HC>(1);
   if (variant == 0)
-    k_inc_step<T, false, false, HC><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
+    k_inc_step<T, false, false, HC, G><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
   else if (variant == 2)
-    k_inc_step<T, true, true, HC><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
+    k_inc_step<T, true, true, HC, G><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
   else
-    k_inc_step<T, true, false, HC><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
+    k_inc_step<T, true, false, HC, G><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
 }
 
 // accumulating adjoint steps (rho: div source; store: keep lambda; dot: fused <sv, b>); returns the block count
-template <class T, int HC>
+template <class T, int HC, class G>
 long long sl_launch_adj(bool rho_on, bool store, bool dot, const T* lam_next, const T* rl_next, const T* rho,
-                        const T* dY, T* lam, T* rl, T* b, const T* gm, T w, T dt, const Dims& d, const T* sv,
+                        const T* dY, T* lam, T* rl, T* b, const G* gm, T w, T dt, const Dims& d, const T* sv,
                         double* part, cudaStream_t st) {
   dim3 grid, block;
   tiled_shape<HC>(d, grid, block);
   const size_t sm = tiled_smem<T, HC>(rho_on ? 2 : 1);
 #define ADJ(R, S, D) \
-  k_adj_step<T, R, S, true, D, HC><<<grid, block, sm, st>>>(lam_next, rl_next, rho, dY, lam, rl, b, gm, w, dt, d, sv, part)
+  k_adj_step<T, R, S, true, D, HC, G><<<grid, block, sm, st>>>(lam_next, rl_next, rho, dY, lam, rl, b, gm, w, dt, d, sv, part)
   if (dot) {
     if (rho_on)
       ADJ(true, false, true);
@@ -515,7 +527,7 @@ long long sl_launch_adj(bool rho_on, bool store, bool dot, const T* lam_next, co
 }
 
 // allow the tiled kernels of halo HC the shared memory of two bricks
-template <class T, int HC> cudaError_t sl_set_attrs() {
+template <class T, int HC, class G> cudaError_t sl_set_attrs_g() {
   if constexpr (HC >= 0) {
     const int two = (int)tiled_smem<T, HC>(2);
     cudaError_t e = cudaSuccess;
@@ -523,28 +535,46 @@ template <class T, int HC> cudaError_t sl_set_attrs() {
       cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, two);
       if (r != cudaSuccess) e = r;
     };
-    set((const void*)k_interp<T, HC>);
-    set((const void*)k_inc_step<T, false, false, HC>);
-    set((const void*)k_inc_step<T, true, true, HC>);
-    set((const void*)k_inc_step<T, true, false, HC>);
-    set((const void*)k_adj_step<T, true, false, true, true, HC>);
-    set((const void*)k_adj_step<T, false, false, true, true, HC>);
-    set((const void*)k_adj_step<T, false, false, true, false, HC>);
-    set((const void*)k_adj_step<T, false, true, true, false, HC>);
-    set((const void*)k_adj_step<T, true, false, true, false, HC>);
-    set((const void*)k_adj_step<T, true, true, true, false, HC>);
+    set((const void*)k_inc_step<T, false, false, HC, G>);
+    set((const void*)k_inc_step<T, true, true, HC, G>);
+    set((const void*)k_inc_step<T, true, false, HC, G>);
+    set((const void*)k_adj_step<T, true, false, true, true, HC, G>);
+    set((const void*)k_adj_step<T, false, false, true, true, HC, G>);
+    set((const void*)k_adj_step<T, false, false, true, false, HC, G>);
+    set((const void*)k_adj_step<T, false, true, true, false, HC, G>);
+    set((const void*)k_adj_step<T, true, false, true, false, HC, G>);
+    set((const void*)k_adj_step<T, true, true, true, false, HC, G>);
     return e;
   } else {
     return cudaSuccess;
   }
 }
 
+// allow the tiled kernels of halo HC the shared memory of two bricks
+template <class T, int HC> cudaError_t sl_set_attrs() {
+  if constexpr (HC >= 0) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_interp<T, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tiled_smem<T, HC>(2));
+    const cudaError_t e1 = sl_set_attrs_g<T, HC, T>();
+    if (e == cudaSuccess) e = e1;
+    if constexpr (sizeof(T) == 4) {
+      const cudaError_t e2 = sl_set_attrs_g<T, HC, __nv_bfloat16>();
+      if (e == cudaSuccess) e = e2;
+    }
+    return e;
+  } else {
+    return cudaSuccess;
+  }
+}
+
+#define CLAIRE_SL_LAUNCHERS_G(EXT, T, HC, G)                                                                      \
+  EXT template void sl_launch_inc<T, HC, G>(int, const T*, const T*, const T*, const G*, T*, const T*, T*, T*, T, T, \
+                                            const Dims&, cudaStream_t);                                           \
+  EXT template long long sl_launch_adj<T, HC, G>(bool, bool, bool, const T*, const T*, const T*, const T*, T*, T*,  \
+                                                 T*, const G*, T, T, const Dims&, const T*, double*, cudaStream_t);
 #define CLAIRE_SL_LAUNCHERS(EXT, T, HC)                                                                           \
   EXT template void sl_launch_interp<T, HC>(const T*, const T*, T*, const Dims&, cudaStream_t);                   \
-  EXT template void sl_launch_inc<T, HC>(int, const T*, const T*, const T*, const T*, T*, const T*, T*, T*, T, T,  \
-                                         const Dims&, cudaStream_t);                                             \
-  EXT template long long sl_launch_adj<T, HC>(bool, bool, bool, const T*, const T*, const T*, const T*, T*, T*, T*, \
-                                              const T*, T, T, const Dims&, const T*, double*, cudaStream_t);       \
+  CLAIRE_SL_LAUNCHERS_G(EXT, T, HC, T)                                                                            \
   EXT template cudaError_t sl_set_attrs<T, HC>();
 
 }  // namespace claire

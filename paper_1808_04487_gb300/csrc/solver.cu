@@ -38,7 +38,12 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
   ok &= takeT(W.dX, 3 * N);
   ok &= takeT(W.dY, 3 * N);
   ok &= takeT(W.m, (nt + 1) * N);
-  ok &= takeT(W.gm, 3 * (nt + 1) * N);
+  if (c->gm16_on) {
+    W.gm16 = c->take(2 * size_t(3 * (nt + 1) * N));
+    ok &= W.gm16 != nullptr;
+  } else {
+    ok &= takeT(W.gm, 3 * (nt + 1) * N);
+  }
   if (!c->o.divfree) ok &= takeT(W.rho, N);
   ok &= takeT(W.la, N);
   ok &= takeT(W.lb, N);
@@ -188,7 +193,16 @@ template <class T> claire_status finish_linearization(claire_ctx* c, const T* v,
   const long long N = c->d.N;
   CL_TRY(sl_departure<T>(c, v, -1, W.dY, st));
   CL_TRY(update_halo<T>(c, W.dY, &c->haloY, st));
-  for (int j = 0; j <= c->o.nt; ++j) CL_TRY(grad_spectral<T>(c, W.m + j * N, W.gm + 3LL * j * N, st));
+  for (int j = 0; j <= c->o.nt; ++j) {
+    if (c->gm16_on) {
+      // FP32 gradient into the b scratch, then stored in BF16
+      CL_TRY(grad_spectral<T>(c, W.m + j * N, W.b, st));
+      CL_TRY(to_bf16(c, reinterpret_cast<const float*>(W.b), static_cast<char*>(W.gm16) + 2 * 3LL * j * N, 3 * N,
+                     st));
+    } else {
+      CL_TRY(grad_spectral<T>(c, W.m + j * N, W.gm + 3LL * j * N, st));
+    }
+  }
   if (!c->o.divfree) CL_TRY(div_spectral<T>(c, v, W.rho, st));
   c->lin_valid = true;
   return CLAIRE_OK;
@@ -205,6 +219,14 @@ template <class T> claire_status linearize(claire_ctx* c, const T* mT, const T* 
 
 inline double tweight(int j, int nt) { return (j == 0 || j == nt) ? 0.5 / nt : 1.0 / nt; }
 
+// slice j of the gradient history (FP32/FP64, or BF16 in the reduced-storage mode)
+template <class T> inline const void* gm_at(claire_ctx* c, int j) {
+  Work<T>& W = c->work<T>();
+  const long long off = 3LL * j * c->d.N;
+  if (c->gm16_on) return static_cast<const char*>(W.gm16) + 2 * off;
+  return W.gm + off;
+}
+
 // adjoint backward from lam^{nt} = mR - m^{nt}; b = sum_j w_j lam^j grad m^j (Eq. (4), (5))
 template <class T> claire_status adjoint_integral(claire_ctx* c, const T* mR, cudaStream_t st) {
   Work<T>& W = c->work<T>();
@@ -213,13 +235,14 @@ template <class T> claire_status adjoint_integral(claire_ctx* c, const T* mR, cu
   T* lam[2] = {W.la, W.lb};
   T* rl[2] = {W.ra, W.rb};
   const T* rho = c->o.divfree ? nullptr : W.rho;
-  CL_TRY(sl_adjoint_terminal<T>(c, mR, W.m + nt * N, rho, lam[0], rl[0], W.b, W.gm + 3LL * nt * N,
+  CL_TRY(sl_adjoint_terminal<T>(c, mR, W.m + nt * N, rho, lam[0], rl[0], W.b, gm_at<T>(c, nt), c->gm16_on,
                                 T(tweight(nt, nt)), st));
   int cur = 0;
   for (int j = nt - 1; j >= 0; --j) {
     const bool store = j > 0;
     CL_TRY(sl_adjoint_step<T>(c, lam[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? lam[1 - cur] : nullptr,
-                              (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)), st,
+                              (store && rho) ? rl[1 - cur] : nullptr, W.b, gm_at<T>(c, j), c->gm16_on,
+                              T(tweight(j, nt)), st,
                               nullptr, nullptr, c->haloY));
     cur = 1 - cur;
   }
@@ -266,17 +289,18 @@ template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStrea
   T* rl[2] = {W.ra, W.rb};
   const T* rho = c->o.divfree ? nullptr : W.rho;
   int cur = 0;
-  CL_TRY(sl_incstate_init<T>(c, vt, W.gm, buf[cur], st));
+  CL_TRY(sl_incstate_init<T>(c, vt, gm_at<T>(c, 0), c->gm16_on, buf[cur], st));
   for (int j = 0; j < nt; ++j) {
     const bool last = j == nt - 1;
-    CL_TRY(sl_incstate_step<T>(c, buf[cur], W.dX, vt, W.gm + 3LL * (j + 1) * N, buf[1 - cur], last, rho,
+    CL_TRY(sl_incstate_step<T>(c, buf[cur], W.dX, vt, gm_at<T>(c, j + 1), c->gm16_on, buf[1 - cur], last, rho,
                                rl[1 - cur], W.b, T(tweight(nt, nt)), st, c->haloX));
     cur = 1 - cur;
   }
   for (int j = nt - 1; j >= 0; --j) {
     const bool store = j > 0;
     CL_TRY(sl_adjoint_step<T>(c, buf[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? buf[1 - cur] : nullptr,
-                              (store && rho) ? rl[1 - cur] : nullptr, W.b, W.gm + 3LL * j * N, T(tweight(j, nt)),
+                              (store && rho) ? rl[1 - cur] : nullptr, W.b, gm_at<T>(c, j), c->gm16_on,
+                              T(tweight(j, nt)),
                               st, (dot && j == 0) ? vt : nullptr, (dot && j == 0) ? W.bigpart : nullptr,
                               c->haloY));
     cur = 1 - cur;
@@ -550,7 +574,7 @@ template <class T> claire_status transport_dev(claire_ctx* c, const T* m0, const
   int cur = 0;
   for (int j = 0; j < nt; ++j) {
     CL_TRY(sl_adjoint_step<T>(c, buf[cur], rho ? rl[cur] : nullptr, rho, W.dY, buf[1 - cur], rho ? rl[1 - cur] : nullptr,
-                              nullptr, nullptr, T(0), st));
+                              nullptr, nullptr, false, T(0), st));
     cur = 1 - cur;
   }
   CL_CUDA(c, cudaMemcpyAsync(m1, buf[cur], sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
@@ -807,9 +831,11 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   const long long N = (long long)o.n[0] * o.n[1] * o.n[2];
   // 32-bit node indices in the kernels and the launch grid's z extent (one i1 slab per grid z index)
   if (N > (1LL << 31) - 1 || o.n[0] > 65535) return CLAIRE_EINVAL;
+  if (o.bf16_mask < 0 || o.bf16_mask > 1 || (o.bf16_mask && o.precision != CLAIRE_F32)) return CLAIRE_EINVAL;
   claire_ctx* c = new (std::nothrow) claire_ctx();
   if (!c) return CLAIRE_ENOMEM;
   c->o = o;
+  c->gm16_on = (o.bf16_mask & 1) != 0;
   c->d.n1 = o.n[0];
   c->d.n2 = o.n[1];
   c->d.n3 = o.n[2];

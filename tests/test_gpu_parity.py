@@ -357,3 +357,47 @@ def test_fullsize_gradient_and_hessvec_closed_forms_at_zero(big_inputs):
     vt32 = torch.from_numpy(vt).float().double().numpy()
     ref_h = O.leray(g, (vt32 * gm).sum(0) * gm)
     assert rel(hv, ref_h) < 1e-5
+
+
+# ------------------------------------------------------------------------------------------------------ precision form
+@pytest.fixture(scope="module")
+def h2_phantom48():
+    n = (48, 48, 48)
+    kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, max_gn=4, gtol_rel=1e-2)
+    p = O.Problem(n, **kw)
+    mT = I.brain_phantom(n, 0)
+    vs = I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=3.0, divfree=True)
+    mR = O.transport(p, mT, vs, +1)
+    return n, kw, p, rounded(mT, "f32"), rounded(mR, "f32")
+
+
+def test_bf16_gradient_history_errors_against_the_oracle(h2_phantom48):
+    """BF16 storage of grad m^j (claire_opts.bf16_mask bit 0): FP32 arithmetic, FP64 reductions. The stated error of
+    the data terms follows from BF16 rounding (relative 2^-9 per stored value); the solve must keep GN +-1 and the
+    final mismatch."""
+    n, kw, p, mT, mR = h2_phantom48
+    v = rounded(I.random_velocity(n, seed=12, kmax=3, max_disp_voxels=2.0, divfree=True), "f32")
+    vt = rounded(I.random_velocity(n, seed=13, kmax=4, amplitude=1.0, divfree=True), "f32")
+    lin = O.linearize(p, mT, v)
+    hd_ref = O.hessvec(p, lin, vt) - p.beta * O.apply_A(p.grid, vt, 2)
+    g_ref = O.reduced_gradient(p, lin, mR)
+    bnd = reg_noise_bound("f32", n, p.beta, 2, v)
+    errs = {}
+    for mask in (0, 1):
+        with ctx(n, "f32", bf16_mask=mask, **kw) as c:
+            c.linearize(dev(mT, "f32"), dev(v, "f32"))
+            errs[("hdata", mask)] = rel(c.hessvec_data(dev(vt, "f32")), hd_ref)
+            g = c.gradient(dev(mT, "f32"), dev(mR, "f32"), dev(v, "f32")).cpu().double().numpy()
+            errs[("grad_abs", mask)] = float(np.linalg.norm(g - g_ref))
+    print("per-operator errors vs the FP64 oracle:", errs, "gradient norm", np.linalg.norm(g_ref), "bound", bnd)
+    assert errs[("hdata", 0)] < 1e-5 and errs[("grad_abs", 0)] <= 1e-5 * np.linalg.norm(g_ref) + bnd
+    assert errs[("hdata", 1)] < 8 * 2.0 ** -9
+    assert errs[("grad_abs", 1)] <= 8 * 2.0 ** -9 * np.linalg.norm(g_ref) + bnd
+    v_ref, rep_ref = O.register(p, mT, mR)
+    with ctx(n, "f32", bf16_mask=1, **kw) as c:
+        v16, rep16, st = c.register(dev(mT, "f32"), dev(mR, "f32"))
+    print("register bf16: rel v err %.3e, GN %d vs %d, mismatch %.6e vs %.6e" % (
+        rel(v16, v_ref), rep16["gn_iters"], rep_ref.gn_iters, rep16["mismatch"], rep_ref.mismatch))
+    assert abs(rep16["gn_iters"] - rep_ref.gn_iters) <= 1
+    assert abs(rep16["mismatch"] - rep_ref.mismatch) <= 2e-2 * rep_ref.mismatch
+    assert rel(v16, v_ref) < 2e-2
