@@ -181,6 +181,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, dist, device=None):
+    """Max of a per-rank float over the process group (no-op without one); the job's time is its slowest rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_seconds_per_registration(ms_max, steps, world):
+    """Whole-job value: `world` replicas each solve `steps` registrations in ms_max (the slowest rank)."""
+    return ms_max / 1e3 / (steps * world)
+
+
 def cpu_baseline(n_target, seconds_budget=30.0):
     """Oracle (FP64 numpy, as it stands) on a bounded sample: the same problem family at 32^3, extrapolated to the
     target grid by voxel count (the solver's work per iteration is linear in N up to the FFT's log factor, and
@@ -379,12 +394,9 @@ def main():
     ctx.profile(False)
     launches = ctx.launches() - launches0
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = ms_per_step / 1e3 / world  # seconds per registration, whole job (N replicas in parallel)
+    value = whole_job_seconds_per_registration(ms, args.steps, world)  # whole job: N replicas in parallel
 
     # ---- Hessian matvecs/s at the converged linearisation (full matvec incl. beta A through its symbol)
     ctx.linearize(mT, v)
@@ -443,11 +455,7 @@ def main():
             ctx.register_host(mT_h, mR_h, v_h.zero_())
         b.record(stream)
         torch.cuda.synchronize()
-        ems = a.elapsed_time(b) / k2
-        if dist is not None:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(a.elapsed_time(b) / k2, dist, dev)
         N = n[0] * n[1] * n[2]
         e2e = {"value": ems / 1e3 / world, "unit": "s", "h2d_bytes_per_step": 5 * N * 4 * world,
                "d2h_bytes_per_step": 3 * N * 4 * world}
