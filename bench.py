@@ -38,8 +38,10 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "precision"],
-                    help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path (own JSON line)")
+    ap.add_argument("--study", default=None, choices=[None, "precision", "batch"],
+                    help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path; batch: 64 "
+                         "population-to-atlas pairs on uneven grids, batched vs sequential (own JSON lines)")
+    ap.add_argument("--pairs", type=int, default=64)
     return ap.parse_args()
 
 
@@ -330,10 +332,65 @@ def precision_study(args):
     return 0
 
 
+BATCH_GRIDS = [(64, 64, 64), (96, 112, 96), (128, 128, 128), (160, 192, 144), (192, 192, 192)]
+
+
+def batch_study(args):
+    """Population-to-atlas batch: pairs with grids drawn uniformly (seeded) from BATCH_GRIDS; per grid one atlas
+    phantom m_R, per pair a template m_T = the atlas warped by its own band-limited v* (|k| <= 5, same physical
+    amplitude as 8 voxels at 256^3); H1, beta = 5e-3, n_t = 4, FP32 with FP64 reductions, to ||g|| <= 5e-2 ||g0||.
+    Times the batched call (concurrent workers) against the same pairs solved one after another."""
+    import numpy as np
+    import torch
+
+    import claire_inputs as I
+    import paper_1808_04487_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    kw = dict(beta=5e-3, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2)
+    rng = np.random.default_rng(2024)
+    choice = rng.integers(0, len(BATCH_GRIDS), size=args.pairs)
+    atlases = {}
+    pairs = []
+    for i, gi in enumerate(choice):
+        n = BATCH_GRIDS[gi]
+        if n not in atlases:
+            atlases[n] = torch.from_numpy(I.brain_phantom(n, seed=7)).float().to(dev)
+        vs = torch.from_numpy(I.random_velocity(n, seed=1000 + i, kmax=5, max_disp_voxels=8.0 * max(n) / 256.0))
+        with pkg.Context(n, precision="f32", **kw) as c:
+            mT = c.transport(atlases[n], vs.float().to(dev), +1)
+        pairs.append((mT, atlases[n], torch.zeros((3,) + n, dtype=torch.float32, device=dev)))
+    voxels = float(sum(np.prod(p[0].shape) for p in pairs))
+    res = {}
+    for nw in (1, 4, 8):
+        for _, _, v in pairs:
+            v.zero_()
+        pkg.register_batch(pairs[: min(4, len(pairs))], nworkers=nw, **kw)  # warm-up (contexts, autotuner)
+        for _, _, v in pairs:
+            v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = pkg.register_batch(pairs, nworkers=nw, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res["workers_%d" % nw] = {"seconds": dt, "pairs_per_s": len(pairs) / dt,
+                                  "converged": sum(1 for r, st in out if r["converged"]),
+                                  "matvecs": sum(r["matvecs"] for r, st in out)}
+    res["speedup_batched_vs_sequential"] = res["workers_1"]["seconds"] / min(
+        res["workers_4"]["seconds"], res["workers_8"]["seconds"])
+    print(json.dumps({"study": "batch", "pairs": len(pairs), "grids": [list(g) for g in BATCH_GRIDS],
+                      "grid_counts": {str(list(BATCH_GRIDS[k])): int((choice == k).sum()) for k in range(len(BATCH_GRIDS))},
+                      "total_voxels": voxels, "solver": kw, "results": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.study == "precision":
         return precision_study(args)
+    if args.study == "batch":
+        return batch_study(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

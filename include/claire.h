@@ -173,6 +173,24 @@ claire_status claire_register_host_f32(claire_ctx* ctx, const float* mT, const f
 claire_status claire_register_host_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
                                        claire_report* rep, void* stream);
 
+/* ---- batched registration of many independent pairs (population-to-atlas) ------------------------------------
+ * Solves every pair with claire_register_f32's algorithm. Pairs may have different grids. nworkers host threads
+ * (>= 1) each own a CUDA stream and one context per grid shape they meet (created from *base with n replaced by the
+ * pair's grid, freed before the call returns); pairs are taken largest grid first from a shared queue, so the
+ * solves of different pairs overlap on the GPU (small grids alone leave most SMs idle, and every GN/PCG step waits
+ * for a host round trip). mT, mR, v are DEVICE arrays of the pair's grid on the current device; v is in/out
+ * (zeros = the plain method). Per-pair results land in rep and status; the call returns CLAIRE_OK when every pair
+ * ran (statuses CLAIRE_OK / ENOTCONV / ELINESEARCH), else the first failing status. Synchronises the device. */
+typedef struct {
+    int n[3];
+    const float* mT;
+    const float* mR;
+    float* v;
+    claire_report rep;
+    int status;
+} claire_pair_f32;
+claire_status claire_register_batch_f32(const claire_opts* base, claire_pair_f32* pairs, int npairs, int nworkers);
+
 /* ---- building blocks exposed for testing and for callers composing their own solver --------------------------
  * claire_departure_*: RK2 departure points of one time step (dt = 1/nt) in grid units, disp = (X - x) / h per
  *   axis (dir = +1: state characteristics X of v; dir = -1: adjoint characteristics Y of -v). v, disp: vectors.

@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["Context", "ClaireError", "Report", "lib", "LIB_PATH", "STATUS"]
+__all__ = ["Context", "ClaireError", "Report", "lib", "LIB_PATH", "STATUS", "register_batch"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libclaire_gb.so")
 
@@ -48,6 +48,11 @@ class Report(ctypes.Structure):
         d["gnorm_rel"] = self.gnorm / self.gnorm0 if self.gnorm0 > 0 else 0.0
         d["mismatch_rel"] = self.mismatch / self.mismatch0 if self.mismatch0 > 0 else 0.0
         return d
+
+
+class PairF32(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("mT", ctypes.c_void_p), ("mR", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("rep", Report), ("status", ctypes.c_int)]
 
 
 class Counters(ctypes.Structure):
@@ -104,6 +109,8 @@ def lib():
     L.claire_workspace_bytes.restype = ctypes.c_size_t
     L.claire_get_counters.argtypes = [_VP, ctypes.POINTER(Counters)]
     L.claire_get_counters.restype = _I
+    L.claire_register_batch_f32.argtypes = [ctypes.POINTER(Opts), ctypes.POINTER(PairF32), _I, _I]
+    L.claire_register_batch_f32.restype = _I
     L.claire_dot_noalloc_f32.argtypes = [_VP, _VP, _LL, _D, _VP, _VP]
     L.claire_dot_noalloc_f32.restype = _I
     L.claire_profile_enable.argtypes = [_VP, _I]
@@ -117,6 +124,32 @@ def lib():
             f.restype = _I
     _lib = L
     return L
+
+
+def register_batch(pairs, nworkers=4, beta=5e-3, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2, max_gn=50,
+                   max_krylov=100, pcg_rtol=0.0):
+    """Batched FP32 registration of independent pairs [(mT, mR, v), ...] of CUDA tensors (grids may differ); v is
+    updated in place. Returns [(report dict, status name), ...] in input order."""
+    L = lib()
+    torch = _torch()
+    o = Opts()
+    L.claire_default_opts(ctypes.byref(o), 4, 4, 4, 0)
+    o.beta, o.nt, o.regnorm, o.divfree = float(beta), int(nt), int(regnorm), int(bool(divfree))
+    o.gtol_rel, o.max_gn, o.max_krylov, o.pcg_rtol = float(gtol_rel), int(max_gn), int(max_krylov), float(pcg_rtol)
+    arr = (PairF32 * len(pairs))()
+    for i, (mT, mR, v) in enumerate(pairs):
+        n = tuple(mT.shape)
+        for t, shp in ((mT, n), (mR, n), (v, (3,) + n)):
+            if t.device.type != "cuda" or t.dtype != torch.float32 or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError("pair %d: contiguous CUDA float32 tensors of matching grids required" % i)
+        for a in range(3):
+            arr[i].n[a] = n[a]
+        arr[i].mT, arr[i].mR, arr[i].v = mT.data_ptr(), mR.data_ptr(), v.data_ptr()
+    torch.cuda.synchronize()
+    st = L.claire_register_batch_f32(ctypes.byref(o), arr, len(pairs), int(nworkers))
+    if st not in (OK, ENOTCONV, ELINESEARCH):
+        raise ClaireError(st, "claire_register_batch_f32 failed")
+    return [(arr[i].rep.as_dict(), STATUS.get(arr[i].status, arr[i].status)) for i in range(len(pairs))]
 
 
 def _torch():

@@ -8,8 +8,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
+#include <tuple>
+#include <vector>
 #include <utility>
 
 #include "impl.cuh"
@@ -166,7 +172,54 @@ template <class T> claire_status spectral_tail(claire_ctx* c, const T* v, const 
   return vec_c2r<T>(c, B, out, st);
 }
 
-// Brick halo for the tiled gathers: max |displacement| D in voxels over the field -> H = ceil(D) + 1
+// slice j of the gradient history (FP32/FP64, or BF16 in the reduced-storage mode)
+template <class T> inline const void* gm_at(claire_ctx* c, int j) {
+  Work<T>& W = c->work<T>();
+  const long long off = 3LL * j * c->d.N;
+  if (c->gm16_on) return static_cast<const char*>(W.gm16) + 2 * off;
+  return W.gm + off;
+}
+
+// Autotuner of the gather schedule: for a grid and brick halo, time the brick-tiled and the plain incremental
+// state step once (on scratch buffers) and keep the faster; the choice is cached for the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, bool> g_tune;
+
+template <class T> claire_status tune_tiling(claire_ctx* c, int H, bool* tiled, cudaStream_t st) {
+  const auto key = std::make_tuple(c->d.n1, c->d.n2, c->d.n3, H, c->gm16_on ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *tiled = it->second;
+      return CLAIRE_OK;
+    }
+  }
+  Work<T>& W = c->work<T>();
+  cudaEvent_t e[3];
+  for (auto& x : e) CL_CUDA(c, cudaEventCreate(&x));
+  float ms[2] = {0.f, 0.f};
+  for (int variant = 0; variant < 2; ++variant) {
+    const int h = variant == 0 ? H : -1;
+    CL_TRY(sl_incstate_step<T>(c, W.la, W.dX, W.s, gm_at<T>(c, 0), c->gm16_on, W.lb, false, nullptr, nullptr,
+                               nullptr, T(0), st, h));  // warm-up
+    CL_CUDA(c, cudaEventRecord(e[0], st));
+    for (int r = 0; r < 3; ++r)
+      CL_TRY(sl_incstate_step<T>(c, W.la, W.dX, W.s, gm_at<T>(c, 0), c->gm16_on, W.lb, false, nullptr, nullptr,
+                                 nullptr, T(0), st, h));
+    CL_CUDA(c, cudaEventRecord(e[1], st));
+    CL_CUDA(c, cudaEventSynchronize(e[1]));
+    CL_CUDA(c, cudaEventElapsedTime(&ms[variant], e[0], e[1]));
+  }
+  for (auto& x : e) cudaEventDestroy(x);
+  *tiled = ms[0] <= ms[1];
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = *tiled;
+  return CLAIRE_OK;
+}
+
+// Brick halo for the tiled gathers: max |displacement| D in voxels over the field -> H = ceil(D) + 1 (or -1 when
+// the autotuner found the plain gathers faster on this grid)
 template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* halo, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   CL_TRY(absmax_partial<T>(c, disp, 3 * c->d.N, W.partials, st));
@@ -174,6 +227,11 @@ template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* 
   double D;
   CL_TRY(read_scalar(c, W.scal + 12, &D, st));
   *halo = (std::isfinite(D) && D < 64.0) ? (int)std::ceil(D + 1e-3) + 1 : -1;
+  if (*halo >= 0 && sizeof(T) == 4 && c->gm_ready) {
+    bool tiled = true;
+    CL_TRY(tune_tiling<T>(c, *halo < 2 ? 2 : *halo, &tiled, st));
+    if (!tiled) *halo = -1;
+  }
   return CLAIRE_OK;
 }
 
@@ -205,6 +263,7 @@ template <class T> claire_status finish_linearization(claire_ctx* c, const T* v,
   }
   if (!c->o.divfree) CL_TRY(div_spectral<T>(c, v, W.rho, st));
   c->lin_valid = true;
+  c->gm_ready = true;
   return CLAIRE_OK;
 }
 
@@ -219,13 +278,6 @@ template <class T> claire_status linearize(claire_ctx* c, const T* mT, const T* 
 
 inline double tweight(int j, int nt) { return (j == 0 || j == nt) ? 0.5 / nt : 1.0 / nt; }
 
-// slice j of the gradient history (FP32/FP64, or BF16 in the reduced-storage mode)
-template <class T> inline const void* gm_at(claire_ctx* c, int j) {
-  Work<T>& W = c->work<T>();
-  const long long off = 3LL * j * c->d.N;
-  if (c->gm16_on) return static_cast<const char*>(W.gm16) + 2 * off;
-  return W.gm + off;
-}
 
 // adjoint backward from lam^{nt} = mR - m^{nt}; b = sum_j w_j lam^j grad m^j (Eq. (4), (5))
 template <class T> claire_status adjoint_integral(claire_ctx* c, const T* mR, cudaStream_t st) {
@@ -998,6 +1050,85 @@ claire_status claire_register_host_f64(claire_ctx* c, const double* mT, const do
                                        claire_report* rep, void* s) {
   return api_register_host<double>(c, mT, mR, v, rep, s);
 }
+claire_status claire_register_batch_f32(const claire_opts* base, claire_pair_f32* pairs, int npairs, int nworkers) {
+  if (!base || (!pairs && npairs > 0) || npairs < 0 || nworkers < 1) return CLAIRE_EINVAL;
+  if (base->precision != CLAIRE_F32) return CLAIRE_EINVAL;
+  for (int i = 0; i < npairs; ++i)
+    if (!pairs[i].mT || !pairs[i].mR || !pairs[i].v) return CLAIRE_EINVAL;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return CLAIRE_ECUDA;
+  // largest grids first (longest-processing-time order over the workers)
+  std::vector<int> order(npairs);
+  for (int i = 0; i < npairs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const long long na = (long long)pairs[a].n[0] * pairs[a].n[1] * pairs[a].n[2];
+    const long long nb = (long long)pairs[b].n[0] * pairs[b].n[1] * pairs[b].n[2];
+    return na > nb;
+  });
+  std::atomic<int> next(0);
+  std::atomic<int> first_error(0);
+  auto worker = [&]() {
+    if (cudaSetDevice(device) != cudaSuccess) {
+      first_error.store(CLAIRE_ECUDA);
+      return;
+    }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      first_error.store(CLAIRE_ECUDA);
+      return;
+    }
+    std::map<std::tuple<int, int, int>, claire_ctx*> ctxs;
+    for (int k = next.fetch_add(1); k < npairs; k = next.fetch_add(1)) {
+      claire_pair_f32& p = pairs[order[k]];
+      const auto key = std::make_tuple(p.n[0], p.n[1], p.n[2]);
+      claire_ctx* c = nullptr;
+      auto it = ctxs.find(key);
+      if (it != ctxs.end()) {
+        c = it->second;
+      } else {
+        claire_opts o = *base;
+        o.n[0] = p.n[0];
+        o.n[1] = p.n[1];
+        o.n[2] = p.n[2];
+        const claire_status cs = claire_create(&o, &c);
+        if (cs != CLAIRE_OK) {
+          p.status = cs;
+          int zero = 0;
+          first_error.compare_exchange_strong(zero, (int)cs);
+          continue;
+        }
+        ctxs[key] = c;
+      }
+      const claire_status rs = register_dev<float>(c, p.mT, p.mR, p.v, &p.rep, st);
+      p.status = rs;
+      if (rs != CLAIRE_OK && rs != CLAIRE_ENOTCONV && rs != CLAIRE_ELINESEARCH) {
+        int zero = 0;
+        first_error.compare_exchange_strong(zero, (int)rs);
+      }
+    }
+    cudaStreamSynchronize(st);
+    for (auto& kv : ctxs) {
+      // the context's own destroy synchronises the whole device; free its memory directly instead
+      claire_ctx* c = kv.second;
+      for (auto& r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+      for (auto e : c->prof_pool) cudaEventDestroy(e);
+      cudaFree(c->arena);
+      cudaFreeHost(c->hscal);
+      delete c;
+    }
+    cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> threads;
+  const int nw = nworkers < npairs ? nworkers : (npairs > 0 ? npairs : 1);
+  for (int w = 0; w < nw; ++w) threads.emplace_back(worker);
+  for (auto& t : threads) t.join();
+  if (cudaDeviceSynchronize() != cudaSuccess) return CLAIRE_ECUDA;
+  return (claire_status)first_error.load();
+}
+
 claire_status claire_departure_f32(claire_ctx* c, const float* v, int dir, float* disp, void* s) {
   return api_departure<float>(c, v, dir, disp, s);
 }

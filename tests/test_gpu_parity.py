@@ -401,3 +401,25 @@ def test_bf16_gradient_history_errors_against_the_oracle(h2_phantom48):
     assert abs(rep16["gn_iters"] - rep_ref.gn_iters) <= 1
     assert abs(rep16["mismatch"] - rep_ref.mismatch) <= 2e-2 * rep_ref.mismatch
     assert rel(v16, v_ref) < 2e-2
+
+
+# ------------------------------------------------------------------------------------------------------ batched form
+def test_register_batch_matches_single_solves_on_uneven_grids():
+    """claire_register_batch_f32 (several workers, pairs of different grids) reproduces the single-pair solves
+    exactly: same kernels and summation order on every stream."""
+    import paper_1808_04487_gb300 as pkg
+    kw = dict(beta=5e-3, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2)
+    grids = [(32, 32, 32), (24, 28, 20), (32, 32, 32), (16, 24, 32), (24, 28, 20)]
+    pairs, singles = [], []
+    for i, n in enumerate(grids):
+        atlas = dev(I.brain_phantom(n, seed=100), "f32")
+        vs = dev(I.random_velocity(n, seed=i, kmax=5, max_disp_voxels=1.5), "f32")
+        with ctx(n, "f32", **kw) as c:
+            mT = c.transport(atlas, vs, +1)
+            v1, rep1, st1 = c.register(mT, atlas)
+        singles.append((v1.clone(), rep1, st1))
+        pairs.append((mT, atlas, torch.zeros((3,) + n, dtype=torch.float32, device="cuda")))
+    out = pkg.register_batch(pairs, nworkers=3, **kw)
+    for (mT, mR, v), (rep, st), (v1, rep1, st1) in zip(pairs, out, singles):
+        assert st == st1 and rep["gn_iters"] == rep1["gn_iters"] and rep["matvecs"] == rep1["matvecs"]
+        assert torch.equal(v, v1)
