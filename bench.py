@@ -38,10 +38,20 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "batch"],
+    ap.add_argument("--study", default=None, choices=[None, "precision", "batch", "warmstart"],
                     help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path; batch: 64 "
-                         "population-to-atlas pairs on uneven grids, batched vs sequential (own JSON lines)")
+                         "population-to-atlas pairs on uneven grids, batched vs sequential; warmstart: train the "
+                         "warm-start network on solver outputs, then warm- vs zero-start solves (own JSON lines)")
     ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--ws-count", type=int, default=2000, help="warmstart: training triples")
+    ap.add_argument("--ws-solve", type=int, default=128, help="warmstart: grid of the training solves")
+    ap.add_argument("--ws-steps", type=int, default=4000, help="warmstart: Adam steps")
+    ap.add_argument("--ws-batch", type=int, default=8, help="warmstart: minibatch")
+    ap.add_argument("--ws-lr", type=float, default=1e-3)
+    ap.add_argument("--ws-eval", type=int, default=16, help="warmstart: held-out pairs on the training grid")
+    ap.add_argument("--ws-eval256", type=int, default=4, help="warmstart: held-out pairs at 256^3")
+    ap.add_argument("--ws-fp64", type=int, default=4, help="warmstart: held-out pairs also solved in FP64")
+    ap.add_argument("--ws-kmax", default="0,8,6", help="warmstart: spectral cutoffs of the prediction to compare")
     return ap.parse_args()
 
 
@@ -385,12 +395,143 @@ def batch_study(args):
     return 0
 
 
+def warmstart_study(args):
+    """Learned warm start: a training set of (m_T, m_R, v) triples made by the plain solver on ws_solve^3 (seeded
+    phantoms, divergence-free band-limited v*, |k| <= 6, the 8-voxels-at-256^3 amplitude), the network trained on
+    their 32^3 spectral truncations, then held-out pairs (unseen phantom seeds and velocities) solved from v = 0
+    and from the network's prediction with the same stopping rule ||g|| <= 1e-2 ||g(v=0)||."""
+    import numpy as np
+    import torch
+
+    import claire_inputs as I
+    import paper_1808_04487_gb300 as pkg
+    from paper_1808_04487_gb300 import warmstart as WS
+
+    torch.cuda.set_device(0)
+
+    def log(msg):
+        print(msg, file=sys.stderr, flush=True)
+
+    n_net = (32, 32, 32)
+    n_tr = (args.ws_solve,) * 3
+    t0 = time.perf_counter()
+    images, targets, gen = WS.make_training_set(args.ws_count, n_solve=n_tr, n_net=n_net, seed=0, phantoms=64,
+                                                beta=SOLVER_KW["beta"], regnorm=SOLVER_KW["regnorm"],
+                                                divfree=SOLVER_KW["divfree"], nt=SOLVER_KW["nt"],
+                                                gtol_rel=SOLVER_KW["gtol_rel"], log=log)
+    t_gen = time.perf_counter() - t0
+    nval = max(8, args.ws_count // 20)
+    tr_img, tr_tgt = images[:-nval], targets[:-nval]
+    va_img, va_tgt = images[-nval:].contiguous(), targets[-nval:].contiguous()
+    rms = float(tr_tgt.pow(2).mean().sqrt())
+    ws = WS.WarmStart(n_net, batch=args.ws_batch, vscale=1.0 / rms, seed=0)
+    val0 = WS.evaluate(ws, va_img, va_tgt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = WS.train(ws, tr_img, tr_tgt, args.ws_steps, lr=args.ws_lr, lr_final=args.ws_lr / 30.0, seed=0,
+                      val=(va_img, va_tgt), log=log, log_every=max(1, args.ws_steps // 10))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val1 = WS.evaluate(ws, va_img, va_tgt)
+    train1 = WS.evaluate(ws, tr_img[: 8 * nval].contiguous(), tr_tgt[: 8 * nval].contiguous())
+    del images, targets, tr_img, tr_tgt
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - a
+
+    def evaluate_grid(n, count, nfp64):
+        ctx = pkg.Context(n, precision="f32", **SOLVER_KW)
+        ctx_net = pkg.Context(n_net, precision="f32")
+        ctx64 = pkg.Context(n, precision="f64", **SOLVER_KW) if nfp64 else None
+        disp_net = 8.0 * max(n_net) / 256.0
+        rows = []
+        for j in range(count):
+            mT = torch.from_numpy(I.brain_phantom(n, seed=500009 + 7 * j)).float().cuda()
+            vs = I.random_velocity(n_net, seed=900001 + 13 * j, kmax=6, max_disp_voxels=disp_net, divfree=True)
+            vs = ctx_net.resample_to(ctx, torch.from_numpy(vs).float().cuda().contiguous())
+            mR = ctx.transport(mT, vs, +1)
+            if j == 0:
+                ctx.register(mT, mR)  # warm-up of this grid's contexts and gather autotuner
+            (vz, rz, sz), tz = timed(lambda: ctx.register(mT, mR))
+            row = {"zero": {"status": sz, "seconds": tz, **{k: rz[k] for k in ("gn_iters", "matvecs", "pde_solves")},
+                            "rel_mismatch": rz["mismatch"] / rz["mismatch0"], "rel_grad": rz["gnorm"] / rz["gnorm0"]}}
+            # the best a network on the 32^3 grid can do: the zero-start solution itself, truncated to that grid
+            vt = ctx_net.resample_to(ctx, ctx.resample_to(ctx_net, vz), project=SOLVER_KW["divfree"])
+            (_, rt, st_), tt = timed(lambda: ctx.register(mT, mR, vt.clone()))
+            row["truncated_solution"] = {"status": st_, "seconds": tt,
+                                         **{k: rt[k] for k in ("gn_iters", "matvecs", "pde_solves")},
+                                         "rel_mismatch": rt["mismatch"] / rz["mismatch0"],
+                                         "prediction_rel_error": float((vt - vz).norm() / vz.norm())}
+            for km in kmaxes:
+                v0, tp = timed(lambda: ws.predict(ctx, mT, mR, kmax=km))
+                (vw, rw, sw), tw = timed(lambda: ctx.register(mT, mR, v0.clone()))
+                row["warm_k%d" % km] = {"status": sw, "seconds": tw + tp, "predict_seconds": tp,
+                                        **{k: rw[k] for k in ("gn_iters", "matvecs", "pde_solves")},
+                                        "rel_mismatch": rw["mismatch"] / rz["mismatch0"],
+                                        "rel_grad": rw["gnorm"] / rw["gnorm0"],
+                                        "J0_over_zero_J0": rw["J0"] / rz["J0"],
+                                        "prediction_rel_error": float((v0 - vz).norm() / vz.norm())}
+            if j < nfp64:
+                mT64, mR64 = mT.double(), mR.double()
+                (v64, r64, s64), t64 = timed(lambda: ctx64.register(mT64, mR64))
+                row["zero_fp64"] = {"status": s64, "seconds": t64,
+                                    **{k: r64[k] for k in ("gn_iters", "matvecs", "pde_solves")},
+                                    "rel_mismatch": r64["mismatch"] / r64["mismatch0"]}
+            rows.append(row)
+            log("%s pair %d: zero %d GN %d mv %.3fs | " % (n, j, rz["gn_iters"], rz["matvecs"], tz) + " | ".join(
+                "k%d: %d GN %d mv %.3fs err %.3f" % (km, row["warm_k%d" % km]["gn_iters"],
+                                                     row["warm_k%d" % km]["matvecs"], row["warm_k%d" % km]["seconds"],
+                                                     row["warm_k%d" % km]["prediction_rel_error"]) for km in kmaxes))
+
+        keys = ["zero", "truncated_solution"] + ["warm_k%d" % km for km in kmaxes] + ["zero_fp64"]
+        summary = {}
+        for key in keys:
+            sel = [r[key] for r in rows if key in r]
+            if not sel:
+                continue
+            summary[key] = {sub: float(np.mean([x[sub] for x in sel])) for sub in sel[0] if sub != "status"}
+            summary[key]["converged"] = sum(1 for x in sel if x["status"] == "OK")
+        for km in kmaxes:
+            w = summary["warm_k%d" % km]
+            w["speedup_vs_zero_fp32"] = summary["zero"]["seconds"] / w["seconds"]
+            w["matvec_ratio"] = w["matvecs"] / summary["zero"]["matvecs"]
+            if "zero_fp64" in summary:
+                w["speedup_vs_zero_fp64"] = summary["zero_fp64"]["seconds"] / w["seconds"]
+        ctx.close()
+        ctx_net.close()
+        if ctx64 is not None:
+            ctx64.close()
+        return {"n": list(n), "pairs": count, "summary": summary}
+
+    kmaxes = [int(k) for k in args.ws_kmax.split(",") if k.strip()]
+    evals = [evaluate_grid(n_tr, args.ws_eval, args.ws_fp64)]
+    if args.ws_eval256 > 0 and args.ws_solve != 256:
+        evals.append(evaluate_grid((256, 256, 256), args.ws_eval256, min(args.ws_fp64, 2)))
+    print(json.dumps({"study": "warmstart", "network": {"grid": list(n_net), "params": ws.num_params,
+                                                         "batch": args.ws_batch, "vscale": ws.vscale},
+                      "training_set": {"count": args.ws_count, "grid": list(n_tr), "seconds": t_gen,
+                                       "converged": gen["converged"], "mean_gn": float(np.mean(gen["gn_iters"])),
+                                       "mean_matvecs": float(np.mean(gen["matvecs"]))},
+                      "training": {"steps": args.ws_steps, "seconds": t_train, "lr": args.ws_lr,
+                                   "val_loss_initial": val0, "val_loss_final": val1, "train_loss_final": train1,
+                                   "curve": losses[:: max(1, len(losses) // 20)]},
+                      "solver": SOLVER_KW, "eval": evals}), flush=True)
+    ws.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.study == "precision":
         return precision_study(args)
     if args.study == "batch":
         return batch_study(args)
+    if args.study == "warmstart":
+        return warmstart_study(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -158,8 +158,9 @@ claire_status claire_precond_f32(claire_ctx* ctx, const float* r, float* z, void
 claire_status claire_precond_f64(claire_ctx* ctx, const double* r, double* z, void* stream);
 
 /* ---- full inexact Gauss-Newton-Krylov solve (Alg. 1 with Alg. 2, Armijo line search, Sec. 2.3.2) -------------
- * v is in/out: on entry the initial guess (zeros = the plain method), on return the solution. The relative
- * stopping test always uses ||g(v = 0)|| (Sec. 2.3.2), also for a nonzero initial guess. rep (host) may be NULL.
+ * v is in/out: on entry the initial guess (zeros = the plain method), on return the solution. With div v = 0 a
+ * nonzero guess is first Leray-projected (Sec. 2.2). The relative stopping test always uses ||g(v = 0)||
+ * (Sec. 2.3.2), also for a nonzero initial guess. rep (host) may be NULL.
  * Returns CLAIRE_OK on convergence, CLAIRE_ENOTCONV when max_gn is reached, CLAIRE_ELINESEARCH when Armijo
  * fails (v = last accepted iterate), CLAIRE_ENAN on a non-finite objective or gradient. Synchronises stream. */
 claire_status claire_register_f32(claire_ctx* ctx, const float* mT, const float* mR, float* v, claire_report* rep,
@@ -252,6 +253,101 @@ claire_status claire_dot_noalloc_f32(const float* a, const float* b, long long c
  * (truncated to len bytes, NUL-terminated), and clears the records. Enabling adds two event records per launch. */
 claire_status claire_profile_enable(claire_ctx* ctx, int on);
 claire_status claire_profile_report(claire_ctx* ctx, char* buf, size_t len);
+
+/* ============================================================================================================
+ * Spectral resampling and the learned warm start. Neither is part of the paper's method: the network only
+ * proposes the initial guess v_0 of Alg. 1, and the solve that follows is the unchanged Gauss-Newton-Krylov
+ * method with ||g(v = 0)|| in its relative stopping test (Sec. 2.3.2). All pointers below are device pointers
+ * unless marked (host); calls are asynchronous on `stream` unless they return a host value.
+ * ============================================================================================================ */
+
+/* g = f resampled from src's grid to dst's grid by truncating or zero-padding its Fourier series: a mode with
+ * signed wavenumber w is kept iff 2|w_i| < n_i on both grids for every axis (Nyquist modes are dropped), so a
+ * trigonometric polynomial of degree below half of both grids is reproduced exactly. f is [ncomp][N_src], g is
+ * [ncomp][N_dst] (planar). kmax > 0 also drops every mode with some |w_i| > kmax (a spectral low-pass; 0: none).
+ * project = 1 (ncomp = 3 only) applies the Leray projection of Sec. 2.2 on dst's grid.
+ * Both contexts must be FP32; their internal work arrays are used (no other call on either context meanwhile;
+ * src == dst is allowed). */
+claire_status claire_resample_f32(claire_ctx* src, claire_ctx* dst, const float* f, float* g, int ncomp, int project,
+                                  int kmax, void* stream);
+
+/* Warm-start network: a 3D encoder-decoder with four levels (16, 32, 64, 128 channels; two periodic 3x3x3
+ * convolutions + ReLU per level, 2x2x2 average pooling, nearest-neighbour upsampling, additive skips; a linear
+ * 16-channel head of which channels 0..2 are the velocity, scaled by vscale). It runs on a coarse network grid
+ * n (each n_i a multiple of 8, (n1/8)(n2/8)(n3/8) a multiple of 16) for up to `batch` samples at a time. BF16
+ * weights and activations, FP32 accumulation on the tensor cores, FP32 master weights, gradients and Adam state.
+ * The handle owns its device memory and an FP32 claire_ctx on the network grid; it is not thread-safe. */
+typedef struct claire_ws claire_ws;
+claire_status claire_ws_create(int batch, int n1, int n2, int n3, float vscale, unsigned long long seed,
+                               claire_ws** out);
+claire_status claire_ws_destroy(claire_ws* ws);
+const char* claire_ws_last_error(const claire_ws* ws);
+/* Parameters in host order: for each layer, weights [Cout][27][Cin] (offset 9(o1+1)+3(o2+1)+(o3+1) for the
+ * neighbour at (i1+o1, i2+o2, i3+o3)) then bias [Cout]. */
+long long claire_ws_num_params(const claire_ws* ws);
+int claire_ws_num_layers(const claire_ws* ws);
+/* info[8] (host) = {Cin used, Cin stored, Cout, level, relu, input tensor, output tensor (-1: prediction),
+ * skip tensor (-1: none)} */
+claire_status claire_ws_layer(const claire_ws* ws, int i, int* info);
+int claire_ws_num_ops(const claire_ws* ws);
+/* info[4] (host) = {kind (0 conv, 1 pool, 2 upsample), layer (conv only), input tensor, output tensor} */
+claire_status claire_ws_op(const claire_ws* ws, int i, int* info);
+/* host copies (synchronise the device); set_params also resets the Adam state */
+claire_status claire_ws_get_params(claire_ws* ws, float* host_params);
+claire_status claire_ws_set_params(claire_ws* ws, const float* host_params);
+claire_status claire_ws_get_grads(claire_ws* ws, float* host_grads);
+/* Samples are rows of images [S][2][N] (m_T, m_R; planar on the network grid) and targets [S][3][N] (v); idx
+ * (host, nb entries) selects rows, NULL means rows 0..nb-1; nb <= batch. v_out is [nb][3][N] (planar, physical
+ * units). The loss is the mean squared error of vscale v over all voxels and 3 components; with backward = 1
+ * the parameter gradients are formed (claire_ws_get_grads). loss (host, optional) synchronises the stream. */
+claire_status claire_ws_forward_f32(claire_ws* ws, const float* images, const int* idx, int nb, float* v_out,
+                                    void* stream);
+claire_status claire_ws_loss_f32(claire_ws* ws, const float* images, const float* targets, const int* idx, int nb,
+                                 int backward, double* loss, void* stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the current gradients */
+claire_status claire_ws_adam_step(claire_ws* ws, float lr, void* stream);
+/* loss + gradients + Adam step; loss (host, optional) is the loss before the step */
+claire_status claire_ws_train_step_f32(claire_ws* ws, const float* images, const float* targets, const int* idx,
+                                       int nb, float lr, double* loss, void* stream);
+/* v = the network's velocity for (mT, mR) on ctx's grid: both images resampled to the network grid, one forward
+ * pass, the prediction resampled back with modes |w_i| <= kmax (kmax <= 0: all the network grid holds), and
+ * Leray-projected when ctx imposes div v = 0. ctx must be FP32. v can be passed as the initial guess of
+ * claire_register_f32. */
+claire_status claire_ws_predict_f32(claire_ws* ws, claire_ctx* ctx, const float* mT, const float* mR, float* v,
+                                    int kmax, void* stream);
+
+/* The network's layers one by one (used to check each against a reference). BF16 tensors are passed as void*,
+ * channels-last [B][n1][n2][n3][C]; C, Cin, Cout multiples of 16 in [16, 128]; B n1 n2 n3 a multiple of 16.
+ * conv3_fwd: y (BF16) and/or yf (FP32; overwritten, or added to with accum = 1) = act(conv(x, w) + bias + skip),
+ * w [Cout][27][Cin]; bias, skip, y, yf optional (y or yf required). conv3_wgrad: dw[Cout][27][Cin] =
+ * sum over voxels of dz[m][co] x[nb(m, off)][ci] (work: claire_nn_wgrad_workspace_bytes). weight_flip: wt =
+ * the weights of the adjoint convolution, [Cin][27][Cout]. relu_bwd: dz = dy where y > 0 (y NULL: everywhere),
+ * FP32 dz and BF16 dzb. bias_grad: db[c] = sum_m dz[m][c] (work: claire_nn_bias_workspace_bytes). pool: 2x2x2
+ * average over the fine grid (n1, n2, n3 even) and its adjoint; up: nearest-neighbour x2 from the coarse grid
+ * (n1, n2, n3) and its adjoint (accum = 1 adds to dx). mse: loss partials (FP64, npartials blocks) of the mean
+ * squared error over the first cu of C channels, grad (optional) = d loss / d pred. adam: one bias-corrected Adam
+ * step number `step` >= 1; pb (optional) receives a BF16 copy of p. */
+claire_status claire_nn_conv3_fwd(const void* x, const void* w, const float* bias, const void* skip, void* y,
+                                  float* yf, int accum, int B, int n1, int n2, int n3, int Cin, int Cout, int relu,
+                                  void* stream);
+size_t claire_nn_wgrad_workspace_bytes(int B, int n1, int n2, int n3, int Cin, int Cout);
+claire_status claire_nn_conv3_wgrad(const void* dz, const void* x, float* dw, float* work, int B, int n1, int n2,
+                                    int n3, int Cin, int Cout, void* stream);
+claire_status claire_nn_weight_flip(const void* w, void* wt, int Cin, int Cout, void* stream);
+claire_status claire_nn_relu_bwd(const float* dy, const void* y, float* dz, void* dzb, long long count,
+                                 void* stream);
+size_t claire_nn_bias_workspace_bytes(int C);
+claire_status claire_nn_bias_grad(const float* dz, long long M, int C, float* db, float* work, void* stream);
+claire_status claire_nn_pool_fwd(const void* x, void* y, int B, int n1, int n2, int n3, int C, void* stream);
+claire_status claire_nn_pool_bwd(const float* dy, float* dx, int accum, int B, int n1, int n2, int n3, int C,
+                                 void* stream);
+claire_status claire_nn_up_fwd(const void* x, void* y, int B, int n1, int n2, int n3, int C, void* stream);
+claire_status claire_nn_up_bwd(const float* dy, float* dx, int accum, int B, int n1, int n2, int n3, int C,
+                               void* stream);
+claire_status claire_nn_mse(const float* pred, const float* target, float* grad, long long M, int C, int cu,
+                            double* partials, int npartials, void* stream);
+claire_status claire_nn_adam(float* p, const float* g, float* m1, float* m2, void* pb, long long count, float lr,
+                             float b1, float b2, float eps, int step, void* stream);
 
 #ifdef __cplusplus
 }

@@ -427,6 +427,9 @@ def register(prob, mT, mR, v0=None):
     rep.gnorm0 = norm(grid, g0)
     rep.pde_solves += 2
     if v0 is not None and np.any(v != 0):
+        if prob.divfree:
+            # the control space is divergence-free (Sec. 2.2): a nonzero initial guess is projected onto it
+            v = leray(grid, v)
         lin = linearize(prob, mT, v)
         g = reduced_gradient(prob, lin, mR)
         rep.pde_solves += 2

@@ -14,7 +14,8 @@ module computes is therefore fixed by the network's specification, restated here
 * Network (channel counts in/out): e0 16/16, 16/16 | pool | e1 16/32, 32/32 | pool | e2 32/64, 64/64 | pool |
   b 64/128, 128/128 | up | d2 128/64 (+ e2's output), 64/64 | up | d1 64/32 (+ e1's), 32/32 | up |
   d0 32/16 (+ e0's), 16/16 | head 16/16. ReLU after every convolution except the head; a skip is added before
-  the ReLU. Input channels: (m_T, m_R, 0, ..., 0); the velocity is channels 0..2 of the head divided by vscale.
+  the ReLU. Input channels: (m_T, 8 (m_R - m_T), 0, ..., 0); the velocity is channels 0..2 of the head divided
+  by vscale.
 * Loss: mean over voxels and the 3 velocity channels of (head - vscale v)^2.
 * Adam: Kingma and Ba (2015), Algorithm 1, with bias-corrected first and second moments.
 * Resampling: Fourier truncation / zero padding. A mode of signed wavenumber w is kept iff 2 |w_a| < n_a on both
@@ -129,12 +130,15 @@ def num_params():
     return sum(27 * cin * cout + cout for (_, cin, cout, _, _, _) in layer_table())
 
 
+DIFF_SCALE = 8.0
+
+
 def pack_input(images):
-    """images [B][2][n1][n2][n3] (m_T, m_R) -> x [B][n1][n2][n3][16] with channels 2..15 zero."""
+    """images [B][2][n1][n2][n3] (m_T, m_R) -> x [B][n1][n2][n3][16]: m_T, 8 (m_R - m_T), then zeros."""
     B = images.shape[0]
     x = np.zeros((B,) + images.shape[2:] + (16,))
     x[..., 0] = images[:, 0]
-    x[..., 1] = images[:, 1]
+    x[..., 1] = DIFF_SCALE * (images[:, 1] - images[:, 0])
     return x
 
 
@@ -231,25 +235,28 @@ def adam_step(p, g, m1, m2, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return p - lr * mhat / (np.sqrt(vhat) + eps), m1, m2
 
 
-def _kept(n_src, n_dst):
+def _kept(n_src, n_dst, kmax=0):
     """Signed wavenumbers kept along a full (non-halved) axis."""
     top = (min(n_src, n_dst) - 1) // 2
+    if kmax > 0:
+        top = min(top, kmax)
     return np.arange(-top, top + 1)
 
 
-def resample(f, n_dst):
-    """Scalar field f on grid f.shape -> grid n_dst by Fourier truncation / zero padding."""
+def resample(f, n_dst, kmax=0):
+    """Scalar field f on grid f.shape -> grid n_dst by Fourier truncation / zero padding; kmax > 0 also drops
+    every mode with some |k_a| > kmax."""
     n_src = f.shape
     F = np.fft.fftn(f)
     G = np.zeros(tuple(n_dst), dtype=complex)
-    k1, k2, k3 = (_kept(n_src[a], n_dst[a]) for a in range(3))
+    k1, k2, k3 = (_kept(n_src[a], n_dst[a], kmax) for a in range(3))
     G[np.ix_(k1 % n_dst[0], k2 % n_dst[1], k3 % n_dst[2])] = F[np.ix_(k1 % n_src[0], k2 % n_src[1], k3 % n_src[2])]
     scale = np.prod(n_dst) / np.prod(n_src)
     return np.real(np.fft.ifftn(G)) * scale
 
 
-def resample_vector(v, n_dst, project=False):
-    out = np.stack([resample(v[c], n_dst) for c in range(v.shape[0])])
+def resample_vector(v, n_dst, project=False, kmax=0):
+    out = np.stack([resample(v[c], n_dst, kmax) for c in range(v.shape[0])])
     if project:
         out = leray(out)
     return out

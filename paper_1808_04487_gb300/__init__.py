@@ -85,6 +85,45 @@ _TYPED = {
     "claire_ifft": [_VP, _VP, _VP],
 }
 
+_PI = ctypes.POINTER(ctypes.c_int)
+_PF = ctypes.POINTER(ctypes.c_float)
+_F = ctypes.c_float
+_SZ = ctypes.c_size_t
+
+# resampling, the warm-start network and its layers: symbol -> (return type, argument types)
+_UNTYPED = {
+    "claire_resample_f32": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _VP]),
+    "claire_ws_create": (_I, [_I, _I, _I, _I, _F, ctypes.c_ulonglong, ctypes.POINTER(_VP)]),
+    "claire_ws_destroy": (_I, [_VP]),
+    "claire_ws_last_error": (ctypes.c_char_p, [_VP]),
+    "claire_ws_num_params": (_LL, [_VP]),
+    "claire_ws_num_layers": (_I, [_VP]),
+    "claire_ws_layer": (_I, [_VP, _I, _PI]),
+    "claire_ws_num_ops": (_I, [_VP]),
+    "claire_ws_op": (_I, [_VP, _I, _PI]),
+    "claire_ws_get_params": (_I, [_VP, _PF]),
+    "claire_ws_set_params": (_I, [_VP, _PF]),
+    "claire_ws_get_grads": (_I, [_VP, _PF]),
+    "claire_ws_forward_f32": (_I, [_VP, _VP, _PI, _I, _VP, _VP]),
+    "claire_ws_loss_f32": (_I, [_VP, _VP, _VP, _PI, _I, _I, _PD, _VP]),
+    "claire_ws_adam_step": (_I, [_VP, _F, _VP]),
+    "claire_ws_train_step_f32": (_I, [_VP, _VP, _VP, _PI, _I, _F, _PD, _VP]),
+    "claire_ws_predict_f32": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _VP]),
+    "claire_nn_conv3_fwd": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_wgrad_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I, _I]),
+    "claire_nn_conv3_wgrad": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_weight_flip": (_I, [_VP, _VP, _I, _I, _VP]),
+    "claire_nn_relu_bwd": (_I, [_VP, _VP, _VP, _VP, _LL, _VP]),
+    "claire_nn_bias_workspace_bytes": (_SZ, [_I]),
+    "claire_nn_bias_grad": (_I, [_VP, _LL, _I, _VP, _VP, _VP]),
+    "claire_nn_pool_fwd": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_pool_bwd": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_up_fwd": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_up_bwd": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_mse": (_I, [_VP, _VP, _VP, _LL, _I, _I, _VP, _I, _VP]),
+    "claire_nn_adam": (_I, [_VP, _VP, _VP, _VP, _VP, _LL, _F, _F, _F, _F, _I, _VP]),
+}
+
 _lib = None
 
 
@@ -122,6 +161,10 @@ def lib():
             f = getattr(L, base + sfx)
             f.argtypes = [_VP] + args
             f.restype = _I
+    for name, (res, args) in _UNTYPED.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
     _lib = L
     return L
 
@@ -359,3 +402,18 @@ class Context:
         c = Counters()
         lib().claire_get_counters(self._h, ctypes.byref(c))
         return int(c.launches)
+
+    def resample_to(self, dst, f, project=False, out=None, kmax=0):
+        """f ([ncomp,] n) on this grid -> dst's grid by Fourier truncation / zero padding (FP32 contexts)."""
+        vec = f.dim() == 4
+        nc = f.shape[0] if vec else 1
+        shape = ((nc,) if vec else ()) + dst.n
+        out = _torch().empty(shape, dtype=dst.dtype, device="cuda") if out is None else out
+        self._check(f, ((nc,) if vec else ()) + self.n, "f")
+        dst._check(out, shape, "out")
+        st = lib().claire_resample_f32(self._h, dst._h, ctypes.c_void_p(f.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), nc, int(bool(project)), int(kmax),
+                                       self._stream())
+        if st != OK:
+            raise ClaireError(st, lib().claire_last_error(dst._h).decode())
+        return out

@@ -493,6 +493,13 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
     double J = rep->mismatch0;
     if (vv > 0.0) {
       CL_TRY(vec_r2c<T>(c, v, W.Vh, st));
+      if (o.divfree) {
+        // The reduced space is divergence-free (Sec. 2.2): project the initial guess onto it and continue from
+        // the projected v. Without this, the curl-free part of v (for a nonzero guess at least its rounding
+        // error) stays in beta A v, where no projected Gauss-Newton step can remove it.
+        CL_TRY(spec_leray<T>(c, W.Vh, W.Vh + c->d.Ns, W.Vh + 2 * c->d.Ns, st));
+        CL_TRY(spec_to_phys<T>(c, W.Vh, v, st));
+      }
       CL_TRY(sp_copy_reg<T>(c, W.Vh, nullptr, W.partials, st));
       CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, 0.5 * o.beta * sc, W.scal + 5, st));
       CL_TRY(linearize<T>(c, mT, v, st));

@@ -467,3 +467,23 @@ def test_P12_bookkeeping_matches_the_papers_table():
     v, rep = O.register(p, mT, mR)
     assert rep.pde_solves == 2 * rep.matvecs + rep.gn_iters + rep.ls_trials + 2
     assert rep.J < rep.J0 and rep.gnorm < rep.gnorm0
+
+
+def test_P13_divfree_initial_guess_is_projected():
+    """Under div v = 0 the control space is divergence-free (Sec. 2.2): a guess v* + grad(phi) must behave exactly
+    like v*, because the Leray projection annihilates gradient fields. Restarting from the solution plus a
+    gradient field therefore needs no Gauss-Newton step and returns the solution."""
+    n = (12, 12, 12)
+    p = O.Problem(n, beta=1e-2, nt=4, regnorm=2, divfree=True, gtol_rel=1e-3)
+    mT = I.trig_image(n, 0)
+    mR = O.transport(p, mT, I.random_velocity(n, seed=1, kmax=2, amplitude=0.3, divfree=True), +1)
+    v, rep = O.register(p, mT, mR)
+    assert rep.converged
+    x1, x2, x3 = I.grid_coords(n)
+    X1, X2 = x1[:, None, None] + 0 * x3, x2[None, :, None] + 0 * x3
+    # phi = sin(x1) cos(2 x2): grad phi = (cos x1 cos 2x2, -2 sin x1 sin 2x2, 0)
+    grad_phi = np.stack([np.cos(X1) * np.cos(2 * X2), -2 * np.sin(X1) * np.sin(2 * X2), np.zeros(n)])
+    v2, rep2 = O.register(p, mT, mR, v + 0.05 * grad_phi)
+    assert rep2.converged and rep2.gn_iters == 0
+    assert np.abs(v2 - v).max() < 1e-12
+    assert abs(rep2.gnorm0 - rep.gnorm0) < 1e-12 * rep.gnorm0

@@ -169,6 +169,11 @@ def test_W8_resample_trig_polynomial():
     assert np.max(np.abs(g - _trig((16, 16, 16), [((1, 1, 1), 0.5, 0.0)]))) < 1e-12
     g = W.resample(_trig((32, 32, 32), [((8, 2, 0), 1.0, 0.0)]), (16, 16, 16))
     assert np.max(np.abs(g)) < 1e-12
+    # a low-pass cutoff keeps exactly the modes with every |k_a| <= kmax
+    f = _trig((24, 20, 16), coeffs)
+    g = W.resample(f, (24, 20, 16), kmax=3)
+    low = [c for c in coeffs if max(abs(k) for k in c[0]) <= 3]
+    assert np.max(np.abs(g - _trig((24, 20, 16), low))) < 1e-12
 
 
 def test_W9_leray():
