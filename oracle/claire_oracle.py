@@ -17,6 +17,10 @@ Discrete conventions (the readings of the paper that both this oracle and the CU
   symbol |k|^4); the penalty is (beta/2) sum_c <v_c, A v_c>.
 * Projection K (Sec. 2.2, after Eq. (5)): identity without the constraint; the Leray projector
   I - k' k'^T / |k'|^2 (identity where k' = 0) with div v = 0.
+* H1-div model (Sec. 2.1-2.2: H1 seminorm for v plus beta_w/2 ||div v||^2_H1 with w = div v in the objective):
+  K^ = I - q(k) k' k'^T, q = beta_w (|k|^2 + 1) / (beta_v |k|^2 + beta_w (|k|^2 + 1) |k'|^2) (the paper's K off
+  the Nyquist planes). Eq. (5) and (7) keep their form with this K; beta_v A + K H_data is self-adjoint in
+  <K^-1 a, b>, which PCG's kappa, mu and the Armijo slope <K^-1 g, dv> use; the stopping test uses ||g||.
 * Semi-Lagrangian transport (Sec. 2.3.1, Sec. 3.4): nodal time grid t_j = j dt, dt = 1/n_t; RK2 (Heun)
   characteristics X* = x - dt v(x), X = x - dt/2 (v(x) + v(X*)) for the state, and Y with -v for the adjoints;
   tricubic Lagrange interpolation on the 4^3 stencil b-1..b+2 around b = floor(xi), indices taken periodically.
@@ -130,6 +134,59 @@ def apply_K(grid, v, divfree):
     return leray(grid, v) if divfree else v
 
 
+def _h1div_coeff(grid, beta, beta_w):
+    """q(k) with K^ = I - q k' k'^T for the H1-div model (Sec. 2.2, the K following Eq. (5), A = -Lap).
+
+    The paper's K = I - grad (beta_v (beta_w (-Lap + I))^-1 + I)^-1 Lap^-1 div has, with first-order symbols k'
+    and even-order symbols k, the symbol I - c(k) k' k'^T / |k'|^2, c = beta_w (|k|^2 + 1) / (beta_v + beta_w
+    (|k|^2 + 1)). Written with |k'|^2 in the denominator's divergence term (equal off the Nyquist planes),
+    q = beta_w (|k|^2 + 1) / (beta_v |k|^2 + beta_w (|k|^2 + 1) |k'|^2), which makes K beta_v^-1 A^-1 the exact
+    inverse of the regularisation operator of the objective (see regularization_h1div)."""
+    ksq, kpsq = grid.ksq, grid.kpsq
+    den = beta * ksq + beta_w * (ksq + 1.0) * kpsq
+    return np.where(den > 0, beta_w * (ksq + 1.0) / np.where(den > 0, den, 1.0), 0.0)
+
+
+def _apply_rank1(grid, v, coeff, sign):
+    """v + sign F^-1[coeff k' (k' . F v)]."""
+    V = [grid.fft(v[c]) for c in range(3)]
+    kv = grid.KP[0] * V[0] + grid.KP[1] * V[1] + grid.KP[2] * V[2]
+    return np.stack([grid.ifft(V[c] + sign * coeff * grid.KP[c] * kv) for c in range(3)])
+
+
+def h1div_K(grid, v, beta, beta_w):
+    """K v of the H1-div model (near-incompressible, Sec. 2.1-2.2)."""
+    return _apply_rank1(grid, v, _h1div_coeff(grid, beta, beta_w), -1.0)
+
+
+def h1div_Kinv(grid, v, beta, beta_w):
+    """K^-1 v = v + F^-1[beta_w (|k|^2 + 1) / (beta_v |k|^2) k' (k' . F v)] (identity at k = 0)."""
+    ksq = grid.ksq
+    s = np.where(ksq > 0, beta_w * (ksq + 1.0) / (beta * np.where(ksq > 0, ksq, 1.0)), 0.0)
+    return _apply_rank1(grid, v, s, +1.0)
+
+
+def regularization_h1div(grid, v, beta_w):
+    """beta_w <w, (-Lap + I) w> with w = div v: twice the divergence penalty of the objective (Eq. (1))."""
+    w = divergence_spectral(grid, v)
+    return beta_w * inner(grid, w, w - laplacian_spectral(grid, w))
+
+
+def apply_Kp(prob, v):
+    """The K of Eq. (5) for the problem's model: identity, Leray, or the H1-div operator."""
+    if prob.beta_w > 0:
+        return h1div_K(prob.grid, v, prob.beta, prob.beta_w)
+    return apply_K(prob.grid, v, prob.divfree)
+
+
+def control_inner(prob, a, b):
+    """Inner product of the Newton system: <a, b>, or <K^-1 a, b> for the H1-div model. With it the operator
+    beta_v A + K H_data of Eq. (7) is self-adjoint, and <K^-1 g, dv> is the derivative of J along dv."""
+    if prob.beta_w > 0:
+        return inner(prob.grid, h1div_Kinv(prob.grid, a, prob.beta, prob.beta_w), b)
+    return inner(prob.grid, a, b)
+
+
 def precond(grid, r, beta, regnorm):
     """Spectral preconditioner M^-1 = (beta A)^-1 with the zero eigenvalue replaced by 1 (Sec. 2.3.3, Remark)."""
     a = reg_symbol(grid, regnorm)
@@ -211,6 +268,7 @@ class Problem:
     nt: int = 4
     regnorm: int = 1          # 1: H1 seminorm (A = -Lap), 2: H2 seminorm (A = Lap^2)
     divfree: bool = False     # div v = 0 via the Leray projection
+    beta_w: float = 0.0       # > 0: H1-div model, penalty beta_w/2 ||div v||_H1^2 (needs regnorm 1, no divfree)
     gtol_rel: float = 5e-2
     gtol_abs: float = 1e-6
     max_gn: int = 50
@@ -223,6 +281,8 @@ class Problem:
         self.grid = Grid(self.n)
         if self.nt < 1 or not (self.beta > 0):
             raise ValueError("nt >= 1 and beta > 0 required")
+        if self.beta_w < 0 or (self.beta_w > 0 and (self.divfree or self.regnorm != 1)):
+            raise ValueError("beta_w > 0 (H1-div) needs regnorm 1 and no div v = 0 constraint")
 
     def time_weights(self):
         dt = 1.0 / self.nt
@@ -287,10 +347,14 @@ def adjoint_integral(prob, lin, lam_final):
 
 
 def objective(prob, mR, m1, v):
-    """J = 1/2 <m_1 - m_R, m_1 - m_R> + beta/2 sum_c <v_c, A v_c> (Eq. (2), objective)."""
+    """J = 1/2 <m_1 - m_R, m_1 - m_R> + beta/2 sum_c <v_c, A v_c> (Eq. (2), objective), plus
+    beta_w/2 (<grad w, grad w> + <w, w>) with w = div v for the H1-div model."""
     g = prob.grid
     res = m1 - mR
-    return 0.5 * inner(g, res, res) + 0.5 * prob.beta * regularization_value(g, v, prob.regnorm)
+    J = 0.5 * inner(g, res, res) + 0.5 * prob.beta * regularization_value(g, v, prob.regnorm)
+    if prob.beta_w > 0:
+        J += 0.5 * regularization_h1div(g, v, prob.beta_w)
+    return J
 
 
 def reduced_gradient(prob, lin, mR):
@@ -298,7 +362,7 @@ def reduced_gradient(prob, lin, mR):
     g = prob.grid
     lam1 = mR - lin.m[prob.nt]
     b = adjoint_integral(prob, lin, lam1)
-    return prob.beta * apply_A(g, lin.v, prob.regnorm) + apply_K(g, b, prob.divfree)
+    return prob.beta * apply_A(g, lin.v, prob.regnorm) + apply_Kp(prob, b)
 
 
 def incremental_state(prob, lin, vt):
@@ -324,7 +388,7 @@ def hessvec(prob, lin, vt):
     g = prob.grid
     mt1 = incremental_state(prob, lin, vt)
     bt = adjoint_integral(prob, lin, -mt1)
-    return prob.beta * apply_A(g, vt, prob.regnorm) + apply_K(g, bt, prob.divfree)
+    return prob.beta * apply_A(g, vt, prob.regnorm) + apply_Kp(prob, bt)
 
 
 def transport(prob, m0, v, direction=+1):
@@ -371,20 +435,23 @@ class Report:
 
 
 def pcg(prob, lin, g_k, eps_H, report):
-    """Alg. 2: PCG on H v~ = -g with the spectral preconditioner; break when ||r|| < eps_H ||r_0||."""
+    """Alg. 2: PCG on H v~ = -g with the spectral preconditioner; break when ||r|| < eps_H ||r_0||.
+
+    The inner products of kappa and mu are control_inner (the K^-1-weighted one for the H1-div model, where
+    H = beta_v A + K H_data is self-adjoint in it); the break test uses the plain norm of r."""
     grid = prob.grid
     vt = np.zeros_like(g_k)
     r = -g_k
     z = precond(grid, r, prob.beta, prob.regnorm)
     s = z.copy()
-    rz = inner(grid, r, z)
+    rz = control_inner(prob, r, z)
     r0 = norm(grid, r)
     it = 0
     while it < prob.max_krylov:
         Hs = hessvec(prob, lin, s)
         report.matvecs += 1
         report.pde_solves += 2
-        sHs = inner(grid, s, Hs)
+        sHs = control_inner(prob, Hs, s)
         if not (sHs > 0):
             if it == 0:
                 vt = s.copy()
@@ -396,7 +463,7 @@ def pcg(prob, lin, g_k, eps_H, report):
         if norm(grid, r) < eps_H * r0:
             break
         z = precond(grid, r, prob.beta, prob.regnorm)
-        rz_new = inner(grid, r, z)
+        rz_new = control_inner(prob, r, z)
         mu = rz_new / rz
         rz = rz_new
         s = z + mu * s
@@ -452,7 +519,7 @@ def register(prob, mT, mR, v0=None):
         vt = pcg(prob, lin, g, eps_H, rep)
         if prob.divfree:
             vt = leray(grid, vt)
-        gvt = inner(grid, g, vt)
+        gvt = control_inner(prob, g, vt)
         alpha = 1.0
         accepted = False
         for _ in range(prob.max_ls):

@@ -487,3 +487,96 @@ def test_P13_divfree_initial_guess_is_projected():
     assert rep2.converged and rep2.gn_iters == 0
     assert np.abs(v2 - v).max() < 1e-12
     assert abs(rep2.gnorm0 - rep.gnorm0) < 1e-12 * rep.gnorm0
+
+
+# ---------------------------------------------------------------------------------------------- H1-div model (P14)
+def _h1div_problem(n=(12, 12, 12), beta=1e-2, beta_w=1e-3):
+    return O.Problem(n, beta=beta, nt=4, regnorm=1, beta_w=beta_w)
+
+
+def test_P14_h1div_K_inverts_the_regularisation_of_the_objective():
+    """<v, K^-1 beta_v A v> must equal twice the regularisation of Eq. (2): beta_v <v, A v> + beta_w <w, (I - Lap) w>
+    with w = div v, computed from the spectral divergence and Laplacian (independent of K's formula)."""
+    p = _h1div_problem()
+    g = p.grid
+    v = I.random_velocity(g.n, seed=4, kmax=4, amplitude=1.0)
+    lhs = O.inner(g, v, O.h1div_Kinv(g, p.beta * O.apply_A(g, v, 1), p.beta, p.beta_w))
+    rhs = p.beta * O.regularization_value(g, v, 1) + O.regularization_h1div(g, v, p.beta_w)
+    assert abs(lhs - rhs) < 1e-12 * rhs
+    assert rel(O.h1div_K(g, O.h1div_Kinv(g, v, p.beta, p.beta_w), p.beta, p.beta_w), v) < 1e-13
+    # K is symmetric and positive definite with eigenvalues in (0, 1]
+    w = I.random_velocity(g.n, seed=5, kmax=4, amplitude=1.0)
+    Kv = O.h1div_K(g, v, p.beta, p.beta_w)
+    assert abs(O.inner(g, Kv, w) - O.inner(g, v, O.h1div_K(g, w, p.beta, p.beta_w))) < 1e-12 * O.norm(g, v) * O.norm(g, w)
+    assert 0 < O.inner(g, Kv, v) <= O.inner(g, v, v)
+
+
+def test_P14_h1div_limits_are_leray_and_identity():
+    g = O.Grid((12, 10, 8))
+    v = I.random_velocity(g.n, seed=6, kmax=3, amplitude=1.0)
+    assert rel(O.h1div_K(g, v, 1e-2, 1e6), O.leray(g, v)) < 1e-6
+    assert rel(O.h1div_K(g, v, 1e-2, 1e-12), v) < 1e-9
+    # a divergence-free field is unchanged for any beta_w
+    assert rel(O.h1div_K(g, O.leray(g, v), 1e-2, 3e-3), O.leray(g, v)) < 1e-13
+
+
+def test_P14_h1div_closed_form_at_zero_and_gradient_fd():
+    p = _h1div_problem((16, 16, 16))
+    g = p.grid
+    mT = I.trig_image(g.n, 0)
+    mR = I.trig_image(g.n, 100)
+    lin0 = O.linearize(p, mT, np.zeros((3,) + g.n))
+    g0 = O.reduced_gradient(p, lin0, mR)
+    gm = lin0.gradm[0]
+    assert rel(g0, O.h1div_K(g, (mR - mT) * gm, p.beta, p.beta_w)) < 1e-13
+    # <K^-1 g, dv> is the derivative of J (with the divergence penalty) along dv, to discretization level
+    out = []
+    for nn in (16, 32):
+        p = _h1div_problem((nn, nn, nn))
+        mT = I.trig_image(p.n, 0)
+        mR = I.trig_image(p.n, 100)
+        v = I.random_velocity(p.n, seed=1, kmax=2, amplitude=0.3)
+        vt = I.random_velocity(p.n, seed=2, kmax=2, amplitude=1.0)
+        gv = O.reduced_gradient(p, O.linearize(p, mT, v), mR)
+        eps = 1e-4
+        fd = (O.evaluate(p, mT, mR, v + eps * vt)[0] - O.evaluate(p, mT, mR, v - eps * vt)[0]) / (2 * eps)
+        out.append(abs(fd - O.control_inner(p, gv, vt)) / abs(fd))
+        plain = abs(fd - O.inner(p.grid, gv, vt)) / abs(fd)
+    assert out[1] < out[0] and out[1] < 2e-2
+    # the plain <g, dv> is not the derivative: without the K^-1 weighting it misses the divergence penalty
+    assert plain > 5 * out[1]
+
+
+def test_P14_h1div_dense_system_at_zero():
+    """At v = 0 the data Hessian is symmetric, so K^-1 H (H = beta_v A + K H_data, Eq. (7)) is a symmetric PSD
+    matrix, and PCG with the K^-1-weighted products reaches the dense solution of H dv = -g."""
+    p = _h1div_problem((8, 8, 8), beta=1e-2, beta_w=1e-2)
+    g = p.grid
+    mT = I.trig_image(g.n, 0, kmax=2)
+    mR = I.trig_image(g.n, 1, kmax=2)
+    lin0 = O.linearize(p, mT, np.zeros((3,) + g.n))
+    n = 3 * g.N
+    H = np.empty((n, n))
+    KH = np.empty((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        col = O.hessvec(p, lin0, e.reshape((3,) + g.n))
+        H[:, i] = col.ravel()
+        KH[:, i] = O.h1div_Kinv(g, col, p.beta, p.beta_w).ravel()
+    assert np.abs(KH - KH.T).max() < 1e-11 * np.abs(KH).max()
+    assert np.abs(H - H.T).max() > 1e-3 * np.abs(H).max()   # H itself is not symmetric
+    assert np.linalg.eigvalsh(0.5 * (KH + KH.T)).min() > -1e-12 * np.abs(KH).max()
+    g0 = O.reduced_gradient(p, lin0, mR)
+    rep = O.Report()
+    p.max_krylov = 500
+    vt = O.pcg(p, lin0, g0, 1e-10, rep)
+    assert rel(vt.ravel(), np.linalg.solve(H, -g0.ravel())) < 1e-7
+
+
+def test_P14_h1div_register_converges():
+    p = O.Problem((16, 16, 16), beta=1e-2, nt=4, regnorm=1, beta_w=1e-4, gtol_rel=1e-2)
+    mT = I.trig_image(p.n, 0)
+    mR = O.transport(p, mT, I.random_velocity(p.n, seed=3, kmax=2, amplitude=0.3), +1)
+    v, rep = O.register(p, mT, mR)
+    assert rep.converged and rep.gnorm <= 1e-2 * rep.gnorm0 and rep.J < rep.J0
