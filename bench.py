@@ -38,10 +38,13 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "batch", "warmstart"],
+    ap.add_argument("--study", default=None, choices=[None, "precision", "batch", "warmstart", "models"],
                     help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path; batch: 64 "
                          "population-to-atlas pairs on uneven grids, batched vs sequential; warmstart: train the "
-                         "warm-start network on solver outputs, then warm- vs zero-start solves (own JSON lines)")
+                         "warm-start network on solver outputs, then warm- vs zero-start solves; models: the H1-div "
+                         "model on the closed-form synthetic problem at several grids and continuation in beta "
+                         "(own JSON lines)")
+    ap.add_argument("--model-sizes", default="128,256,512", help="models: grids of the synthetic H1-div runs")
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--ws-count", type=int, default=2000, help="warmstart: training triples")
     ap.add_argument("--ws-solve", type=int, default=128, help="warmstart: grid of the training solves")
@@ -524,6 +527,85 @@ def warmstart_study(args):
     return 0
 
 
+def models_study(args):
+    """(1) The H1-div model (H1 seminorm, beta_v = 1e-3, divergence penalty beta_w = 1e-4) on the closed-form
+    synthetic problem of Sec. 4.2, FP32 to ||g|| <= 1e-2 ||g(0)||, at each grid of --model-sizes: the configuration
+    of Tab. 4 (which used the two-level preconditioner on a CPU cluster; here the spectral one on one GPU).
+    (2) Parameter continuation in beta_v (Sec. 3.6: 1, 1e-1, 1e-2, 1e-3) against the direct solve, H1-div
+    beta_w = 1e-4, on the brain phantom at 256^3 to ||g|| <= 5e-2 ||g(0)|| (the tolerance of Tab. 3)."""
+    import numpy as np
+    import torch
+
+    import claire_inputs as I
+    import paper_1808_04487_gb300 as pkg
+
+    torch.cuda.set_device(0)
+
+    def log(msg):
+        print(msg, file=sys.stderr, flush=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - a
+
+    keys = ("gn_iters", "matvecs", "pde_solves", "ls_trials", "converged")
+    synth = []
+    kw = dict(beta=1e-3, nt=4, regnorm=1, beta_w=1e-4, gtol_rel=1e-2)
+    for nn in [int(x) for x in args.model_sizes.split(",") if x.strip()]:
+        n = (nn,) * 3
+        mT_np, vs_np = I.paper_synthetic(n)
+        ctx = pkg.Context(n, precision="f32", **kw)
+        mT = torch.from_numpy(mT_np).float().cuda()
+        vs = torch.from_numpy(vs_np).float().cuda()
+        del mT_np, vs_np
+        mR = ctx.transport(mT, vs, +1)
+        del vs
+        ctx.register(mT, mR)  # warm-up: autotuner and first-touch of the workspace
+        times, rep = [], None
+        for _ in range(2):
+            (v, rep, status), dt = timed(lambda: ctx.register(mT, mR))
+            times.append(dt)
+        row = {"n": list(n), "seconds": min(times), "status": status, **{k: rep[k] for k in keys},
+               "rel_mismatch": rep["mismatch"] / rep["mismatch0"], "rel_grad": rep["gnorm"] / rep["gnorm0"],
+               "workspace_gb": ctx.workspace_bytes() / 1e9,
+               "device_memory_gb": torch.cuda.max_memory_allocated() / 1e9}
+        log("synthetic H1-div %s: %.3f s, %d GN, %d matvecs, %d PDE, rel grad %.2e, workspace %.1f GB"
+            % (n, row["seconds"], rep["gn_iters"], rep["matvecs"], rep["pde_solves"], row["rel_grad"],
+               row["workspace_gb"]))
+        synth.append(row)
+        ctx.close()
+        del mT, mR, v
+        torch.cuda.empty_cache()
+    n = (256, 256, 256)
+    mT_np, vstar_np = make_inputs(n)
+    kwc = dict(beta=1e-3, nt=4, regnorm=1, beta_w=1e-4, gtol_rel=5e-2)
+    ctx = pkg.Context(n, precision="f32", **kwc)
+    mT = torch.from_numpy(mT_np).float().cuda()
+    mR = ctx.transport(mT, torch.from_numpy(vstar_np).float().cuda(), +1)
+    ctx.register(mT, mR)  # warm-up
+    (vd, rd, sd), td = timed(lambda: ctx.register(mT, mR))
+    (vc, rcs, sc), tc = timed(lambda: ctx.register_continuation(mT, mR))
+    cont = {"n": list(n), "solver": kwc,
+            "direct": {"seconds": td, "status": sd, **{k: rd[k] for k in keys},
+                       "rel_mismatch": rd["mismatch"] / rd["mismatch0"]},
+            "continuation": {"seconds": tc, "status": sc, "levels": len(rcs),
+                             "gn_per_level": [r["gn_iters"] for r in rcs],
+                             "matvecs_per_level": [r["matvecs"] for r in rcs],
+                             "pde_solves": sum(r["pde_solves"] for r in rcs),
+                             "rel_mismatch": rcs[-1]["mismatch"] / rcs[-1]["mismatch0"]},
+            "speedup": td / tc, "solution_rel_difference": float((vc - vd).norm() / vd.norm())}
+    log("continuation 256^3: direct %.3f s (%d GN, %d mv) | continuation %.3f s (GN %s, mv %s)"
+        % (td, rd["gn_iters"], rd["matvecs"], tc, cont["continuation"]["gn_per_level"],
+           cont["continuation"]["matvecs_per_level"]))
+    print(json.dumps({"study": "models", "synthetic_h1div": {"solver": kw, "runs": synth},
+                      "continuation": cont}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.study == "precision":
@@ -532,6 +614,8 @@ def main():
         return batch_study(args)
     if args.study == "warmstart":
         return warmstart_study(args)
+    if args.study == "models":
+        return models_study(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

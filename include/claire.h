@@ -63,7 +63,8 @@ typedef struct {
     double beta;         /* regularisation weight beta_v > 0 */
     int nt;              /* number of semi-Lagrangian time steps (default 4, Sec. 2.3.1) */
     int regnorm;         /* 1: H1 seminorm, A = -Laplacian; 2: H2 seminorm, A = Laplacian^2 (Sec. 2.1) */
-    int divfree;         /* 0: K = I; 1: div v = 0 via the Leray projection K = I - grad Lap^-1 div (Sec. 2.2) */
+    int divfree;         /* 0: K = I (or the H1-div K, see beta_w); 1: div v = 0 via the Leray projection
+                            K = I - grad Lap^-1 div (Sec. 2.2) */
     double gtol_rel;     /* eps_g: stop when ||g_k|| <= eps_g ||g(v=0)|| (default 5e-2, Sec. 2.3.2) */
     double gtol_abs;     /* stop when ||g_k|| <= gtol_abs (default 1e-6, Sec. 2.3.2) */
     int max_gn;          /* Gauss-Newton iteration cap (default 50, Sec. 4.4) */
@@ -75,6 +76,11 @@ typedef struct {
                             gradients of the state history, grad m^j, in BF16 (read by every incremental state and
                             adjoint step; arithmetic stays FP32, reductions FP64). The error this adds is measured,
                             not bounded by the FP32 tolerance. */
+    double beta_w;       /* > 0: the H1-div model (Sec. 2.1-2.2): regnorm 1 plus the penalty beta_w/2 ||div v||^2_H1
+                            (w = div v in Eq. (2)), K = I - grad (beta_v (beta_w (-Lap + I))^-1 + I)^-1 Lap^-1 div in
+                            Eq. (5) and (7); requires regnorm = 1 and divfree = 0. 0 (default): off. PCG and the
+                            Armijo slope use the <K^-1 a, b> products in which beta_v A + K H_data is self-adjoint;
+                            the stopping test uses ||g|| of Eq. (5). */
 } claire_opts;
 
 /* What claire_register reports (the quantities of Table 3 plus timing). Host struct, filled on return. */
@@ -173,6 +179,22 @@ claire_status claire_register_host_f32(claire_ctx* ctx, const float* mT, const f
                                        claire_report* rep, void* stream);
 claire_status claire_register_host_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
                                        claire_report* rep, void* stream);
+
+/* Parameter continuation in beta_v (Sec. 3.6: start at beta_v = 1 and reduce it until the target is reached).
+ * Levels beta_start, beta_start*factor, beta_start*factor^2, ... while above the context's beta (the target), then
+ * the target itself, at most max_levels in all; every level is a claire_register solve warm-started from the
+ * previous level's v (with its own ||g(v = 0)|| in the relative test). v is in/out as for claire_register. reps
+ * (host, max_levels entries, may be NULL) receives one report per level, *nlevels (host, may be NULL) the number
+ * of levels run. Stops early on a status other than OK / ENOTCONV and returns the last level's status. The
+ * context's beta is restored before returning. 0 < factor < 1, beta_start > 0, else CLAIRE_EINVAL. */
+claire_status claire_register_continuation_f32(claire_ctx* ctx, const float* mT, const float* mR, float* v,
+                                               double beta_start, double factor, claire_report* reps,
+                                               int max_levels, int* nlevels, void* stream);
+claire_status claire_register_continuation_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
+                                               double beta_start, double factor, claire_report* reps,
+                                               int max_levels, int* nlevels, void* stream);
+/* Changes the regularisation weight beta_v of a context (beta > 0); nothing else is invalidated. */
+claire_status claire_set_beta(claire_ctx* ctx, double beta);
 
 /* ---- batched registration of many independent pairs (population-to-atlas) ------------------------------------
  * Solves every pair with claire_register_f32's algorithm. Pairs may have different grids. nworkers host threads

@@ -546,3 +546,29 @@ def register(prob, mT, mR, v0=None):
     rep.mismatch = 0.5 * inner(grid, res, res)
     rep.gnorm = gnorm
     return v, rep
+
+
+def continuation_levels(beta_target, beta_start=1.0, factor=0.1, max_levels=16):
+    """beta_v of each level of the parameter continuation (Sec. 3.6): beta_start, beta_start*factor, ... while
+    above the target, then the target."""
+    betas = []
+    b = beta_start
+    while b > beta_target * (1.0 + 1e-12) and len(betas) < max_levels - 1:
+        betas.append(b)
+        b *= factor
+    betas.append(beta_target)
+    return betas
+
+
+def register_continuation(prob, mT, mR, v0=None, beta_start=1.0, factor=0.1, max_levels=16):
+    """Parameter continuation in beta_v (Sec. 3.6): one full solve per level, each warm-started from the previous
+    level's solution; returns (v, [Report per level])."""
+    from dataclasses import replace
+    v = v0
+    reports = []
+    for b in continuation_levels(prob.beta, beta_start, factor, max_levels):
+        v, rep = register(replace(prob, beta=b), mT, mR, v)
+        reports.append(rep)
+        if not rep.converged and rep.status != "max_gn":
+            break
+    return v, reports

@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
                 ("nt", ctypes.c_int), ("regnorm", ctypes.c_int), ("divfree", ctypes.c_int),
                 ("gtol_rel", ctypes.c_double), ("gtol_abs", ctypes.c_double), ("max_gn", ctypes.c_int),
                 ("max_krylov", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("max_ls", ctypes.c_int),
-                ("armijo_c1", ctypes.c_double), ("bf16_mask", ctypes.c_int)]
+                ("armijo_c1", ctypes.c_double), ("bf16_mask", ctypes.c_int), ("beta_w", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -76,6 +76,7 @@ _TYPED = {
     "claire_precond": [_VP, _VP, _VP],
     "claire_register": [_VP, _VP, _VP, ctypes.POINTER(Report), _VP],
     "claire_register_host": [_VP, _VP, _VP, ctypes.POINTER(Report), _VP],
+    "claire_register_continuation": [_VP, _VP, _VP, _D, _D, ctypes.POINTER(Report), _I, ctypes.POINTER(_I), _VP],
     "claire_departure": [_VP, _I, _VP, _VP],
     "claire_interp": [_VP, _VP, _VP, _VP],
     "claire_spectral": [_I, _VP, _VP, _VP],
@@ -93,6 +94,7 @@ _SZ = ctypes.c_size_t
 # resampling, the warm-start network and its layers: symbol -> (return type, argument types)
 _UNTYPED = {
     "claire_resample_f32": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _VP]),
+    "claire_set_beta": (_I, [_VP, _D]),
     "claire_ws_create": (_I, [_I, _I, _I, _I, _F, ctypes.c_ulonglong, ctypes.POINTER(_VP)]),
     "claire_ws_destroy": (_I, [_VP]),
     "claire_ws_last_error": (ctypes.c_char_p, [_VP]),
@@ -204,7 +206,8 @@ class Context:
     """One registration problem setup (grid, precision, beta, n_t, norm, constraint) and its device workspace."""
 
     def __init__(self, n, precision="f32", beta=1e-2, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2,
-                 gtol_abs=1e-6, max_gn=50, max_krylov=100, pcg_rtol=0.0, max_ls=10, armijo_c1=1e-4, bf16_mask=0):
+                 gtol_abs=1e-6, max_gn=50, max_krylov=100, pcg_rtol=0.0, max_ls=10, armijo_c1=1e-4, bf16_mask=0,
+                 beta_w=0.0):
         L = lib()
         torch = _torch()
         if not torch.cuda.is_available():
@@ -219,6 +222,7 @@ class Context:
         o.gtol_rel, o.gtol_abs, o.max_gn, o.max_krylov = float(gtol_rel), float(gtol_abs), int(max_gn), int(max_krylov)
         o.pcg_rtol, o.max_ls, o.armijo_c1 = float(pcg_rtol), int(max_ls), float(armijo_c1)
         o.bf16_mask = int(bf16_mask)
+        o.beta_w = float(beta_w)
         self.opts = o
         torch.cuda.init()
         h = _VP()
@@ -324,6 +328,22 @@ class Context:
         st = self._call("claire_register", self._s(mT, "mT"), self._s(mR, "mR"), self._v(v, "v"), ctypes.byref(rep),
                         self._stream(), allow=(OK, ENOTCONV, ELINESEARCH))
         return v, rep.as_dict(), STATUS[st]
+
+    def register_continuation(self, mT, mR, v=None, beta_start=1.0, factor=0.1, max_levels=16):
+        """Continuation in beta_v down to this context's beta (Sec. 3.6); returns (v, [report dict per level],
+        status name of the last level)."""
+        v = _torch().zeros((3,) + self.n, dtype=self.dtype, device="cuda") if v is None else v
+        reps = (Report * max_levels)()
+        nlev = ctypes.c_int(0)
+        st = self._call("claire_register_continuation", self._s(mT, "mT"), self._s(mR, "mR"), self._v(v, "v"),
+                        float(beta_start), float(factor), reps, int(max_levels), ctypes.byref(nlev), self._stream(),
+                        allow=(OK, ENOTCONV, ELINESEARCH))
+        return v, [reps[i].as_dict() for i in range(nlev.value)], STATUS[st]
+
+    def set_beta(self, beta):
+        st = lib().claire_set_beta(self._h, float(beta))
+        if st != OK:
+            raise ClaireError(st, "claire_set_beta(%r)" % beta)
 
     def register_host(self, mT, mR, v):
         """Same solve on HOST tensors (CPU, ideally pinned); v is updated in place."""

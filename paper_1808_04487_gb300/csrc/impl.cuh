@@ -147,6 +147,8 @@ template <class T> claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx
 template <class T> claire_status spec_div(claire_ctx* c, const cplx<T>* V0, const cplx<T>* V1, const cplx<T>* V2,
                                           cplx<T>* D, cudaStream_t st);
 template <class T> claire_status spec_leray(claire_ctx* c, cplx<T>* V0, cplx<T>* V1, cplx<T>* V2, cudaStream_t st);
+// V = K V with the context's K of Eq. (5) (identity, Leray, or the H1-div operator)
+template <class T> claire_status spec_kop(claire_ctx* c, cplx<T>* V0, cplx<T>* V1, cplx<T>* V2, cudaStream_t st);
 // mode 0: V *= scale * a(k); mode 1: V *= 1/(beta a(k)) (1 where a = 0); mode 2: V *= -|k|^2 (Laplacian)
 template <class T> claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp, long long comp_stride, int mode,
                                             double beta, cudaStream_t st);

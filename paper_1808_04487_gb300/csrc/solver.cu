@@ -327,6 +327,11 @@ template <class T> claire_status add_projected_b(claire_ctx* c, const T* u, T* o
   const long long n3 = 3 * c->d.N;
   if (c->o.divfree) {
     CL_TRY(leray_inplace<T>(c, W.b, W.b, st));
+  } else if (c->o.beta_w > 0.0) {
+    const long long Ns = c->d.Ns;
+    CL_TRY(vec_r2c<T>(c, W.b, W.spec, st));
+    CL_TRY(spec_kop<T>(c, W.spec, W.spec + Ns, W.spec + 2 * Ns, st));
+    CL_TRY(vec_c2r<T>(c, W.spec, W.b, st));
   }
   return waxpy<T>(c, n3, u, 1.0, W.b, out, st);
 }
@@ -775,6 +780,39 @@ template <class T> claire_status api_register(claire_ctx* c, const T* mT, const 
   claire_report local;
   return register_dev<T>(c, mT, mR, v, rep ? rep : &local, (cudaStream_t)s);
 }
+// Parameter continuation in beta_v (Sec. 3.6): levels beta_start, beta_start f, beta_start f^2, ... while above the
+// context's beta_v, then beta_v itself; each level is a full solve warm-started from the previous level's v.
+template <class T> claire_status api_register_continuation(claire_ctx* c, const T* mT, const T* mR, T* v,
+                                                           double beta_start, double factor, claire_report* reps,
+                                                           int max_levels, int* nlevels, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, mR);
+  CHECK_PTR(c, v);
+  if (!(beta_start > 0.0) || !(factor > 0.0 && factor < 1.0) || max_levels < 1) {
+    c->set_error("continuation needs beta_start > 0, 0 < factor < 1 and max_levels >= 1");
+    return CLAIRE_EINVAL;
+  }
+  const double target = c->o.beta;
+  std::vector<double> betas;
+  for (double b = beta_start; b > target * (1.0 + 1e-12) && (int)betas.size() < max_levels - 1; b *= factor)
+    betas.push_back(b);
+  betas.push_back(target);
+  claire_status st = CLAIRE_OK;
+  int done = 0;
+  for (double b : betas) {
+    c->o.beta = b;
+    claire_report local;
+    claire_report* r = reps ? reps + done : &local;
+    st = register_dev<T>(c, mT, mR, v, r, (cudaStream_t)s);
+    ++done;
+    if (st != CLAIRE_OK && st != CLAIRE_ENOTCONV) break;
+  }
+  c->o.beta = target;
+  if (nlevels) *nlevels = done;
+  return st;
+}
+
 template <class T> claire_status api_register_host(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
                                                    void* s) {
   CHECK_CTX(c, T);
@@ -891,6 +929,7 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   // 32-bit node indices in the kernels and the launch grid's z extent (one i1 slab per grid z index)
   if (N > (1LL << 31) - 1 || o.n[0] > 65535) return CLAIRE_EINVAL;
   if (o.bf16_mask < 0 || o.bf16_mask > 1 || (o.bf16_mask && o.precision != CLAIRE_F32)) return CLAIRE_EINVAL;
+  if (!(o.beta_w >= 0.0) || (o.beta_w > 0.0 && (o.divfree || o.regnorm != 1))) return CLAIRE_EINVAL;
   claire_ctx* c = new (std::nothrow) claire_ctx();
   if (!c) return CLAIRE_ENOMEM;
   c->o = o;
@@ -1048,6 +1087,21 @@ claire_status claire_register_f32(claire_ctx* c, const float* mT, const float* m
 claire_status claire_register_f64(claire_ctx* c, const double* mT, const double* mR, double* v, claire_report* rep,
                                   void* s) {
   return api_register<double>(c, mT, mR, v, rep, s);
+}
+claire_status claire_register_continuation_f32(claire_ctx* c, const float* mT, const float* mR, float* v,
+                                               double beta_start, double factor, claire_report* reps,
+                                               int max_levels, int* nlevels, void* s) {
+  return api_register_continuation<float>(c, mT, mR, v, beta_start, factor, reps, max_levels, nlevels, s);
+}
+claire_status claire_register_continuation_f64(claire_ctx* c, const double* mT, const double* mR, double* v,
+                                               double beta_start, double factor, claire_report* reps,
+                                               int max_levels, int* nlevels, void* s) {
+  return api_register_continuation<double>(c, mT, mR, v, beta_start, factor, reps, max_levels, nlevels, s);
+}
+claire_status claire_set_beta(claire_ctx* c, double beta) {
+  if (!c || !(beta > 0.0)) return CLAIRE_EINVAL;
+  c->o.beta = beta;
+  return CLAIRE_OK;
 }
 claire_status claire_register_host_f32(claire_ctx* c, const float* mT, const float* mR, float* v, claire_report* rep,
                                        void* s) {

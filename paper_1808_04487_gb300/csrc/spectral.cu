@@ -3,6 +3,13 @@
 // |k|^2 (H1) or |k|^4 (H2) (Sec. 2.1), its inverse as the spectral preconditioner with the zero eigenvalue set to
 // 1 (Sec. 2.3.3, Remark), and the Parseval form of sum_c <v_c, A v_c>. Integer wavenumbers; first-order symbols
 // use k' with the Nyquist entry zeroed, even-order symbols the full k. All kernels stream float2/double2 values.
+//
+// K of Eq. (5) comes in three forms (kmode): 0 identity, 1 Leray (div v = 0), 2 the H1-div model (H1 seminorm for
+// v plus the penalty beta_w/2 ||div v||^2_H1, Sec. 2.1-2.2): K^ = I - q k'k'^T with
+// q = rw (|k|^2 + 1) / (|k|^2 + rw (|k|^2 + 1) |k'|^2), rw = beta_w / beta_v, which is the paper's
+// I - grad (beta_v (beta_w (-Lap + I))^-1 + I)^-1 Lap^-1 div off the Nyquist planes. beta_v A + K H_data (Eq. (7))
+// is then self-adjoint in <K^-1 a, b>, K^-1 = I + s k'k'^T with s = rw (|k|^2 + 1) / |k|^2; the PCG products and
+// the Armijo slope of the solver use that form, and the regularisation value gains rw (|k|^2 + 1) |k'.v|^2.
 #include "impl.cuh"
 
 namespace claire {
@@ -58,7 +65,8 @@ __global__ void k_spec_div(const cplx<T>* __restrict__ V0, const cplx<T>* __rest
   D[idx] = mk<T>(a.x + b.x + c.x, a.y + b.y + c.y);
 }
 
-template <class T> __device__ __forceinline__ void leray_apply(const Wave& w, cplx<T>& a, cplx<T>& b, cplx<T>& c) {
+template <class T, class WV>
+__device__ __forceinline__ void leray_apply(const WV& w, cplx<T>& a, cplx<T>& b, cplx<T>& c) {
   const T q1 = T(w.p1), q2 = T(w.p2), q3 = T(w.p3);
   const T qq = q1 * q1 + q2 * q2 + q3 * q3;
   if (qq > T(0)) {
@@ -71,6 +79,66 @@ template <class T> __device__ __forceinline__ void leray_apply(const Wave& w, cp
   }
 }
 
+// k'.x for the three components (complex)
+template <class T, class WV> __device__ __forceinline__ cplx<T> kdot(const WV& w, cplx<T> a, cplx<T> b, cplx<T> c) {
+  const T q1 = T(w.p1), q2 = T(w.p2), q3 = T(w.p3);
+  return mk<T>(q1 * a.x + q2 * b.x + q3 * c.x, q1 * a.y + q2 * b.y + q3 * c.y);
+}
+template <class T, class WV> __device__ __forceinline__ T ksq_of(const WV& w) {
+  return T(w.k1) * T(w.k1) + T(w.k2) * T(w.k2) + T(w.k3) * T(w.k3);
+}
+
+// x = K x for kmode 0 / 1 / 2
+template <class T, class WV>
+__device__ __forceinline__ void kop_apply(int kmode, T rw, const WV& w, cplx<T>& a, cplx<T>& b, cplx<T>& c) {
+  if (kmode == 1) {
+    leray_apply<T>(w, a, b, c);
+  } else if (kmode == 2) {
+    const T ksq = ksq_of<T>(w);
+    const T kpsq = T(w.p1) * T(w.p1) + T(w.p2) * T(w.p2) + T(w.p3) * T(w.p3);
+    const T num = rw * (ksq + T(1));
+    const T den = ksq + num * kpsq;
+    if (den > T(0)) {
+      const T q = num / den;
+      const cplx<T> d = kdot<T>(w, a, b, c);
+      const T q1 = q * T(w.p1), q2 = q * T(w.p2), q3 = q * T(w.p3);
+      a = mk<T>(a.x - q1 * d.x, a.y - q1 * d.y);
+      b = mk<T>(b.x - q2 * d.x, b.y - q2 * d.y);
+      c = mk<T>(c.x - q3 * d.x, c.y - q3 * d.y);
+    }
+  }
+}
+
+// the weight s of K^-1 = I + s k'k'^T (kmode 2; 0 otherwise and at k = 0)
+template <class T, class WV> __device__ __forceinline__ T kinv_s(int kmode, T rw, const WV& w) {
+  if (kmode != 2) return T(0);
+  const T ksq = ksq_of<T>(w);
+  return ksq > T(0) ? rw * (ksq + T(1)) / ksq : T(0);
+}
+// Re(x . conj y) + s Re((k'.x) conj(k'.y)): <K^-1 x, y> per mode (s = 0: the plain product)
+template <class T, class WV>
+__device__ __forceinline__ T kinv_dot(T s, const WV& w, const cplx<T> (&x)[3], const cplx<T> (&y)[3]) {
+  T e = x[0].x * y[0].x + x[0].y * y[0].y + x[1].x * y[1].x + x[1].y * y[1].y + x[2].x * y[2].x + x[2].y * y[2].y;
+  if (s != T(0)) {
+    const cplx<T> dx = kdot<T>(w, x[0], x[1], x[2]), dy = kdot<T>(w, y[0], y[1], y[2]);
+    e += s * (dx.x * dy.x + dx.y * dy.y);
+  }
+  return e;
+}
+// a(k) |x|^2, plus rw (|k|^2 + 1) |k'.x|^2 for kmode 2: the regularisation density divided by beta_v
+template <class T, class WV>
+__device__ __forceinline__ T reg_density(int regnorm, int kmode, T rw, const WV& w, const cplx<T> (&x)[3]) {
+  const T ksq = ksq_of<T>(w);
+  const T a = regnorm == 2 ? ksq * ksq : ksq;
+  T e = a * (x[0].x * x[0].x + x[0].y * x[0].y + x[1].x * x[1].x + x[1].y * x[1].y + x[2].x * x[2].x +
+             x[2].y * x[2].y);
+  if (kmode == 2) {
+    const cplx<T> d = kdot<T>(w, x[0], x[1], x[2]);
+    e += rw * (ksq + T(1)) * (d.x * d.x + d.y * d.y);
+  }
+  return e;
+}
+
 template <class T>
 __global__ void k_spec_leray(cplx<T>* __restrict__ V0, cplx<T>* __restrict__ V1, cplx<T>* __restrict__ V2, Dims d) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,6 +146,20 @@ __global__ void k_spec_leray(cplx<T>* __restrict__ V0, cplx<T>* __restrict__ V1,
   const Wave w = wavenumbers(idx, d);
   cplx<T> a = V0[idx], b = V1[idx], c = V2[idx];
   leray_apply<T>(w, a, b, c);
+  V0[idx] = a;
+  V1[idx] = b;
+  V2[idx] = c;
+}
+
+// V = K V (kmode 1: Leray, 2: H1-div)
+template <class T>
+__global__ void k_spec_kop(cplx<T>* __restrict__ V0, cplx<T>* __restrict__ V1, cplx<T>* __restrict__ V2, int kmode,
+                           T rw, Dims d) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.Ns) return;
+  const Wave w = wavenumbers(idx, d);
+  cplx<T> a = V0[idx], b = V1[idx], c = V2[idx];
+  kop_apply<T>(kmode, rw, w, a, b, c);
   V0[idx] = a;
   V1[idx] = b;
   V2[idx] = c;
@@ -105,14 +187,14 @@ __global__ void k_spec_scale(cplx<T>* __restrict__ V, int ncomp, long long cstri
 }
 
 template <class T>
-__global__ void k_spec_combine(const cplx<T>* __restrict__ V, cplx<T>* __restrict__ B, int regnorm, int divfree,
-                               T beta, Dims d) {
+__global__ void k_spec_combine(const cplx<T>* __restrict__ V, cplx<T>* __restrict__ B, int regnorm, int kmode,
+                               T rw, T beta, Dims d) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= d.Ns) return;
   const Wave w = wavenumbers(idx, d);
   const long long s = d.Ns;
   cplx<T> b0 = B[idx], b1 = B[s + idx], b2 = B[2 * s + idx];
-  if (divfree) leray_apply<T>(w, b0, b1, b2);
+  kop_apply<T>(kmode, rw, w, b0, b1, b2);
   const T f = beta * reg_symbol<T>(w, regnorm);
   const cplx<T> v0 = V[idx], v1 = V[s + idx], v2 = V[2 * s + idx];
   B[idx] = mk<T>(f * v0.x + b0.x, f * v0.y + b0.y);
@@ -122,18 +204,16 @@ __global__ void k_spec_combine(const cplx<T>* __restrict__ V, cplx<T>* __restric
 
 // sum over the half spectrum with weight 1 on the k3 = 0 and k3 = n3/2 planes and 2 elsewhere (Parseval)
 template <class T>
-__global__ void __launch_bounds__(256) k_spec_reg_partial(const cplx<T>* __restrict__ V, int regnorm, Dims d,
-                                                          double* __restrict__ partials) {
+__global__ void __launch_bounds__(256) k_spec_reg_partial(const cplx<T>* __restrict__ V, int regnorm, int kmode,
+                                                          T rw, Dims d, double* __restrict__ partials) {
   Acc<T> acc;
   const long long s = d.Ns;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < s;
        idx += (long long)gridDim.x * blockDim.x) {
     const Wave w = wavenumbers(idx, d);
-    const T a = reg_symbol<T>(w, regnorm);
     const T wt = (w.k3 == 0 || 2 * w.k3 == d.n3) ? T(1) : T(2);
-    T e = T(0);
-    for (int c = 0; c < 3; ++c) e += V[c * s + idx].x * V[c * s + idx].x + V[c * s + idx].y * V[c * s + idx].y;
-    acc.add(wt * a * e);
+    const cplx<T> x[3] = {V[idx], V[s + idx], V[2 * s + idx]};
+    acc.add(wt * reg_density<T>(regnorm, kmode, rw, w, x));
   }
   __shared__ double red[256 / 32];
   double t0 = acc.value();
@@ -179,16 +259,6 @@ template <class T> __device__ __forceinline__ T hsym(const HWave& h, int regnorm
   return regnorm == 2 ? ksq * ksq : ksq;
 }
 
-template <class T> __device__ __forceinline__ void hleray(const HWave& h, cplx<T>& a, cplx<T>& b, cplx<T>& c) {
-  Wave w;
-  w.k1 = h.k1;
-  w.k2 = h.k2;
-  w.k3 = h.k3;
-  w.p1 = h.p1;
-  w.p2 = h.p2;
-  w.p3 = h.p3;
-  leray_apply<T>(w, a, b, c);
-}
 
 template <class T> __device__ __forceinline__ T csq(cplx<T> a) { return a.x * a.x + a.y * a.y; }
 template <class T> __device__ __forceinline__ T cre(cplx<T> a, cplx<T> b) { return a.x * b.x + a.y * b.y; }
@@ -219,14 +289,14 @@ __device__ __forceinline__ void block_reduce_v(const Acc<T> (&accs)[V], double* 
 // G = beta a V + K B (V may be null: v = 0); partial ||G||^2
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ B,
-                                                 cplx<T>* __restrict__ G, int regnorm, int divfree, T beta, Dims d,
-                                                 double* __restrict__ partials) {
+                                                 cplx<T>* __restrict__ G, int regnorm, int kmode, T rw, T beta,
+                                                 Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
     cplx<T> b0 = B[j], b1 = B[s + j], b2 = B[2 * s + j];
-    if (divfree) hleray<T>(h, b0, b1, b2);
+    kop_apply<T>(kmode, rw, h, b0, b1, b2);
     if (V) {
       const T f = beta * hsym<T>(h, regnorm);
       const cplx<T> v0 = V[j], v1 = V[s + j], v2 = V[2 * s + j];
@@ -242,11 +312,11 @@ __global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, 
   block_reduce_v<T, 1>(acc, partials);
 }
 
-// PCG start (Alg. 2): R = -G, S = Z = M^-1 R, Vt = 0; partials <R,Z>, ||R||^2, <S, beta A S>
+// PCG start (Alg. 2): R = -G, S = Z = M^-1 R, Vt = 0; partials <K^-1 R, Z>, ||R||^2, <K^-1 S, beta A S>
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ R,
                                                  cplx<T>* __restrict__ S, cplx<T>* __restrict__ Vt, int regnorm,
-                                                 T beta, Dims d, double* __restrict__ partials) {
+                                                 int kmode, T rw, T beta, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[3];
   HLOOP {
@@ -254,30 +324,31 @@ __global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, 
     const T a = hsym<T>(h, regnorm);
     const T ba = beta * a;
     const T m = precond_sym(ba, a);
-    T rr = T(0);
+    const T sk = kinv_s<T>(kmode, rw, h);
+    cplx<T> rv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> g = G[c * s + j];
       const cplx<T> r = mk<T>(-g.x, -g.y);
-      const cplx<T> z = mk<T>(m * r.x, m * r.y);
+      rv[c] = r;
       R[c * s + j] = r;
-      S[c * s + j] = z;
+      S[c * s + j] = mk<T>(m * r.x, m * r.y);
       Vt[c * s + j] = mk<T>(T(0), T(0));
-      rr += csq<T>(r);
     }
-    const T wrr = T(h.w) * rr;
-    acc[0].add(m * wrr);
-    acc[1].add(wrr);
-    acc[2].add(ba * m * m * wrr);
+    const T rr = T(h.w) * (csq<T>(rv[0]) + csq<T>(rv[1]) + csq<T>(rv[2]));
+    const T rkr = T(h.w) * kinv_dot<T>(sk, h, rv, rv);
+    acc[0].add(m * rkr);
+    acc[1].add(rr);
+    acc[2].add(ba * m * m * rkr);
   }
   block_reduce_v<T, 3>(acc, partials);
 }
 
-// PCG update: H S = beta a S + K Bt; R -= kappa H S; Vt += kappa S; partials ||R||^2, <R, M^-1 R>
+// PCG update: H S = beta a S + K Bt; R -= kappa H S; Vt += kappa S; partials ||R||^2, <K^-1 R, M^-1 R>
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ Bt,
                                                      cplx<T>* __restrict__ R, cplx<T>* __restrict__ Vt, T kappa,
-                                                     int regnorm, int divfree, T beta, Dims d,
+                                                     int regnorm, int kmode, T rw, T beta, Dims d,
                                                      double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[2];
@@ -287,9 +358,9 @@ __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__
     const T ba = beta * a;
     const T m = precond_sym(ba, a);
     cplx<T> b0 = Bt[j], b1 = Bt[s + j], b2 = Bt[2 * s + j];
-    if (divfree) hleray<T>(h, b0, b1, b2);
+    kop_apply<T>(kmode, rw, h, b0, b1, b2);
     const cplx<T> bb[3] = {b0, b1, b2};
-    T rr = T(0);
+    cplx<T> rv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> sv = S[c * s + j];
@@ -297,21 +368,21 @@ __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__
       cplx<T> r = R[c * s + j];
       r = mk<T>(fma(-kappa, hs.x, r.x), fma(-kappa, hs.y, r.y));
       R[c * s + j] = r;
+      rv[c] = r;
       cplx<T> vt = Vt[c * s + j];
       Vt[c * s + j] = mk<T>(fma(kappa, sv.x, vt.x), fma(kappa, sv.y, vt.y));
-      rr += csq<T>(r);
     }
-    const T wrr = T(h.w) * rr;
-    acc[0].add(wrr);
-    acc[1].add(m * wrr);
+    acc[0].add(T(h.w) * (csq<T>(rv[0]) + csq<T>(rv[1]) + csq<T>(rv[2])));
+    acc[1].add(m * T(h.w) * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, rv, rv));
   }
   block_reduce_v<T, 2>(acc, partials);
 }
 
-// PCG direction: S = M^-1 R + mu S; partial <S, beta A S>
+// PCG direction: S = M^-1 R + mu S; partial <K^-1 S, beta A S>
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ S, T mu,
-                                                    int regnorm, T beta, Dims d, double* __restrict__ partials) {
+                                                    int regnorm, int kmode, T rw, T beta, Dims d,
+                                                    double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[1];
   HLOOP {
@@ -319,36 +390,38 @@ __global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ 
     const T a = hsym<T>(h, regnorm);
     const T ba = beta * a;
     const T m = precond_sym(ba, a);
-    T ss = T(0);
+    cplx<T> sw[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> r = R[c * s + j];
       cplx<T> sv = S[c * s + j];
       sv = mk<T>(fma(mu, sv.x, m * r.x), fma(mu, sv.y, m * r.y));
       S[c * s + j] = sv;
-      ss += csq<T>(sv);
+      sw[c] = sv;
     }
-    acc[0].add(T(h.w) * ba * ss);
+    acc[0].add(T(h.w) * ba * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, sw, sw));
   }
   block_reduce_v<T, 1>(acc, partials);
 }
 
-// optional projection Vt = K Vt (div v = 0), then partial <G, Vt>
+// projection Vt = K Vt under div v = 0 (kmode 1), then partial <K^-1 G, Vt> (the slope of J along Vt)
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_project_dot(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Vt,
-                                                        int divfree, Dims d, double* __restrict__ partials) {
+                                                        int kmode, T rw, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
     cplx<T> v0 = Vt[j], v1 = Vt[s + j], v2 = Vt[2 * s + j];
-    if (divfree) {
-      hleray<T>(h, v0, v1, v2);
+    if (kmode == 1) {
+      leray_apply<T>(h, v0, v1, v2);
       Vt[j] = v0;
       Vt[s + j] = v1;
       Vt[2 * s + j] = v2;
     }
-    acc[0].add(T(h.w) * (cre<T>(G[j], v0) + cre<T>(G[s + j], v1) + cre<T>(G[2 * s + j], v2)));
+    const cplx<T> gv[3] = {G[j], G[s + j], G[2 * s + j]};
+    const cplx<T> vv[3] = {v0, v1, v2};
+    acc[0].add(T(h.w) * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, gv, vv));
   }
   block_reduce_v<T, 1>(acc, partials);
 }
@@ -358,21 +431,22 @@ __global__ void __launch_bounds__(256) k_sp_project_dot(const cplx<T>* __restric
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_trial(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ Vt,
                                                   cplx<T>* __restrict__ Vtr, cplx<T>* __restrict__ Sc, T alpha,
-                                                  int regnorm, Dims d, double* __restrict__ partials) {
+                                                  int regnorm, int kmode, T rw, Dims d,
+                                                  double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
-    T e = T(0);
+    cplx<T> xs[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> v = V[c * s + j], t = Vt[c * s + j];
       const cplx<T> x = mk<T>(fma(alpha, t.x, v.x), fma(alpha, t.y, v.y));
       Vtr[c * s + j] = x;
       Sc[c * s + j] = x;
-      e += csq<T>(x);
+      xs[c] = x;
     }
-    acc[0].add(T(h.w) * hsym<T>(h, regnorm) * e);
+    acc[0].add(T(h.w) * reg_density<T>(regnorm, kmode, rw, h, xs));
   }
   block_reduce_v<T, 1>(acc, partials);
 }
@@ -380,25 +454,29 @@ __global__ void __launch_bounds__(256) k_sp_trial(const cplx<T>* __restrict__ V,
 // partial sum_k w a(k) |V|^2 and a copy of V into Sc (used for a nonzero initial guess)
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_copy_reg(const cplx<T>* __restrict__ V, cplx<T>* __restrict__ Sc,
-                                                     int regnorm, Dims d, double* __restrict__ partials) {
+                                                     int regnorm, int kmode, T rw, Dims d,
+                                                     double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
-    T e = T(0);
+    cplx<T> xs[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cplx<T> x = V[c * s + j];
       if (Sc) Sc[c * s + j] = x;
-      e += csq<T>(x);
+      xs[c] = x;
     }
-    acc[0].add(T(h.w) * hsym<T>(h, regnorm) * e);
+    acc[0].add(T(h.w) * reg_density<T>(regnorm, kmode, rw, h, xs));
   }
   block_reduce_v<T, 1>(acc, partials);
 }
 #undef HLOOP
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+// form of K (0 identity, 1 Leray, 2 H1-div) and rw = beta_w / beta_v
+static inline int kmode_of(const claire_ctx* c) { return c->o.divfree ? 1 : (c->o.beta_w > 0.0 ? 2 : 0); }
+static inline double rw_of(const claire_ctx* c) { return c->o.beta_w > 0.0 ? c->o.beta_w / c->o.beta : 0.0; }
 
 template <class T>
 claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G1, cplx<T>* G2, cudaStream_t st) {
@@ -421,6 +499,12 @@ template <class T> claire_status spec_leray(claire_ctx* c, cplx<T>* V0, cplx<T>*
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
+template <class T> claire_status spec_kop(claire_ctx* c, cplx<T>* V0, cplx<T>* V1, cplx<T>* V2, cudaStream_t st) {
+  c->prof_begin("spec_kop", st);
+  k_spec_kop<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V0, V1, V2, kmode_of(c), T(rw_of(c)), c->d);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
 template <class T>
 claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp, long long cstride, int mode, double beta,
                          cudaStream_t st) {
@@ -431,13 +515,14 @@ claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp, long long cstride
 }
 template <class T> claire_status spec_combine(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st) {
   c->prof_begin("spec_combine", st);
-  k_spec_combine<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V, B, c->o.regnorm, c->o.divfree, T(c->o.beta), c->d);
+  k_spec_combine<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V, B, c->o.regnorm, kmode_of(c), T(rw_of(c)),
+                                                               T(c->o.beta), c->d);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T> claire_status spec_reg_partial(claire_ctx* c, const cplx<T>* V, double* partials, cudaStream_t st) {
   c->prof_begin("spec_reg_partial", st);
-  k_spec_reg_partial<T><<<kReduceBlocks, 256, 0, st>>>(V, c->o.regnorm, c->d, partials);
+  k_spec_reg_partial<T><<<kReduceBlocks, 256, 0, st>>>(V, c->o.regnorm, kmode_of(c), T(rw_of(c)), c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -446,7 +531,8 @@ template <class T>
 claire_status sp_grad(claire_ctx* c, const cplx<T>* V, const cplx<T>* B, cplx<T>* G, double* partials,
                       cudaStream_t st) {
   c->prof_begin("sp_grad", st);
-  k_sp_grad<T><<<kReduceBlocks, 256, 0, st>>>(V, B, G, c->o.regnorm, c->o.divfree, T(c->o.beta), c->d, partials);
+  k_sp_grad<T><<<kReduceBlocks, 256, 0, st>>>(V, B, G, c->o.regnorm, kmode_of(c), T(rw_of(c)), T(c->o.beta), c->d,
+                                              partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -454,7 +540,8 @@ template <class T>
 claire_status sp_pcg0(claire_ctx* c, const cplx<T>* G, cplx<T>* R, cplx<T>* S, cplx<T>* Vt, double* partials,
                       cudaStream_t st) {
   c->prof_begin("sp_pcg0", st);
-  k_sp_pcg0<T><<<kReduceBlocks, 256, 0, st>>>(G, R, S, Vt, c->o.regnorm, T(c->o.beta), c->d, partials);
+  k_sp_pcg0<T><<<kReduceBlocks, 256, 0, st>>>(G, R, S, Vt, c->o.regnorm, kmode_of(c), T(rw_of(c)), T(c->o.beta), c->d,
+                                              partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -462,22 +549,23 @@ template <class T>
 claire_status sp_pcg_step(claire_ctx* c, const cplx<T>* S, const cplx<T>* Bt, cplx<T>* R, cplx<T>* Vt, double kappa,
                           double* partials, cudaStream_t st) {
   c->prof_begin("sp_pcg_step", st);
-  k_sp_pcg_step<T><<<kReduceBlocks, 256, 0, st>>>(S, Bt, R, Vt, T(kappa), c->o.regnorm, c->o.divfree, T(c->o.beta),
-                                                  c->d, partials);
+  k_sp_pcg_step<T><<<kReduceBlocks, 256, 0, st>>>(S, Bt, R, Vt, T(kappa), c->o.regnorm, kmode_of(c), T(rw_of(c)),
+                                                  T(c->o.beta), c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T>
 claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cplx<T>* S, double mu, double* partials, cudaStream_t st) {
   c->prof_begin("sp_pcg_dir", st);
-  k_sp_pcg_dir<T><<<kReduceBlocks, 256, 0, st>>>(R, S, T(mu), c->o.regnorm, T(c->o.beta), c->d, partials);
+  k_sp_pcg_dir<T><<<kReduceBlocks, 256, 0, st>>>(R, S, T(mu), c->o.regnorm, kmode_of(c), T(rw_of(c)), T(c->o.beta),
+                                                 c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T>
 claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G, cplx<T>* Vt, double* partials, cudaStream_t st) {
   c->prof_begin("sp_project_dot", st);
-  k_sp_project_dot<T><<<kReduceBlocks, 256, 0, st>>>(G, Vt, c->o.divfree, c->d, partials);
+  k_sp_project_dot<T><<<kReduceBlocks, 256, 0, st>>>(G, Vt, kmode_of(c), T(rw_of(c)), c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -485,14 +573,15 @@ template <class T>
 claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr, cplx<T>* Sc, double alpha,
                        double* partials, cudaStream_t st) {
   c->prof_begin("sp_trial", st);
-  k_sp_trial<T><<<kReduceBlocks, 256, 0, st>>>(V, Vt, Vtr, Sc, T(alpha), c->o.regnorm, c->d, partials);
+  k_sp_trial<T><<<kReduceBlocks, 256, 0, st>>>(V, Vt, Vtr, Sc, T(alpha), c->o.regnorm, kmode_of(c), T(rw_of(c)), c->d,
+                                               partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T>
 claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* partials, cudaStream_t st) {
   c->prof_begin("sp_copy_reg", st);
-  k_sp_copy_reg<T><<<kReduceBlocks, 256, 0, st>>>(V, Sc, c->o.regnorm, c->d, partials);
+  k_sp_copy_reg<T><<<kReduceBlocks, 256, 0, st>>>(V, Sc, c->o.regnorm, kmode_of(c), T(rw_of(c)), c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -512,6 +601,7 @@ claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* 
   template claire_status spec_div<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*,      \
                                      cudaStream_t);                                                              \
   template claire_status spec_leray<T>(claire_ctx*, cplx<T>*, cplx<T>*, cplx<T>*, cudaStream_t);                 \
+  template claire_status spec_kop<T>(claire_ctx*, cplx<T>*, cplx<T>*, cplx<T>*, cudaStream_t);                   \
   template claire_status spec_scale<T>(claire_ctx*, cplx<T>*, int, long long, int, double, cudaStream_t);        \
   template claire_status spec_combine<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cudaStream_t);                   \
   template claire_status spec_reg_partial<T>(claire_ctx*, const cplx<T>*, double*, cudaStream_t);

@@ -46,7 +46,8 @@ def test_default_opts_are_the_papers(L):
 @pytest.mark.parametrize("bad", [
     dict(n=(31, 32, 32)), dict(n=(2, 32, 32)), dict(n=(22, 32, 32)), dict(nt=0), dict(beta=0.0), dict(beta=-1.0),
     dict(regnorm=3), dict(divfree=2), dict(precision=5), dict(max_krylov=0), dict(max_ls=0), dict(bf16_mask=2),
-    dict(bf16_mask=1, precision=1)])
+    dict(bf16_mask=1, precision=1), dict(beta_w=-1e-4), dict(beta_w=1e-4, divfree=1),
+    dict(beta_w=1e-4, regnorm=2)])
 def test_create_rejects_bad_options_before_any_device_call(L, bad):
     import paper_1808_04487_gb300 as pkg
     o = pkg.Opts()

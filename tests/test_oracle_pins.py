@@ -580,3 +580,30 @@ def test_P14_h1div_register_converges():
     mR = O.transport(p, mT, I.random_velocity(p.n, seed=3, kmax=2, amplitude=0.3), +1)
     v, rep = O.register(p, mT, mR)
     assert rep.converged and rep.gnorm <= 1e-2 * rep.gnorm0 and rep.J < rep.J0
+
+
+# ---------------------------------------------------------------------------------------- continuation in beta (P15)
+def test_P15_continuation_levels_follow_the_paper():
+    """Starting at beta_v = 1 and dividing by 10: three levels for a target of 1e-2, four for 1e-3 (the level
+    counts of the continuation runs of Tab. 3)."""
+    assert O.continuation_levels(1e-2) == pytest.approx([1.0, 1e-1, 1e-2])
+    assert O.continuation_levels(1e-3) == pytest.approx([1.0, 1e-1, 1e-2, 1e-3])
+    assert O.continuation_levels(2.0) == [2.0]
+    assert len(O.continuation_levels(1e-9, max_levels=4)) == 4
+
+
+def test_P15_continuation_solves_each_level_and_ends_at_the_target():
+    n = (16, 16, 16)
+    p = O.Problem(n, beta=1e-3, nt=4, regnorm=1, beta_w=1e-4, gtol_rel=1e-2)
+    mT = I.trig_image(n, 0)
+    mR = O.transport(p, mT, I.random_velocity(n, seed=3, kmax=2, amplitude=0.3), +1)
+    v, reps = O.register_continuation(p, mT, mR)
+    assert len(reps) == 4 and all(r.converged for r in reps)
+    # the last level is a solve of the target problem: its stopping test holds at v
+    lin = O.linearize(p, mT, v)
+    g = O.reduced_gradient(p, lin, mR)
+    assert O.norm(p.grid, g) <= 1e-2 * reps[-1].gnorm0 * (1 + 1e-9)
+    # a single level (start at the target) is exactly the plain solve
+    v1, reps1 = O.register_continuation(p, mT, mR, beta_start=1e-3)
+    v2, rep2 = O.register(p, mT, mR)
+    assert len(reps1) == 1 and np.array_equal(v1, v2) and reps1[0].gn_iters == rep2.gn_iters
