@@ -269,6 +269,8 @@ class Problem:
     regnorm: int = 1          # 1: H1 seminorm (A = -Lap), 2: H2 seminorm (A = Lap^2)
     divfree: bool = False     # div v = 0 via the Leray projection
     beta_w: float = 0.0       # > 0: H1-div model, penalty beta_w/2 ||div v||_H1^2 (needs regnorm 1, no divfree)
+    precond: int = 0          # 0: spectral preconditioner; 1: two-level preconditioner (Sec. 2.3.3)
+    pc_kappa: float = 0.1     # nested PCG tolerance eps_M = pc_kappa eps_H (two-level)
     gtol_rel: float = 5e-2
     gtol_abs: float = 1e-6
     max_gn: int = 50
@@ -283,6 +285,8 @@ class Problem:
             raise ValueError("nt >= 1 and beta > 0 required")
         if self.beta_w < 0 or (self.beta_w > 0 and (self.divfree or self.regnorm != 1)):
             raise ValueError("beta_w > 0 (H1-div) needs regnorm 1 and no div v = 0 constraint")
+        if self.precond == 1 and any(a % 4 for a in self.n):
+            raise ValueError("the two-level preconditioner needs grid sizes divisible by 4")
 
     def time_weights(self):
         dt = 1.0 / self.nt
@@ -422,6 +426,7 @@ class Report:
     mismatch: float = 0.0
     gnorm0: float = 0.0
     gnorm: float = 0.0
+    coarse_matvecs: int = 0
     converged: bool = False
     status: str = "ok"
 
@@ -434,15 +439,21 @@ class Report:
         return self.mismatch / self.mismatch0 if self.mismatch0 > 0 else 0.0
 
 
-def pcg(prob, lin, g_k, eps_H, report):
+def pcg(prob, lin, g_k, eps_H, report, coarse=None):
     """Alg. 2: PCG on H v~ = -g with the spectral preconditioner; break when ||r|| < eps_H ||r_0||.
 
     The inner products of kappa and mu are control_inner (the K^-1-weighted one for the H1-div model, where
     H = beta_v A + K H_data is self-adjoint in it); the break test uses the plain norm of r."""
     grid = prob.grid
+
+    def M(r):
+        if prob.precond == 1:
+            return twolevel_apply(prob, coarse, r, prob.pc_kappa * eps_H, report)
+        return precond(grid, r, prob.beta, prob.regnorm)
+
     vt = np.zeros_like(g_k)
     r = -g_k
-    z = precond(grid, r, prob.beta, prob.regnorm)
+    z = M(r)
     s = z.copy()
     rz = control_inner(prob, r, z)
     r0 = norm(grid, r)
@@ -462,7 +473,7 @@ def pcg(prob, lin, g_k, eps_H, report):
         it += 1
         if norm(grid, r) < eps_H * r0:
             break
-        z = precond(grid, r, prob.beta, prob.regnorm)
+        z = M(r)
         rz_new = control_inner(prob, r, z)
         mu = rz_new / rz
         rz = rz_new
@@ -505,6 +516,8 @@ def register(prob, mT, mR, v0=None):
     J = objective(prob, mR, lin.m[-1], v)
     rep.J0 = J
     gnorm = norm(grid, g)
+    cprob = coarse_problem(prob) if prob.precond == 1 else None
+    mT_c = restrict_field(grid, cprob.grid, mT) if cprob is not None else None
     while True:
         if gnorm <= prob.gtol_rel * rep.gnorm0 or gnorm <= prob.gtol_abs:
             rep.converged = True
@@ -516,7 +529,11 @@ def register(prob, mT, mR, v0=None):
             eps_H = prob.pcg_rtol
         else:
             eps_H = min(0.5, math.sqrt(gnorm / rep.gnorm0))
-        vt = pcg(prob, lin, g, eps_H, rep)
+        coarse = None
+        if cprob is not None:
+            coarse = (cprob, linearize(cprob, mT_c, np.stack([restrict_field(grid, cprob.grid, v[c])
+                                                              for c in range(3)])))
+        vt = pcg(prob, lin, g, eps_H, rep, coarse)
         if prob.divfree:
             vt = leray(grid, vt)
         gvt = control_inner(prob, g, vt)
@@ -572,3 +589,122 @@ def register_continuation(prob, mT, mR, v0=None, beta_start=1.0, factor=0.1, max
         if not rep.converged and rep.status != "max_gn":
             break
     return v, reports
+
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# Two-level preconditioner (Sec. 2.3.3)
+# ----------------------------------------------------------------------------------------------------------------
+# It acts on the regularisation split-preconditioned system (I + R^-1/2 H_data R^-1/2) w = -R^-1/2 g with
+# R = beta A (its zero eigenvalue set to 1) and w = R^1/2 v~. For s = R^-1/2 r, the low-frequency part (the modes
+# the half-resolution grid holds, Nyquist excluded) is replaced by the nested-PCG solution of the same system
+# discretised directly on the coarse grid; the high-frequency part is kept (H_H replaced by I). Restriction and
+# prolongation are spectral. In the original variables the preconditioner is M^-1 r = R^-1/2 P(R^-1/2 r).
+def coarse_problem(prob):
+    """The same problem on the grid n/2 (spectral preconditioner; the nested solver iterates on it)."""
+    from dataclasses import replace
+    return replace(prob, n=tuple(a // 2 for a in prob.n), precond=0)
+
+
+def split_symbol(grid, beta, regnorm):
+    """(beta a(k))^-1/2, 1 where a(k) = 0."""
+    a = reg_symbol(grid, regnorm)
+    return np.where(a > 0, 1.0 / np.sqrt(np.where(a > 0, beta * a, 1.0)), 1.0)
+
+
+def _kept_pairs(n_f, n_c, half):
+    """Index pairs (fine, coarse) of the wavenumbers kept along one axis: 2|k| < n_c (coarse Nyquist dropped)."""
+    top = (n_c - 1) // 2
+    ks = np.arange(0, top + 1) if half else np.arange(-top, top + 1)
+    return ks % n_f, ks % n_c
+
+
+def low_mask(grid_f, grid_c):
+    """Fine half-spectrum mask of the modes the coarse grid holds."""
+    mask = np.zeros((grid_f.n[0], grid_f.n[1], grid_f.n[2] // 2 + 1), dtype=bool)
+    f1, _ = _kept_pairs(grid_f.n[0], grid_c.n[0], False)
+    f2, _ = _kept_pairs(grid_f.n[1], grid_c.n[1], False)
+    f3, _ = _kept_pairs(grid_f.n[2], grid_c.n[2], True)
+    mask[np.ix_(f1, f2, f3)] = True
+    return mask
+
+
+def restrict_spectrum(grid_f, grid_c, F):
+    """Fine half spectrum -> coarse half spectrum of the same function (scaled by N_c / N_f)."""
+    f1, c1 = _kept_pairs(grid_f.n[0], grid_c.n[0], False)
+    f2, c2 = _kept_pairs(grid_f.n[1], grid_c.n[1], False)
+    f3, c3 = _kept_pairs(grid_f.n[2], grid_c.n[2], True)
+    G = np.zeros((grid_c.n[0], grid_c.n[1], grid_c.n[2] // 2 + 1), dtype=complex)
+    G[np.ix_(c1, c2, c3)] = F[np.ix_(f1, f2, f3)] * (grid_c.N / grid_f.N)
+    return G
+
+
+def prolong_spectrum(grid_f, grid_c, G):
+    """Coarse half spectrum -> fine half spectrum (zero outside the coarse modes; scaled by N_f / N_c)."""
+    f1, c1 = _kept_pairs(grid_f.n[0], grid_c.n[0], False)
+    f2, c2 = _kept_pairs(grid_f.n[1], grid_c.n[1], False)
+    f3, c3 = _kept_pairs(grid_f.n[2], grid_c.n[2], True)
+    F = np.zeros((grid_f.n[0], grid_f.n[1], grid_f.n[2] // 2 + 1), dtype=complex)
+    F[np.ix_(f1, f2, f3)] = G[np.ix_(c1, c2, c3)] * (grid_f.N / grid_c.N)
+    return F
+
+
+def restrict_field(grid_f, grid_c, f):
+    return grid_c.ifft(restrict_spectrum(grid_f, grid_c, grid_f.fft(f)))
+
+
+def hess_data(prob, lin, vt):
+    """Data part K[int lam~ grad m dt] of the Gauss-Newton matvec (Eq. (7)-(9))."""
+    mt1 = incremental_state(prob, lin, vt)
+    return apply_Kp(prob, adjoint_integral(prob, lin, -mt1))
+
+
+def _scale(grid, x, sym):
+    return np.stack([grid.ifft(sym * grid.fft(x[c])) for c in range(3)])
+
+
+def coarse_operator(cprob, clin, x):
+    """(I + R^-1/2 H_data R^-1/2) x on the coarse grid."""
+    s = split_symbol(cprob.grid, cprob.beta, cprob.regnorm)
+    return x + _scale(cprob.grid, hess_data(cprob, clin, _scale(cprob.grid, x, s)), s)
+
+
+def nested_pcg(cprob, clin, f, eps_M, report):
+    """CG on the coarse split system (already regularisation-preconditioned, so no further preconditioner);
+    u = 0 at the start, break when ||r|| < eps_M ||f||, at most max_krylov iterations."""
+    grid = cprob.grid
+    u = np.zeros_like(f)
+    r = f.copy()
+    p = r.copy()
+    rr = control_inner(cprob, r, r)
+    f0 = norm(grid, f)
+    if f0 == 0.0:
+        return u
+    for _ in range(cprob.max_krylov):
+        Hp = coarse_operator(cprob, clin, p)
+        report.coarse_matvecs += 1
+        pHp = control_inner(cprob, Hp, p)
+        if not (pHp > 0):
+            break
+        alpha = rr / pHp
+        u = u + alpha * p
+        r = r - alpha * Hp
+        if norm(grid, r) < eps_M * f0:
+            break
+        rr_new = control_inner(cprob, r, r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return u
+
+
+def twolevel_apply(prob, coarse, r, eps_M, report):
+    """z = M^-1 r of the two-level preconditioner; coarse = (coarse problem, its linearization at v)."""
+    cprob, clin = coarse
+    gf, gc = prob.grid, cprob.grid
+    sf = split_symbol(gf, prob.beta, prob.regnorm)
+    Y = [gf.fft(r[c]) * sf for c in range(3)]
+    f = np.stack([gc.ifft(restrict_spectrum(gf, gc, Y[c])) for c in range(3)])
+    u = nested_pcg(cprob, clin, f, eps_M, report)
+    low = low_mask(gf, gc)
+    Z = [np.where(low, prolong_spectrum(gf, gc, gc.fft(u[c])), Y[c]) * sf for c in range(3)]
+    return np.stack([gf.ifft(Z[c]) for c in range(3)])

@@ -607,3 +607,106 @@ def test_P15_continuation_solves_each_level_and_ends_at_the_target():
     v1, reps1 = O.register_continuation(p, mT, mR, beta_start=1e-3)
     v2, rep2 = O.register(p, mT, mR)
     assert len(reps1) == 1 and np.array_equal(v1, v2) and reps1[0].gn_iters == rep2.gn_iters
+
+
+# ------------------------------------------------------------------------------- two-level preconditioner (P16)
+def test_P16_spectral_transfer_operators():
+    gf, gc = O.Grid((16, 12, 20)), O.Grid((8, 6, 10))
+    rng = np.random.default_rng(0)
+    # a trigonometric polynomial the coarse grid holds (|k_a| < n_c/2) restricts to its coarse samples
+    x = [2 * np.pi * np.arange(m) / m for m in gf.n]
+    xc = [2 * np.pi * np.arange(m) / m for m in gc.n]
+    f = lambda X: 0.3 + np.cos(X[0] + 2 * X[1]) - 0.5 * np.sin(3 * X[0] - X[1] + 4 * X[2])
+    F = f(np.meshgrid(*x, indexing="ij"))
+    assert np.abs(O.restrict_field(gf, gc, F) - f(np.meshgrid(*xc, indexing="ij"))).max() < 1e-12
+    # restriction after prolongation is the identity on coarse spectra without the coarse Nyquist modes
+    G = gc.fft(rng.normal(size=gc.n))
+    G2 = O.restrict_spectrum(gf, gc, O.prolong_spectrum(gf, gc, G))
+    keep = O.restrict_spectrum(gf, gc, O.low_mask(gf, gc).astype(complex) * (gf.N / gc.N)) != 0
+    assert np.abs(G2[keep] - G[keep]).max() < 1e-12 * np.abs(G).max() and np.all(G2[~keep] == 0)
+    # prolongation after restriction is the cut-off filter F_L
+    Ff = gf.fft(rng.normal(size=gf.n))
+    low = O.low_mask(gf, gc)
+    assert np.allclose(O.prolong_spectrum(gf, gc, O.restrict_spectrum(gf, gc, Ff)), np.where(low, Ff, 0), atol=1e-12)
+
+
+def _tl_problem(n=(16, 16, 16), beta=1e-3, **kw):
+    p = O.Problem(n, beta=beta, nt=4, regnorm=1, precond=1, **kw)
+    mT = I.trig_image(n, 0, kmax=3)
+    mR = I.trig_image(n, 1, kmax=3)
+    v = I.random_velocity(n, seed=4, kmax=2, amplitude=0.2)
+    cp = O.coarse_problem(p)
+    lin = O.linearize(p, mT, v)
+    clin = O.linearize(cp, O.restrict_field(p.grid, cp.grid, mT),
+                       np.stack([O.restrict_field(p.grid, cp.grid, v[c]) for c in range(3)]))
+    return p, mT, mR, v, lin, (cp, clin)
+
+
+def test_P16_high_frequencies_and_zero_data_reduce_to_the_spectral_preconditioner():
+    p, mT, mR, v, lin, coarse = _tl_problem()
+    g = p.grid
+    rep = O.Report()
+    # a residual without coarse modes is only scaled: M^-1 r = (beta A)^-1 r
+    r = np.random.default_rng(1).normal(size=(3,) + g.n)
+    low = O.low_mask(g, coarse[0].grid)
+    r = np.stack([g.ifft(np.where(low, 0, g.fft(r[c]))) for c in range(3)])
+    z = O.twolevel_apply(p, coarse, r, 1e-8, rep)
+    assert rel(z, O.precond(g, r, p.beta, p.regnorm)) < 1e-12
+    # with a constant template the data Hessian vanishes, the coarse system is the identity, and M^-1 = (beta A)^-1
+    cp = coarse[0]
+    flat = O.linearize(cp, np.full(cp.grid.n, 0.4), np.zeros((3,) + cp.grid.n))
+    r = np.random.default_rng(2).normal(size=(3,) + g.n)
+    z = O.twolevel_apply(p, (cp, flat), r, 1e-8, rep)
+    assert rel(z, O.precond(g, r, p.beta, p.regnorm)) < 1e-12
+
+
+def test_P16_twolevel_pcg_reaches_the_dense_solution():
+    """8^3 fine / 4^3 coarse at v = 0: PCG with the two-level preconditioner (tight outer and nested tolerances)
+    solves the dense Gauss-Newton system."""
+    p = O.Problem((8, 8, 8), beta=1e-3, nt=4, regnorm=1, precond=1, pc_kappa=1e-6, max_krylov=400)
+    mT = I.trig_image(p.n, 0, kmax=2)
+    mR = I.trig_image(p.n, 1, kmax=2)
+    lin = O.linearize(p, mT, np.zeros((3,) + p.n))
+    cp = O.coarse_problem(p)
+    clin = O.linearize(cp, O.restrict_field(p.grid, cp.grid, mT), np.zeros((3,) + cp.grid.n))
+    n = 3 * p.grid.N
+    H = np.empty((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        H[:, i] = O.hessvec(p, lin, e.reshape((3,) + p.n)).ravel()
+    g0 = O.reduced_gradient(p, lin, mR)
+    rep = O.Report()
+    vt = O.pcg(p, lin, g0, 1e-9, rep, (cp, clin))
+    assert rel(vt.ravel(), np.linalg.solve(H, -g0.ravel())) < 1e-6
+
+
+def test_P16_twolevel_needs_fewer_fine_matvecs_at_small_beta():
+    """H2, beta 1e-4 on the phantom at 16^3: the Newton system at v = 0 solved to 1e-3 takes well under half the
+    fine-grid matvecs with the two-level preconditioner, and both reach the same step within the tolerance."""
+    n = (16, 16, 16)
+    mT = I.brain_phantom(n, 0)
+    p0 = O.Problem(n, beta=1e-4, nt=4, regnorm=2, max_krylov=500)
+    mR = O.transport(p0, mT, I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=0.5), +1)
+    lin = O.linearize(p0, mT, np.zeros((3,) + n))
+    g0 = O.reduced_gradient(p0, lin, mR)
+    r1 = O.Report()
+    vt1 = O.pcg(p0, lin, g0, 1e-3, r1)
+    p1 = O.Problem(n, beta=1e-4, nt=4, regnorm=2, max_krylov=500, precond=1)
+    cp = O.coarse_problem(p1)
+    clin = O.linearize(cp, O.restrict_field(p1.grid, cp.grid, mT), np.zeros((3,) + cp.grid.n))
+    r2 = O.Report()
+    vt2 = O.pcg(p1, lin, g0, 1e-3, r2, (cp, clin))
+    assert 2 * r2.matvecs < r1.matvecs and r2.coarse_matvecs > 0
+    assert rel(vt2, vt1) < 1e-2
+
+
+def test_P16_twolevel_register_converges():
+    n = (16, 16, 16)
+    kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, gtol_rel=1e-2)
+    mT = I.brain_phantom(n, 0)
+    mR = O.transport(O.Problem(n, **kw), mT,
+                     I.random_velocity(n, seed=1, kmax=4, max_disp_voxels=0.5, divfree=True), +1)
+    v, rep = O.register(O.Problem(n, precond=1, **kw), mT, mR)
+    assert rep.converged and rep.coarse_matvecs > 0
+    assert np.abs(O.divergence_spectral(O.Grid(n), v)).max() < 1e-10 * np.abs(v).max()
