@@ -532,7 +532,9 @@ def models_study(args):
     synthetic problem of Sec. 4.2, FP32 to ||g|| <= 1e-2 ||g(0)||, at each grid of --model-sizes: the configuration
     of Tab. 4 (which used the two-level preconditioner on a CPU cluster; here the spectral one on one GPU).
     (2) Parameter continuation in beta_v (Sec. 3.6: 1, 1e-1, 1e-2, 1e-3) against the direct solve, H1-div
-    beta_w = 1e-4, on the brain phantom at 256^3 to ||g|| <= 5e-2 ||g(0)|| (the tolerance of Tab. 3)."""
+    beta_w = 1e-4, on the brain phantom at 256^3 to ||g|| <= 5e-2 ||g(0)|| (the tolerance of Tab. 3).
+    (3) Spectral against two-level preconditioner (Sec. 2.3.3) on the phantom (H2, beta 1e-3 and 1e-4,
+    div v = 0) and the synthetic H1-div problem."""
     import numpy as np
     import torch
 
@@ -600,9 +602,44 @@ def models_study(args):
     log("continuation 256^3: direct %.3f s (%d GN, %d mv) | continuation %.3f s (GN %s, mv %s)"
         % (td, rd["gn_iters"], rd["matvecs"], tc, cont["continuation"]["gn_per_level"],
            cont["continuation"]["matvecs_per_level"]))
-    print(json.dumps({"study": "models", "synthetic_h1div": {"solver": kw, "runs": synth},
-                      "continuation": cont}), flush=True)
     ctx.close()
+    del mT, mR, vd, vc
+    torch.cuda.empty_cache()
+    # (3) spectral vs two-level preconditioner (Sec. 2.3.3) on three problems at 256^3 (and the synthetic at 512^3)
+    pcs = []
+    cases = [("phantom H2 beta 1e-3 div v = 0", (256,) * 3, dict(SOLVER_KW), "phantom"),
+             ("phantom H2 beta 1e-4 div v = 0", (256,) * 3, dict(SOLVER_KW, beta=1e-4), "phantom"),
+             ("synthetic H1-div beta 1e-3", (256,) * 3, dict(kw), "synthetic"),
+             ("synthetic H1-div beta 1e-3", (512,) * 3, dict(kw), "synthetic")]
+    for name, n, ckw, kind in cases:
+        if kind == "phantom":
+            mT_np, vs_np = make_inputs(n)
+        else:
+            mT_np, vs_np = I.paper_synthetic(n)
+        mT = torch.from_numpy(mT_np).float().cuda()
+        vs = torch.from_numpy(vs_np).float().cuda()
+        del mT_np, vs_np
+        row = {"problem": name, "n": list(n), "solver": ckw}
+        for pc in (0, 1):
+            c = pkg.Context(n, precision="f32", precond=pc, **ckw)
+            mR = c.transport(mT, vs, +1)
+            c.register(mT, mR)  # warm-up
+            (v, r, st), dt = timed(lambda: c.register(mT, mR))
+            row["spectral" if pc == 0 else "two_level"] = {
+                "seconds": dt, "status": st, **{k: r[k] for k in keys}, "coarse_matvecs": r["coarse_matvecs"],
+                "rel_grad": r["gnorm"] / r["gnorm0"], "rel_mismatch": r["mismatch"] / r["mismatch0"]}
+            c.close()
+            del mR, v
+        row["speedup_two_level"] = row["spectral"]["seconds"] / row["two_level"]["seconds"]
+        log("%s %s: spectral %.3f s (%d GN, %d mv) | two-level %.3f s (%d GN, %d mv, %d coarse mv)"
+            % (name, n, row["spectral"]["seconds"], row["spectral"]["gn_iters"], row["spectral"]["matvecs"],
+               row["two_level"]["seconds"], row["two_level"]["gn_iters"], row["two_level"]["matvecs"],
+               row["two_level"]["coarse_matvecs"]))
+        pcs.append(row)
+        del mT, vs
+        torch.cuda.empty_cache()
+    print(json.dumps({"study": "models", "synthetic_h1div": {"solver": kw, "runs": synth},
+                      "continuation": cont, "preconditioners": pcs}), flush=True)
     return 0
 
 

@@ -81,6 +81,12 @@ typedef struct {
                             Eq. (5) and (7); requires regnorm = 1 and divfree = 0. 0 (default): off. PCG and the
                             Armijo slope use the <K^-1 a, b> products in which beta_v A + K H_data is self-adjoint;
                             the stopping test uses ||g|| of Eq. (5). */
+    int precond;         /* 0 (default): spectral preconditioner (beta A)^-1; 1: two-level preconditioner (Sec. 2.3.3)
+                            on the half-resolution grid (n_a divisible by 4, n_a >= 8): the low modes of
+                            R^-1/2 r, R = beta A, are replaced by a nested CG solution of the coarse split system
+                            I + R^-1/2 H_data R^-1/2 (direct coarse discretisation, spectral transfer), the high
+                            modes are kept */
+    double pc_kappa;     /* nested tolerance eps_M = pc_kappa eps_H of the two-level preconditioner (default 0.1) */
 } claire_opts;
 
 /* What claire_register reports (the quantities of Table 3 plus timing). Host struct, filled on return. */
@@ -97,6 +103,7 @@ typedef struct {
     double gnorm0;       /* ||g(v = 0)||, the reference of the relative stopping test */
     double gnorm;        /* ||g|| at the returned v */
     double ms_total;     /* wall time of the call on the stream, milliseconds (CUDA events) */
+    int coarse_matvecs;  /* matvecs of the nested solver on the half-resolution grid (two-level preconditioner) */
 } claire_report;
 
 typedef struct claire_ctx claire_ctx;

@@ -33,7 +33,8 @@ class Opts(ctypes.Structure):
                 ("nt", ctypes.c_int), ("regnorm", ctypes.c_int), ("divfree", ctypes.c_int),
                 ("gtol_rel", ctypes.c_double), ("gtol_abs", ctypes.c_double), ("max_gn", ctypes.c_int),
                 ("max_krylov", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("max_ls", ctypes.c_int),
-                ("armijo_c1", ctypes.c_double), ("bf16_mask", ctypes.c_int), ("beta_w", ctypes.c_double)]
+                ("armijo_c1", ctypes.c_double), ("bf16_mask", ctypes.c_int), ("beta_w", ctypes.c_double),
+                ("precond", ctypes.c_int), ("pc_kappa", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -41,7 +42,7 @@ class Report(ctypes.Structure):
                 ("ls_trials", ctypes.c_int), ("pcg_breakdowns", ctypes.c_int), ("converged", ctypes.c_int),
                 ("J0", ctypes.c_double), ("J", ctypes.c_double), ("mismatch0", ctypes.c_double),
                 ("mismatch", ctypes.c_double), ("gnorm0", ctypes.c_double), ("gnorm", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("coarse_matvecs", ctypes.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -207,7 +208,7 @@ class Context:
 
     def __init__(self, n, precision="f32", beta=1e-2, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2,
                  gtol_abs=1e-6, max_gn=50, max_krylov=100, pcg_rtol=0.0, max_ls=10, armijo_c1=1e-4, bf16_mask=0,
-                 beta_w=0.0):
+                 beta_w=0.0, precond=0, pc_kappa=0.1):
         L = lib()
         torch = _torch()
         if not torch.cuda.is_available():
@@ -223,6 +224,7 @@ class Context:
         o.pcg_rtol, o.max_ls, o.armijo_c1 = float(pcg_rtol), int(max_ls), float(armijo_c1)
         o.bf16_mask = int(bf16_mask)
         o.beta_w = float(beta_w)
+        o.precond, o.pc_kappa = int(precond), float(pc_kappa)
         self.opts = o
         torch.cuda.init()
         h = _VP()

@@ -59,6 +59,7 @@ constexpr int kThreads = 256;
 
 struct claire_ctx {
   claire_opts o{};
+  claire_ctx* coarse = nullptr;  // half-resolution context of the two-level preconditioner (opts.precond = 1)
   claire::Dims d{};
   claire::Counters counters{};
   std::string err;
@@ -170,6 +171,23 @@ template <class T> claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G,
                                                 cudaStream_t st);
 template <class T> claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr,
                                           cplx<T>* Sc, double alpha, double* partials, cudaStream_t st);
+// two-level preconditioner (Sec. 2.3.3): c the fine context, cc its half-resolution context
+template <class T>
+claire_status tl_restrict(claire_ctx* c, claire_ctx* cc, const cplx<T>* R, cplx<T>* F, cplx<T>* P, cplx<T>* X,
+                          int ncomp, bool split, double* partials, cudaStream_t st);
+template <class T> claire_status tl_scale(claire_ctx* cc, const cplx<T>* P, cplx<T>* U, cudaStream_t st);
+template <class T>
+claire_status tl_apply(claire_ctx* cc, const cplx<T>* P, const cplx<T>* Bt, cplx<T>* HP, double* partials,
+                       cudaStream_t st);
+template <class T>
+claire_status tl_update(claire_ctx* cc, cplx<T>* X, cplx<T>* Rr, const cplx<T>* P, const cplx<T>* HP, double alpha,
+                        double* partials, cudaStream_t st);
+template <class T> claire_status tl_dir2(claire_ctx* cc, const cplx<T>* Rr, cplx<T>* P, double mu, cudaStream_t st);
+template <class T>
+claire_status tl_prolong(claire_ctx* c, claire_ctx* cc, const cplx<T>* R, const cplx<T>* X, cplx<T>* Z,
+                         double* partials, cudaStream_t st);
+template <class T>
+claire_status tl_dir(claire_ctx* c, const cplx<T>* Z, cplx<T>* S, double mu, double* partials, cudaStream_t st);
 template <class T> claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* partials,
                                              cudaStream_t st);
 

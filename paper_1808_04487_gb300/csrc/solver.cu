@@ -411,6 +411,72 @@ template <class T> claire_status gradient_spec(claire_ctx* c, const T* mR, const
   return reduce_final_v(c, W.partials, 1, kReduceBlocks, cellvol(c->d) / double(c->d.N), W.scal + slot, st);
 }
 
+// Two-level preconditioner (Sec. 2.3.3): Z = M^-1 R for the fine residual W.Rh into W.Vtrh, with rz = <R, Z>
+// (the K^-1-weighted product for the H1-div model). The coarse right-hand side is the restriction of
+// R^-1/2 R; CG on the coarse split system I + R^-1/2 H_data R^-1/2 (direct coarse discretisation at the coarse
+// linearisation; no further preconditioner) runs to ||r|| < eps_M ||f||; its solution replaces the coarse modes
+// of R^-1/2 R, and Z = R^-1/2 of the result. Coarse vectors: X = VTh, residual Rh, direction Sh, H P = Gh.
+template <class T> claire_status twolevel_apply(claire_ctx* c, double eps_M, claire_report* rep, double* rz,
+                                                cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  claire_ctx* cc = c->coarse;
+  Work<T>& Wc = cc->work<T>();
+  const double scc = cellvol(cc->d) / double(cc->d.N);
+  CL_TRY(tl_restrict<T>(c, cc, W.Rh, Wc.Rh, Wc.Sh, Wc.VTh, 3, true, Wc.partials, st));
+  CL_TRY(reduce_final_v(cc, Wc.partials, 2, kReduceBlocks, scc, Wc.scal, st));  // ||f||^2, <K^-1 f, f>
+  double v2[2];
+  CL_TRY(read_scalars(cc, Wc.scal, 2, v2, st));
+  const double f0 = std::sqrt(v2[0]);
+  double rr = v2[1];
+  if (!std::isfinite(f0) || !std::isfinite(rr)) {
+    c->set_error("non-finite coarse right-hand side");
+    return CLAIRE_ENAN;
+  }
+  for (int it = 0; f0 > 0.0 && it < cc->o.max_krylov; ++it) {
+    CL_TRY(tl_scale<T>(cc, Wc.Sh, Wc.Sc, st));
+    CL_TRY(vec_c2r<T>(cc, Wc.Sc, Wc.s, st));
+    CL_TRY(hess_data<T>(cc, Wc.s, st));
+    CL_TRY(vec_r2c<T>(cc, Wc.b, Wc.Bh, st));
+    CL_TRY(tl_apply<T>(cc, Wc.Sh, Wc.Bh, Wc.Gh, Wc.partials, st));
+    CL_TRY(reduce_final_v(cc, Wc.partials, 1, kReduceBlocks, scc, Wc.scal + 2, st));
+    double pHp;
+    CL_TRY(read_scalars(cc, Wc.scal + 2, 1, &pHp, st));
+    rep->coarse_matvecs++;
+    if (!(pHp > 0.0)) break;
+    const double alpha = rr / pHp;
+    CL_TRY(tl_update<T>(cc, Wc.VTh, Wc.Rh, Wc.Sh, Wc.Gh, alpha, Wc.partials, st));
+    CL_TRY(reduce_final_v(cc, Wc.partials, 2, kReduceBlocks, scc, Wc.scal, st));
+    CL_TRY(read_scalars(cc, Wc.scal, 2, v2, st));
+    if (std::sqrt(v2[0]) < eps_M * f0) break;
+    const double mu = v2[1] / rr;
+    rr = v2[1];
+    CL_TRY(tl_dir2<T>(cc, Wc.Rh, Wc.Sh, mu, st));
+  }
+  CL_TRY(tl_prolong<T>(c, cc, W.Rh, Wc.VTh, W.Vtrh, W.partials, st));
+  CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, cellvol(c->d) / double(c->d.N), W.scal, st));
+  return read_scalars(c, W.scal, 1, rz, st);
+}
+
+// the coarse problem's linearisation at the current iterate: v restricted spectrally from its master copy W.Vh
+template <class T> claire_status coarse_linearize(claire_ctx* c, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  claire_ctx* cc = c->coarse;
+  Work<T>& Wc = cc->work<T>();
+  CL_TRY(tl_restrict<T>(c, cc, W.Vh, Wc.Vh, nullptr, nullptr, 3, false, Wc.partials, st));
+  CL_TRY(vec_c2r<T>(cc, Wc.Vh, Wc.vdev, st));
+  return linearize<T>(cc, Wc.mTdev, Wc.vdev, st);
+}
+
+// m_T on the coarse grid (spectral restriction), kept in the coarse context's Wc.mTdev
+template <class T> claire_status coarse_template(claire_ctx* c, const T* mT, cudaStream_t st) {
+  Work<T>& W = c->work<T>();
+  claire_ctx* cc = c->coarse;
+  Work<T>& Wc = cc->work<T>();
+  CL_TRY(fft_r2c<T>(c, mT, W.spec, st));
+  CL_TRY(tl_restrict<T>(c, cc, W.spec, Wc.spec, nullptr, nullptr, 1, false, Wc.partials, st));
+  return fft_c2r<T>(cc, Wc.spec, Wc.mTdev, T(1.0 / double(cc->d.N)), st);
+}
+
 // Alg. 2 in the Fourier domain: PCG for H vt = -g with M^-1 = (beta A)^-1 and the relative break
 // ||r|| < eps_H ||r_0||. r, s, vt and g are half spectra; beta A, M^-1 and K act as exact diagonal multiplies, and
 // inner products follow from Parseval, so the iterates are those of Alg. 2 in exact arithmetic. Each iteration
@@ -419,6 +485,8 @@ template <class T> claire_status gradient_spec(claire_ctx* c, const T* mR, const
 template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report* rep, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const double sc = cellvol(c->d) / double(c->d.N);  // Parseval scale h1 h2 h3 / N
+  const bool two = c->coarse != nullptr;
+  const double eps_M = c->o.pc_kappa * eps_H;
   CL_TRY(sp_pcg0<T>(c, W.Gh, W.Rh, W.Sh, W.VTh, W.partials, st));
   CL_TRY(reduce_final_v(c, W.partials, 3, kReduceBlocks, sc, W.scal, st));  // <r,z>, ||r||^2, <s,beta A s>
   double v3[3];
@@ -426,6 +494,13 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
   double rz = v3[0];
   const double r0 = std::sqrt(v3[1]);
   double sAs = v3[2];
+  if (two) {
+    // z = M^-1 r of the two-level preconditioner replaces the spectral one: s = z
+    CL_TRY(twolevel_apply<T>(c, eps_M, rep, &rz, st));
+    CL_TRY(tl_dir<T>(c, W.Vtrh, W.Sh, 0.0, W.partials, st));
+    CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 2, st));
+    CL_TRY(read_scalars(c, W.scal + 2, 1, &sAs, st));
+  }
   if (!std::isfinite(rz) || !std::isfinite(r0)) {
     c->set_error("non-finite PCG scalar");
     return CLAIRE_ENAN;
@@ -456,9 +531,17 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
     double v2[2];
     CL_TRY(read_scalars(c, W.scal, 2, v2, st));
     if (std::sqrt(v2[0]) < eps_H * r0) break;
-    const double mu = v2[1] / rz;
-    rz = v2[1];
-    CL_TRY(sp_pcg_dir<T>(c, W.Rh, W.Sh, mu, W.partials, st));
+    if (two) {
+      double rz_new;
+      CL_TRY(twolevel_apply<T>(c, eps_M, rep, &rz_new, st));
+      const double mu = rz_new / rz;
+      rz = rz_new;
+      CL_TRY(tl_dir<T>(c, W.Vtrh, W.Sh, mu, W.partials, st));
+    } else {
+      const double mu = v2[1] / rz;
+      rz = v2[1];
+      CL_TRY(sp_pcg_dir<T>(c, W.Rh, W.Sh, mu, W.partials, st));
+    }
     CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 2, st));
     CL_TRY(read_scalars(c, W.scal + 2, 1, &sAs, st));
     CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
@@ -536,6 +619,10 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
         break;
       }
       const double eps_H = o.pcg_rtol > 0 ? o.pcg_rtol : std::fmin(0.5, std::sqrt(gnorm / rep->gnorm0));
+      if (c->coarse) {
+        if (rep->gn_iters == 0) CL_TRY(coarse_template<T>(c, mT, st));
+        CL_TRY(coarse_linearize<T>(c, st));
+      }
       CL_TRY(pcg<T>(c, eps_H, rep, st));
       // re-project the step under div v = 0 (idempotent in exact arithmetic) and <g, vt> for the Armijo test
       CL_TRY(sp_project_dot<T>(c, W.Gh, W.VTh, W.partials, st));
@@ -802,6 +889,7 @@ template <class T> claire_status api_register_continuation(claire_ctx* c, const 
   int done = 0;
   for (double b : betas) {
     c->o.beta = b;
+    if (c->coarse) c->coarse->o.beta = b;
     claire_report local;
     claire_report* r = reps ? reps + done : &local;
     st = register_dev<T>(c, mT, mR, v, r, (cudaStream_t)s);
@@ -809,6 +897,7 @@ template <class T> claire_status api_register_continuation(claire_ctx* c, const 
     if (st != CLAIRE_OK && st != CLAIRE_ENOTCONV) break;
   }
   c->o.beta = target;
+  if (c->coarse) c->coarse->o.beta = target;
   if (nlevels) *nlevels = done;
   return st;
 }
@@ -913,6 +1002,7 @@ claire_status claire_default_opts(claire_opts* o, int n1, int n2, int n3, int pr
   o->pcg_rtol = 0.0;
   o->max_ls = 10;
   o->armijo_c1 = 1e-4;
+  o->pc_kappa = 0.1;
   return CLAIRE_OK;
 }
 
@@ -930,6 +1020,12 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   if (N > (1LL << 31) - 1 || o.n[0] > 65535) return CLAIRE_EINVAL;
   if (o.bf16_mask < 0 || o.bf16_mask > 1 || (o.bf16_mask && o.precision != CLAIRE_F32)) return CLAIRE_EINVAL;
   if (!(o.beta_w >= 0.0) || (o.beta_w > 0.0 && (o.divfree || o.regnorm != 1))) return CLAIRE_EINVAL;
+  if (o.precond != 0 && o.precond != 1) return CLAIRE_EINVAL;
+  if (o.precond == 1) {
+    for (int a = 0; a < 3; ++a)
+      if (o.n[a] % 4 || o.n[a] < 8) return CLAIRE_EINVAL;
+    if (!(o.pc_kappa > 0.0 && o.pc_kappa < 1.0)) return CLAIRE_EINVAL;
+  }
   claire_ctx* c = new (std::nothrow) claire_ctx();
   if (!c) return CLAIRE_ENOMEM;
   c->o = o;
@@ -969,6 +1065,18 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
     delete c;
     return s;
   }
+  if (o.precond == 1) {
+    // the half-resolution problem of the two-level preconditioner: same model, spectral preconditioner
+    claire_opts oc = o;
+    for (int a = 0; a < 3; ++a) oc.n[a] = o.n[a] / 2;
+    oc.precond = 0;
+    s = claire_create(&oc, &c->coarse);
+    if (s != CLAIRE_OK) {
+      c->coarse = nullptr;
+      claire_destroy(c);
+      return s;
+    }
+  }
   *out = c;
   return CLAIRE_OK;
 }
@@ -976,6 +1084,7 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
 claire_status claire_profile_enable(claire_ctx* c, int on) {
   if (!c) return CLAIRE_EINVAL;
   c->prof_on = on != 0;
+  if (c->coarse) c->coarse->prof_on = on != 0;
   return CLAIRE_OK;
 }
 
@@ -983,16 +1092,19 @@ claire_status claire_profile_report(claire_ctx* c, char* buf, size_t len) {
   if (!c || !buf || len == 0) return CLAIRE_EINVAL;
   CL_CUDA(c, cudaDeviceSynchronize());
   std::map<std::string, std::pair<long long, double>> agg;
-  for (auto& r : c->prof_recs) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) ms = 0.f;
-    auto& e = agg[r.name];
-    e.first += 1;
-    e.second += ms;
-    c->prof_pool.push_back(r.a);
-    c->prof_pool.push_back(r.b);
+  for (claire_ctx* x : {c, c->coarse}) {
+    if (!x) continue;
+    for (auto& r : x->prof_recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) ms = 0.f;
+      auto& e = agg[std::string(x == c ? "" : "coarse:") + r.name];
+      e.first += 1;
+      e.second += ms;
+      x->prof_pool.push_back(r.a);
+      x->prof_pool.push_back(r.b);
+    }
+    x->prof_recs.clear();
   }
-  c->prof_recs.clear();
   std::string out = "{";
   bool first = true;
   for (auto& kv : agg) {
@@ -1011,6 +1123,7 @@ claire_status claire_profile_report(claire_ctx* c, char* buf, size_t len) {
 claire_status claire_destroy(claire_ctx* c) {
   if (!c) return CLAIRE_OK;
   cudaDeviceSynchronize();
+  if (c->coarse) claire_destroy(c->coarse);
   for (auto& r : c->prof_recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -1028,7 +1141,7 @@ size_t claire_workspace_bytes(const claire_ctx* c) { return c ? c->arena_bytes :
 
 claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   if (!c || !out) return CLAIRE_EINVAL;
-  out->launches = c->counters.launches;
+  out->launches = c->counters.launches + (c->coarse ? c->coarse->counters.launches : 0);
   return CLAIRE_OK;
 }
 
@@ -1101,6 +1214,7 @@ claire_status claire_register_continuation_f64(claire_ctx* c, const double* mT, 
 claire_status claire_set_beta(claire_ctx* c, double beta) {
   if (!c || !(beta > 0.0)) return CLAIRE_EINVAL;
   c->o.beta = beta;
+  if (c->coarse) c->coarse->o.beta = beta;
   return CLAIRE_OK;
 }
 claire_status claire_register_host_f32(claire_ctx* c, const float* mT, const float* mR, float* v, claire_report* rep,

@@ -471,6 +471,179 @@ __global__ void __launch_bounds__(256) k_sp_copy_reg(const cplx<T>* __restrict__
   }
   block_reduce_v<T, 1>(acc, partials);
 }
+// ---------------------------------------------------------------------------------------------------------------
+// Two-level preconditioner (Sec. 2.3.3) on the split system I + R^-1/2 H_data R^-1/2, R = beta A (zero mode 1):
+// spectral transfer between the fine half spectrum and the half-resolution one (a mode moves iff 2|k_a| < n_a of
+// the coarse grid, i.e. the coarse Nyquist modes are dropped), the scaled operator pieces of the nested CG on the
+// coarse grid, and the assembly z = R^-1/2 (y_H + P x) of the preconditioned residual.
+__device__ __forceinline__ bool on_coarse(const HWave& h, const Dims& dc) {
+  return 2 * abs(h.k1) < dc.n1 && 2 * abs(h.k2) < dc.n2 && 2 * h.k3 < dc.n3;
+}
+__device__ __forceinline__ unsigned index_of(const HWave& h, const Dims& d) {
+  const unsigned i1 = (unsigned)(h.k1 < 0 ? h.k1 + d.n1 : h.k1);
+  const unsigned i2 = (unsigned)(h.k2 < 0 ? h.k2 + d.n2 : h.k2);
+  return (i1 * (unsigned)d.n2 + i2) * (unsigned)d.n3h + (unsigned)h.k3;
+}
+// (beta a(k))^-1/2, 1 at a = 0
+template <class T> __device__ __forceinline__ T split_sym(const HWave& h, int regnorm, T beta) {
+  const T a = hsym<T>(h, regnorm);
+  return a > T(0) ? T(1) / sqrt(beta * a) : T(1);
+}
+
+#define CLOOP for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < (unsigned)dc.Ns; j += gridDim.x * blockDim.x)
+#define FLOOP for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < (unsigned)df.Ns; j += gridDim.x * blockDim.x)
+
+// coarse F = scale * (split ? R^-1/2 : 1) * (fine R restricted); optional copies P = F, X = 0;
+// partials ||F||^2 and <K^-1 F, F> (coarse Parseval weights)
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_restrict(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ F,
+                                                     cplx<T>* __restrict__ P, cplx<T>* __restrict__ X, int ncomp,
+                                                     Dims df, Dims dc, int split, int regnorm, T beta, int kmode,
+                                                     T rw, T scale, double* __restrict__ partials) {
+  Acc<T> acc[2];
+  CLOOP {
+    const HWave h = hwave(j, dc);
+    const bool keep = on_coarse(h, dc);
+    const unsigned jf = keep ? index_of(h, df) : 0u;
+    const T f = scale * (split ? split_sym<T>(h, regnorm, beta) : T(1));
+    cplx<T> x[3] = {mk<T>(T(0), T(0)), mk<T>(T(0), T(0)), mk<T>(T(0), T(0))};
+    for (int c = 0; c < ncomp; ++c) {
+      if (keep) {
+        const cplx<T> r = R[(long long)c * df.Ns + jf];
+        x[c] = mk<T>(f * r.x, f * r.y);
+      }
+      F[(long long)c * dc.Ns + j] = x[c];
+      if (P) P[(long long)c * dc.Ns + j] = x[c];
+      if (X) X[(long long)c * dc.Ns + j] = mk<T>(T(0), T(0));
+    }
+    if (ncomp == 3) {
+      acc[0].add(T(h.w) * (csq<T>(x[0]) + csq<T>(x[1]) + csq<T>(x[2])));
+      acc[1].add(T(h.w) * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, x, x));
+    }
+  }
+  block_reduce_v<T, 2>(acc, partials);
+}
+
+// U = R^-1/2 P (coarse; U is the input of the inverse transforms)
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_scale(const cplx<T>* __restrict__ P, cplx<T>* __restrict__ U, Dims dc,
+                                                  int regnorm, T beta) {
+  CLOOP {
+    const HWave h = hwave(j, dc);
+    const T f = split_sym<T>(h, regnorm, beta);
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> p = P[(long long)c * dc.Ns + j];
+      U[(long long)c * dc.Ns + j] = mk<T>(f * p.x, f * p.y);
+    }
+  }
+}
+
+// HP = P + R^-1/2 K Bt (Bt: transform of the data term at U = R^-1/2 P); partial <K^-1 HP, P>
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_apply(const cplx<T>* __restrict__ P, const cplx<T>* __restrict__ Bt,
+                                                  cplx<T>* __restrict__ HP, Dims dc, int regnorm, T beta, int kmode,
+                                                  T rw, double* __restrict__ partials) {
+  Acc<T> acc[1];
+  CLOOP {
+    const HWave h = hwave(j, dc);
+    const T f = split_sym<T>(h, regnorm, beta);
+    cplx<T> b0 = Bt[j], b1 = Bt[dc.Ns + j], b2 = Bt[2 * dc.Ns + j];
+    kop_apply<T>(kmode, rw, h, b0, b1, b2);
+    const cplx<T> bb[3] = {b0, b1, b2};
+    cplx<T> hp[3], pv[3];
+    for (int c = 0; c < 3; ++c) {
+      pv[c] = P[(long long)c * dc.Ns + j];
+      hp[c] = mk<T>(fma(f, bb[c].x, pv[c].x), fma(f, bb[c].y, pv[c].y));
+      HP[(long long)c * dc.Ns + j] = hp[c];
+    }
+    acc[0].add(T(h.w) * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, hp, pv));
+  }
+  block_reduce_v<T, 1>(acc, partials);
+}
+
+// X += alpha P, Rr -= alpha HP; partials ||Rr||^2 and <K^-1 Rr, Rr>
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_update(cplx<T>* __restrict__ X, cplx<T>* __restrict__ Rr,
+                                                   const cplx<T>* __restrict__ P, const cplx<T>* __restrict__ HP,
+                                                   T alpha, Dims dc, int kmode, T rw, double* __restrict__ partials) {
+  Acc<T> acc[2];
+  CLOOP {
+    const HWave h = hwave(j, dc);
+    cplx<T> rv[3];
+    for (int c = 0; c < 3; ++c) {
+      const long long o = (long long)c * dc.Ns + j;
+      const cplx<T> p = P[o], hp = HP[o];
+      cplx<T> x = X[o], r = Rr[o];
+      X[o] = mk<T>(fma(alpha, p.x, x.x), fma(alpha, p.y, x.y));
+      r = mk<T>(fma(-alpha, hp.x, r.x), fma(-alpha, hp.y, r.y));
+      Rr[o] = r;
+      rv[c] = r;
+    }
+    acc[0].add(T(h.w) * (csq<T>(rv[0]) + csq<T>(rv[1]) + csq<T>(rv[2])));
+    acc[1].add(T(h.w) * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, rv, rv));
+  }
+  block_reduce_v<T, 2>(acc, partials);
+}
+
+// P = Rr + mu P
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_dir2(const cplx<T>* __restrict__ Rr, cplx<T>* __restrict__ P, T mu,
+                                                 Dims dc) {
+  CLOOP {
+    for (int c = 0; c < 3; ++c) {
+      const long long o = (long long)c * dc.Ns + j;
+      const cplx<T> r = Rr[o], p = P[o];
+      P[o] = mk<T>(fma(mu, p.x, r.x), fma(mu, p.y, r.y));
+    }
+  }
+}
+
+// fine Z = R^-1/2 (y with its coarse modes replaced by scale * X), y = R^-1/2 R; partial <K^-1 R, Z>
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_prolong(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ X,
+                                                    cplx<T>* __restrict__ Z, Dims df, Dims dc, int regnorm, T beta,
+                                                    int kmode, T rw, T scale, double* __restrict__ partials) {
+  Acc<T> acc[1];
+  FLOOP {
+    const HWave h = hwave(j, df);
+    const T f = split_sym<T>(h, regnorm, beta);
+    const bool low = on_coarse(h, dc);
+    const unsigned jc = low ? index_of(h, dc) : 0u;
+    cplx<T> rv[3], zv[3];
+    for (int c = 0; c < 3; ++c) {
+      rv[c] = R[(long long)c * df.Ns + j];
+      cplx<T> y = low ? X[(long long)c * dc.Ns + jc] : rv[c];
+      const T g = low ? scale * f : f * f;
+      zv[c] = mk<T>(g * y.x, g * y.y);
+      Z[(long long)c * df.Ns + j] = zv[c];
+    }
+    acc[0].add(T(h.w) * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, rv, zv));
+  }
+  block_reduce_v<T, 1>(acc, partials);
+}
+
+// outer direction with an explicit preconditioned residual: S = Z + mu S; partial <K^-1 S, beta A S>
+template <class T>
+__global__ void __launch_bounds__(256) k_tl_dir(const cplx<T>* __restrict__ Z, cplx<T>* __restrict__ S, T mu,
+                                                Dims df, int regnorm, T beta, int kmode, T rw,
+                                                double* __restrict__ partials) {
+  Acc<T> acc[1];
+  FLOOP {
+    const HWave h = hwave(j, df);
+    const T ba = beta * hsym<T>(h, regnorm);
+    cplx<T> sw[3];
+    for (int c = 0; c < 3; ++c) {
+      const long long o = (long long)c * df.Ns + j;
+      const cplx<T> z = Z[o], sv = S[o];
+      sw[c] = mk<T>(fma(mu, sv.x, z.x), fma(mu, sv.y, z.y));
+      S[o] = sw[c];
+    }
+    acc[0].add(T(h.w) * ba * kinv_dot<T>(kinv_s<T>(kmode, rw, h), h, sw, sw));
+  }
+  block_reduce_v<T, 1>(acc, partials);
+}
+#undef CLOOP
+#undef FLOOP
 #undef HLOOP
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -586,6 +759,63 @@ claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* 
   return CLAIRE_OK;
 }
 
+template <class T>
+claire_status tl_restrict(claire_ctx* c, claire_ctx* cc, const cplx<T>* R, cplx<T>* F, cplx<T>* P, cplx<T>* X,
+                          int ncomp, bool split, double* partials, cudaStream_t st) {
+  cc->prof_begin("tl_restrict", st);
+  k_tl_restrict<T><<<kReduceBlocks, 256, 0, st>>>(R, F, P, X, ncomp, c->d, cc->d, split ? 1 : 0, c->o.regnorm,
+                                                  T(c->o.beta), kmode_of(c), T(rw_of(c)),
+                                                  T(double(cc->d.N) / double(c->d.N)), partials);
+  CL_LAUNCHED(cc);
+  return CLAIRE_OK;
+}
+template <class T> claire_status tl_scale(claire_ctx* cc, const cplx<T>* P, cplx<T>* U, cudaStream_t st) {
+  cc->prof_begin("tl_scale", st);
+  k_tl_scale<T><<<kReduceBlocks, 256, 0, st>>>(P, U, cc->d, cc->o.regnorm, T(cc->o.beta));
+  CL_LAUNCHED(cc);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status tl_apply(claire_ctx* cc, const cplx<T>* P, const cplx<T>* Bt, cplx<T>* HP, double* partials,
+                       cudaStream_t st) {
+  cc->prof_begin("tl_apply", st);
+  k_tl_apply<T><<<kReduceBlocks, 256, 0, st>>>(P, Bt, HP, cc->d, cc->o.regnorm, T(cc->o.beta), kmode_of(cc),
+                                               T(rw_of(cc)), partials);
+  CL_LAUNCHED(cc);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status tl_update(claire_ctx* cc, cplx<T>* X, cplx<T>* Rr, const cplx<T>* P, const cplx<T>* HP, double alpha,
+                        double* partials, cudaStream_t st) {
+  cc->prof_begin("tl_update", st);
+  k_tl_update<T><<<kReduceBlocks, 256, 0, st>>>(X, Rr, P, HP, T(alpha), cc->d, kmode_of(cc), T(rw_of(cc)), partials);
+  CL_LAUNCHED(cc);
+  return CLAIRE_OK;
+}
+template <class T> claire_status tl_dir2(claire_ctx* cc, const cplx<T>* Rr, cplx<T>* P, double mu, cudaStream_t st) {
+  cc->prof_begin("tl_dir2", st);
+  k_tl_dir2<T><<<kReduceBlocks, 256, 0, st>>>(Rr, P, T(mu), cc->d);
+  CL_LAUNCHED(cc);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status tl_prolong(claire_ctx* c, claire_ctx* cc, const cplx<T>* R, const cplx<T>* X, cplx<T>* Z,
+                         double* partials, cudaStream_t st) {
+  c->prof_begin("tl_prolong", st);
+  k_tl_prolong<T><<<kReduceBlocks, 256, 0, st>>>(R, X, Z, c->d, cc->d, c->o.regnorm, T(c->o.beta), kmode_of(c),
+                                                 T(rw_of(c)), T(double(c->d.N) / double(cc->d.N)), partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
+claire_status tl_dir(claire_ctx* c, const cplx<T>* Z, cplx<T>* S, double mu, double* partials, cudaStream_t st) {
+  c->prof_begin("tl_dir", st);
+  k_tl_dir<T><<<kReduceBlocks, 256, 0, st>>>(Z, S, T(mu), c->d, c->o.regnorm, T(c->o.beta), kmode_of(c),
+                                             T(rw_of(c)), partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+
 #define INST(T)                                                                                                   \
   template claire_status sp_grad<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, double*, cudaStream_t); \
   template claire_status sp_pcg0<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, double*,           \
@@ -604,7 +834,18 @@ claire_status sp_copy_reg(claire_ctx* c, const cplx<T>* V, cplx<T>* Sc, double* 
   template claire_status spec_kop<T>(claire_ctx*, cplx<T>*, cplx<T>*, cplx<T>*, cudaStream_t);                   \
   template claire_status spec_scale<T>(claire_ctx*, cplx<T>*, int, long long, int, double, cudaStream_t);        \
   template claire_status spec_combine<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cudaStream_t);                   \
-  template claire_status spec_reg_partial<T>(claire_ctx*, const cplx<T>*, double*, cudaStream_t);
+  template claire_status spec_reg_partial<T>(claire_ctx*, const cplx<T>*, double*, cudaStream_t);                \
+  template claire_status tl_restrict<T>(claire_ctx*, claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*,  \
+                                        int, bool, double*, cudaStream_t);                                       \
+  template claire_status tl_scale<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cudaStream_t);                       \
+  template claire_status tl_apply<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, double*,            \
+                                     cudaStream_t);                                                              \
+  template claire_status tl_update<T>(claire_ctx*, cplx<T>*, cplx<T>*, const cplx<T>*, const cplx<T>*, double,  \
+                                      double*, cudaStream_t);                                                    \
+  template claire_status tl_dir2<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double, cudaStream_t);                \
+  template claire_status tl_prolong<T>(claire_ctx*, claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*,      \
+                                       double*, cudaStream_t);                                                   \
+  template claire_status tl_dir<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double, double*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

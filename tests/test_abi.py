@@ -41,13 +41,14 @@ def test_default_opts_are_the_papers(L):
     assert L.claire_default_opts(ctypes.byref(o), 32, 32, 32, 0) == 0
     assert (o.nt, o.regnorm, o.divfree, o.max_gn, o.max_krylov, o.max_ls) == (4, 1, 0, 50, 100, 10)
     assert (o.gtol_rel, o.gtol_abs, o.armijo_c1) == (5e-2, 1e-6, 1e-4)
+    assert (o.beta_w, o.precond, o.pc_kappa) == (0.0, 0, 0.1)
 
 
 @pytest.mark.parametrize("bad", [
     dict(n=(31, 32, 32)), dict(n=(2, 32, 32)), dict(n=(22, 32, 32)), dict(nt=0), dict(beta=0.0), dict(beta=-1.0),
     dict(regnorm=3), dict(divfree=2), dict(precision=5), dict(max_krylov=0), dict(max_ls=0), dict(bf16_mask=2),
     dict(bf16_mask=1, precision=1), dict(beta_w=-1e-4), dict(beta_w=1e-4, divfree=1),
-    dict(beta_w=1e-4, regnorm=2)])
+    dict(beta_w=1e-4, regnorm=2), dict(precond=2), dict(precond=1, n=(18, 16, 16)), dict(precond=1, n=(4, 16, 16)), dict(precond=1, pc_kappa=1.5)])
 def test_create_rejects_bad_options_before_any_device_call(L, bad):
     import paper_1808_04487_gb300 as pkg
     o = pkg.Opts()
