@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the two-level preconditioner variant")
     ap.add_argument("--study", default=None, choices=[None, "precision", "batch", "warmstart", "models"],
                     help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path; batch: 64 "
                          "population-to-atlas pairs on uneven grids, batched vs sequential; warmstart: train the "
@@ -114,12 +115,16 @@ def algorithmic_bytes(name, n, word=4):
     return None
 
 
+# the sources that define the semi-Lagrangian gather kernels (the dominant kernels of the bench): DRAM traffic
+# recorded in profiles/dram_traffic.txt is valid only for the digest of these files it was taken with
+GATHER_SOURCES = ("common.cuh", "sl_kernels.cuh", "sl.cu", "sl_h2.cu", "sl_h3.cu", "sl_h4.cu", "sl_h5.cu")
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1808_04487_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in GATHER_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -712,6 +717,7 @@ def main():
     prof = ctx.profile_report()
     ctx.profile(False)
     launches = ctx.launches() - launches0
+    gather = ctx.gather_schedule()
     clk = clocks.stop()
     ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
@@ -779,6 +785,28 @@ def main():
         e2e = {"value": ems / 1e3 / world, "unit": "s", "h2d_bytes_per_step": 5 * N * 4 * world,
                "d2h_bytes_per_step": 3 * N * 4 * world}
 
+    # ---- variant: the same solve with the two-level preconditioner (Sec. 2.3.3), timed outside the headline
+    variants = None
+    if not args.no_variants:
+        ctx2 = pkg.Context(n, precision="f32", precond=1, **SOLVER_KW)
+        ctx2.register(mT, mR)
+        ts, r2 = [], None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, r2, st2 = ctx2.register(mT, mR)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        ctx2.close()
+        variants = {"two_level_preconditioner": {
+            "seconds": min(ts), "status": st2, "gn_iters": r2["gn_iters"], "matvecs": r2["matvecs"],
+            "coarse_matvecs": r2["coarse_matvecs"], "pde_solves": r2["pde_solves"], "gnorm_rel": r2["gnorm_rel"],
+            "mismatch_rel": r2["mismatch_rel"],
+            "note": "same workload and stopping test; coarse grid n/2, nested CG at 0.1 eps_H (Sec. 2.3.3)"}}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -795,8 +823,9 @@ def main():
                   "pde_solves": rep["pde_solves"], "ls_trials": rep["ls_trials"], "gnorm_rel": rep["gnorm_rel"],
                   "mismatch_rel": rep["mismatch_rel"]},
         "hessian_matvecs_per_s": 1e3 / matvec_ms, "hessian_matvec_ms": matvec_ms,
-        "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
-        "cpu_baseline": cb,
+        "roofline": roof, "kernels": kernels, "gather_schedule": gather, "clocks": clk, "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cb, "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -254,9 +254,13 @@ claire_status claire_fft_f64(claire_ctx* ctx, const double* f, double* spec, voi
 claire_status claire_ifft_f32(claire_ctx* ctx, const float* spec, float* f, void* stream);
 claire_status claire_ifft_f64(claire_ctx* ctx, const double* spec, double* f, void* stream);
 
-/* Number of kernel launches the library has made on this context since claire_create. */
+/* Kernel launches the library has made on this context (and its coarse context) since claire_create, and the
+ * gather schedule of the cached linearisation: the brick halo (voxels) of the shared-memory tiled gathers along X
+ * (state, incremental state) and Y (adjoints), or -1 where the plain gathers run (chosen per grid by timing both
+ * once; the environment variable CLAIRE_GATHER=plain or =tiled overrides the choice). */
 typedef struct {
     long long launches;
+    int halo_x, halo_y;
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 

@@ -57,7 +57,7 @@ class PairF32(ctypes.Structure):
 
 
 class Counters(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong)]
+    _fields_ = [("launches", ctypes.c_longlong), ("halo_x", ctypes.c_int), ("halo_y", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p
@@ -424,6 +424,12 @@ class Context:
         c = Counters()
         lib().claire_get_counters(self._h, ctypes.byref(c))
         return int(c.launches)
+
+    def gather_schedule(self):
+        """{"halo_x", "halo_y"}: brick halos of the tiled gathers of the cached linearisation (-1: plain)."""
+        c = Counters()
+        lib().claire_get_counters(self._h, ctypes.byref(c))
+        return {"halo_x": int(c.halo_x), "halo_y": int(c.halo_y)}
 
     def resample_to(self, dst, f, project=False, out=None, kmax=0):
         """f ([ncomp,] n) on this grid -> dst's grid by Fourier truncation / zero padding (FP32 contexts)."""

@@ -7,6 +7,7 @@
 // is reduced in FP64 on the device and read back once per use.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <atomic>
@@ -186,6 +187,12 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, bool> g_tune;
 
 template <class T> claire_status tune_tiling(claire_ctx* c, int H, bool* tiled, cudaStream_t st) {
+  if (const char* force = std::getenv("CLAIRE_GATHER")) {
+    if (std::strcmp(force, "plain") == 0 || std::strcmp(force, "tiled") == 0) {
+      *tiled = force[0] == 't';
+      return CLAIRE_OK;
+    }
+  }
   const auto key = std::make_tuple(c->d.n1, c->d.n2, c->d.n3, H, c->gm16_on ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -227,7 +234,10 @@ template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* 
   double D;
   CL_TRY(read_scalar(c, W.scal + 12, &D, st));
   *halo = (std::isfinite(D) && D < 64.0) ? (int)std::ceil(D + 1e-3) + 1 : -1;
-  if (*halo >= 0 && sizeof(T) == 4 && c->gm_ready) {
+  const char* force = std::getenv("CLAIRE_GATHER");
+  if (*halo >= 0 && force && std::strcmp(force, "plain") == 0) {
+    *halo = -1;
+  } else if (*halo >= 0 && sizeof(T) == 4 && c->gm_ready) {
     bool tiled = true;
     CL_TRY(tune_tiling<T>(c, *halo < 2 ? 2 : *halo, &tiled, st));
     if (!tiled) *halo = -1;
@@ -1142,6 +1152,8 @@ size_t claire_workspace_bytes(const claire_ctx* c) { return c ? c->arena_bytes :
 claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   if (!c || !out) return CLAIRE_EINVAL;
   out->launches = c->counters.launches + (c->coarse ? c->coarse->counters.launches : 0);
+  out->halo_x = c->haloX;
+  out->halo_y = c->haloY;
   return CLAIRE_OK;
 }
 
