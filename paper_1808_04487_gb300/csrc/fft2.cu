@@ -215,26 +215,21 @@ __global__ void __launch_bounds__(LPC * cmax<R1, R2>()) k_fft2_z_c2r(const cplx<
   const long long line = (long long)blockIdx.x * LPC + l;
   const bool ok = line < nlines;
   cplx<T>* Yl = Y + l * S;
-  if (ok) {
-    const cplx<T>* src = in + line * (L + 1);
-    for (int k = t; k <= L; k += TT) Yl[padi<R1>(k)] = src[k];
-  }
   __syncthreads();
-  // Z'[k] = (X[k] + conj X[L-k]) + i exp(+2 pi i k / n3) (X[k] - conj X[L-k]) for the stage-1 inputs k = t + r R2
+  // Z'[k] = (X[k] + conj X[L-k]) + i exp(+2 pi i k / n3) (X[k] - conj X[L-k]) for the stage-1 inputs k = t + r R2,
+  // read straight from global memory (the mirrored read X[L-k] of one thread is another thread's X[k]: L1 hits)
   cplx<T> v[R1];
   if (t < R2) {
+    const cplx<T>* src = in + line * (L + 1);
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
       const int k = t + r * R2;
-      const cplx<T> xk = Yl[padi<R1>(k)];
-      const cplx<T> xc = cconj<T>(Yl[padi<R1>(L - k)]);
+      const cplx<T> xk = ok ? src[k] : mk<T>(T(0), T(0));
+      const cplx<T> xc = ok ? cconj<T>(src[L - k]) : mk<T>(T(0), T(0));
       const cplx<T> sum = cadd<T>(xk, xc), dif = csub<T>(xk, xc);
       const cplx<T> wd = cmulc<T>(dif, W2[k]);
       v[r] = mk<T>(sum.x - wd.y, sum.y + wd.x);
     }
-  }
-  __syncthreads();
-  if (t < R2) {
     rdft<T, +1, R1, L>(v, W);
 #pragma unroll
     for (int q = 0; q < R1; ++q) Yl[padi<R1>(t * R1 + q)] = v[q];
