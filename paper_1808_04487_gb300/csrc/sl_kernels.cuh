@@ -301,9 +301,12 @@ template <int H> __device__ __forceinline__ Tile tile_or_empty(const Dims& d) {
   }
 }
 
+// Launch bounds of the gather kernels: 8 resident CTAs (32 registers) for the FP32 one-field gathers -- measured
+// 4-10% faster at 256^3 than the compiler's own 40-48 registers, since their long-scoreboard stalls want more warps;
+// 4 CTAs (64 registers) for FP64 and for the variants with more live state (RHO, last step), which spill at 32.
 template <class T, int H>
-__global__ void __launch_bounds__(256) k_interp(const T* __restrict__ f, const T* __restrict__ disp,
-                                                T* __restrict__ out, Dims d) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
+    k_interp(const T* __restrict__ f, const T* __restrict__ disp, T* __restrict__ out, Dims d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   const Tile tl = tile_or_empty<H>(d);
@@ -341,7 +344,8 @@ __global__ void __launch_bounds__(256) k_adj_terminal(const T* __restrict__ mR, 
 //   a = lam^{j+1}(Y); with the div source: c = (rho lam^{j+1})(Y), lam^j = a + dt/2 (c + rho(x)(a + dt c)).
 // Epilogue: optional store of lam^j and rho lam^j, and b += w_j lam^j grad m^j.
 template <class T, bool RHO, bool STORE, bool ACC, bool DOT, int H, class G>
-__global__ void __launch_bounds__(256) k_adj_step(const T* __restrict__ lam_next, const T* __restrict__ rl_next,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RHO) ? 8 : 4)
+    k_adj_step(const T* __restrict__ lam_next, const T* __restrict__ rl_next,
                                                   const T* __restrict__ rho, const T* __restrict__ dY,
                                                   T* __restrict__ lam, T* __restrict__ rl, T* __restrict__ b,
                                                   const G* __restrict__ gm, T w, T dt, Dims d,
@@ -411,7 +415,8 @@ __global__ void __launch_bounds__(256) k_inc_init(const T* __restrict__ vt, cons
 // m~^{j+1}(x) = q^j(X) + dt/2 f^{j+1}(x); not last: q^{j+1} = m~^{j+1} + dt/2 f^{j+1}.
 // last: lam~ = -m~(1) (Eq. (9) final condition), rl = rho lam~, b = w lam~ grad m^{nt}.
 template <class T, bool LAST, bool RHO, int H, class G>
-__global__ void __launch_bounds__(256) k_inc_step(const T* __restrict__ q, const T* __restrict__ dX,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && !LAST) ? 8 : 4)
+    k_inc_step(const T* __restrict__ q, const T* __restrict__ dX,
                                                   const T* __restrict__ vt, const G* __restrict__ gm,
                                                   T* __restrict__ qout, const T* __restrict__ rho,
                                                   T* __restrict__ rl, T* __restrict__ b, T hdt, T w, Dims d) {
