@@ -352,7 +352,7 @@ claire_status claire_ws_predict_f32(claire_ws* ws, claire_ctx* ctx, const float*
 /* The network's layers one by one (used to check each against a reference). BF16 tensors are passed as void*,
  * channels-last [B][n1][n2][n3][C]; C, Cin, Cout multiples of 16 in [16, 128]; B n1 n2 n3 a multiple of 16.
  * conv3_fwd: y (BF16) and/or yf (FP32; overwritten, or added to with accum = 1) = act(conv(x, w) + bias + skip),
- * w [Cout][27][Cin]; bias, skip, y, yf optional (y or yf required). conv3_wgrad: dw[Cout][27][Cin] =
+ * w [Cout][27][Cin]; bias, skip, y, yf optional (y or yf required); work optional (see below). conv3_wgrad: dw[Cout][27][Cin] =
  * sum over voxels of dz[m][co] x[nb(m, off)][ci] (work: claire_nn_wgrad_workspace_bytes). weight_flip: wt =
  * the weights of the adjoint convolution, [Cin][27][Cout]. relu_bwd: dz = dy where y > 0 (y NULL: everywhere),
  * FP32 dz and BF16 dzb. bias_grad: db[c] = sum_m dz[m][c] (work: claire_nn_bias_workspace_bytes). pool: 2x2x2
@@ -362,7 +362,10 @@ claire_status claire_ws_predict_f32(claire_ws* ws, claire_ctx* ctx, const float*
  * step number `step` >= 1; pb (optional) receives a BF16 copy of p. */
 claire_status claire_nn_conv3_fwd(const void* x, const void* w, const float* bias, const void* skip, void* y,
                                   float* yf, int accum, int B, int n1, int n2, int n3, int Cin, int Cout, int relu,
-                                  void* stream);
+                                  float* work, void* stream);
+/* work of claire_nn_conv3_fwd (device, may be NULL): grids with fewer 128-voxel tiles than about two per SM split
+ * the 27 neighbour offsets over CTAs and reduce the FP32 partial sums in a fixed order; 0 bytes when not needed */
+size_t claire_nn_fwd_workspace_bytes(int B, int n1, int n2, int n3, int Cout);
 size_t claire_nn_wgrad_workspace_bytes(int B, int n1, int n2, int n3, int Cin, int Cout);
 claire_status claire_nn_conv3_wgrad(const void* dz, const void* x, float* dw, float* work, int B, int n1, int n2,
                                     int n3, int Cin, int Cout, void* stream);
@@ -381,6 +384,10 @@ claire_status claire_nn_mse(const float* pred, const float* target, float* grad,
                             double* partials, int npartials, void* stream);
 claire_status claire_nn_adam(float* p, const float* g, float* m1, float* m2, void* pb, long long count, float lr,
                              float b1, float b2, float eps, int step, void* stream);
+/* Synchronises the stream, then reports whether a convolution's bounded tensor-core wait timed out since the last
+ * call (CLAIRE_ECUDA; the flag is cleared) or CLAIRE_OK. claire_ws_loss_f32 / _train_step_f32 (with a loss) and
+ * claire_ws_predict_f32 check it themselves. */
+claire_status claire_nn_status(void* stream);
 
 #ifdef __cplusplus
 }

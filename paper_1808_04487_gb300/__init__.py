@@ -112,7 +112,8 @@ _UNTYPED = {
     "claire_ws_adam_step": (_I, [_VP, _F, _VP]),
     "claire_ws_train_step_f32": (_I, [_VP, _VP, _VP, _PI, _I, _F, _PD, _VP]),
     "claire_ws_predict_f32": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _VP]),
-    "claire_nn_conv3_fwd": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _I, _I, _VP]),
+    "claire_nn_conv3_fwd": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _I, _I, _VP, _VP]),
+    "claire_nn_fwd_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I]),
     "claire_nn_wgrad_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I, _I]),
     "claire_nn_conv3_wgrad": (_I, [_VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
     "claire_nn_weight_flip": (_I, [_VP, _VP, _I, _I, _VP]),
@@ -125,6 +126,7 @@ _UNTYPED = {
     "claire_nn_up_bwd": (_I, [_VP, _VP, _I, _I, _I, _I, _I, _I, _VP]),
     "claire_nn_mse": (_I, [_VP, _VP, _VP, _LL, _I, _I, _VP, _I, _VP]),
     "claire_nn_adam": (_I, [_VP, _VP, _VP, _VP, _VP, _LL, _F, _F, _F, _F, _I, _VP]),
+    "claire_nn_status": (_I, [_VP]),
 }
 
 _lib = None

@@ -4,29 +4,35 @@
 //
 // Activations are channels-last BF16, gradients FP32 (rounded to BF16 where they feed a tensor-core product),
 // weights [Cout][27][Cin]. Convolutions are 3x3x3, stride 1, periodic (the registration domain is periodic), and
-// run as implicit GEMMs on the tensor cores through the warp-level WMMA interface (16x16x16 BF16 tiles, FP32
-// accumulators):
-//   forward  y[m, co] = sum_{off, ci} x[nb(m, off), ci] w[co, off, ci]      (M = voxels, N = Cout, K = 27 Cin)
+// run as implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma, BF16 operands staged in shared memory,
+// FP32 accumulators in tensor memory; tc.cuh):
+//   forward  y[m, co] = sum_{off, ci} x[nb(m, off), ci] w[co, off, ci]      (M = voxels, N = Cout, K = 27 Cin):
+//            a CTA owns 128 voxels; per neighbour offset it stages the 128 neighbour rows and the offset's
+//            Cout x Cin weight slice, and one thread issues Cin/16 MMAs into the 128 x Cout accumulator
 //   dgrad    the forward kernel applied to dz with w^T[ci, 26 - off, co] = w[co, off, ci]
-//   wgrad    dw[co, off, ci] = sum_m dz[m, co] x[nb(m, off), ci]           (K = voxels, split into chunks that
-//            are reduced in a fixed order, so the result does not depend on scheduling)
-// A 16-voxel tile is 16 consecutive voxels of the flattened batch; each row of a staged tile carries its own
-// periodic neighbour index, so no grid extent needs to be a multiple of 16.
+//   wgrad    dw[co, off, ci] = sum_m dz[m, co] x[nb(m, off), ci]           (M = Cout padded to 128, N = Cin,
+//            K = voxels): a CTA owns one offset and one chunk of voxels; chunks are summed in a fixed order,
+//            so results do not depend on scheduling
+// Every wait on the tensor core is bounded (about a second); a timeout sets an error flag that
+// claire_nn_status reports, and the CTA still waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
-#include <mma.h>
 
 #include <cmath>
 
 #include "impl.cuh"
 #include "nn.cuh"
+#include "tc.cuh"
 
 namespace claire {
 namespace nn {
 namespace {
 
-using namespace nvcuda;
-
 constexpr int kMaxC = 128;
+constexpr int kTileM = 128;                        // voxels (forward) or output channels (wgrad) per CTA
+constexpr int kTileK = 64;                         // voxels per K step of the weight gradient
+constexpr long long kWaitCycles = 2000000000LL;    // bound of every tensor-core wait (~1 s at 2 GHz)
+
+__device__ int g_nn_error = 0;                     // set by a CTA whose tensor-core wait timed out
 
 __device__ __forceinline__ int pw(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -50,98 +56,288 @@ __device__ __forceinline__ int nb_of(const Geo& g, const Vox& v, int off) {
   return ((v.b * g.n1 + pw(v.i1 + o1, g.n1)) * g.n2 + pw(v.i2 + o2, g.n2)) * g.n3 + pw(v.i3 + o3, g.n3);
 }
 
-// 4 warps per CTA, one 16-voxel tile per warp, NT tiles of 16 output channels per warp. For each of the 27
-// offsets the warp stages its 16 neighbour rows (all Cin channels, 16-byte vectors) in shared memory and runs
-// Cin/16 x NT tensor-core products; B fragments come from the weights through L1/L2.
-template <int NT>
-__global__ void __launch_bounds__(128) k_conv3_fwd(const bf16* __restrict__ x, const bf16* __restrict__ w,
-                                                   const float* __restrict__ bias, const bf16* __restrict__ skip,
-                                                   bf16* __restrict__ y, float* __restrict__ yf, int accum, Geo g,
-                                                   int Cin, int Cout, int relu) {
-  __shared__ __align__(128) bf16 As[4][16 * kMaxC];
-  __shared__ __align__(128) float Cs[4][256];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = (blockIdx.x * 4 + warp) * 16;
-  if (m0 >= g.M) return;
-  const int j = lane >> 1, h = lane & 1;
-  const Vox me = vox_of(g, m0 + j);
-  bf16* A = As[warp];
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) wmma::fill_fragment(acc[t], 0.0f);
-  const int kcb = Cin / 16, nvec = Cin / 8;
-  const long long ldb = 27LL * Cin;
-  for (int off = 0; off < 27; ++off) {
-    const uint4* src = reinterpret_cast<const uint4*>(x + (long long)nb_of(g, me, off) * Cin);
-    uint4* dst = reinterpret_cast<uint4*>(A + j * Cin);
-    for (int q = h; q < nvec; q += 2) dst[q] = src[q];
-    __syncwarp();
-    for (int cb = 0; cb < kcb; ++cb) {
-      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
-      wmma::load_matrix_sync(a, A + cb * 16, (unsigned)Cin);
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> bm;
-        wmma::load_matrix_sync(bm, w + (long long)t * 16 * ldb + off * Cin + cb * 16, (unsigned)ldb);
-        wmma::mma_sync(acc[t], a, bm, acc[t]);
+// Forward convolution on tcgen05: 128 threads; thread r stages row r (voxel m0 + r). Offsets [off0, off1) of the
+// 27 (split-K when the grid has few voxel tiles: blockIdx.y picks the range), taken G = group at a time so that
+// a K step spans G Cin = min(64, Cin) or more channels: the A tile row r holds x[nb(m0 + r, off), ci] for the G
+// offsets side by side (K index j Cin + ci), the B tile row co the matching contiguous run of w[co][off][ci]. Two
+// shared-memory stages {A [128 x KS], B [Cout x KS]}, KS = G Cin, as K-major core-matrix tiles, with one
+// mbarrier each: the staging of step i + 1 overlaps the MMAs of step i, and a stage is rewritten only after the
+// MMAs that read it have completed. Epilogue: with part == nullptr the full result (bias, skip, ReLU) goes to
+// y / yf; otherwise the raw FP32 partial sums go to part[blockIdx.y][m][co] for k_conv3_reduce.
+__global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict__ x, const bf16* __restrict__ w,
+                                                         const float* __restrict__ bias,
+                                                         const bf16* __restrict__ skip, bf16* __restrict__ y,
+                                                         float* __restrict__ yf, int accum, Geo g, int Cin, int Cout,
+                                                         int relu, int offs_per_split, int group,
+                                                         float* __restrict__ part) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
+  const int KS = group * Cin;  // K extent of a full step
+  const uint32_t a_bytes = (uint32_t)kTileM * KS * 2, b_bytes = (uint32_t)Cout * KS * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;  // a multiple of 512 (unswizzled tiles need 16-byte alignment)
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + 2 * stage_bytes);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tc::tmem_cols(Cout);
+  const uint32_t bar_a[2] = {tc::smem_addr(bar), tc::smem_addr(bar + 1)};
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
+  if (tid == 0) {
+    tc::mbar_init(bar_a[0], 1);
+    tc::mbar_init(bar_a[1], 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *slot;
+  const int m0 = blockIdx.x * kTileM;
+  const int m = m0 + tid;
+  const bool valid = m < g.M;
+  const Vox me = vox_of(g, valid ? m : 0);
+  const int nvec = Cin / 8;
+  const uint32_t kbytes = 16u * (uint32_t)KS;  // row-group stride of both tiles
+  const uint32_t idesc = tc::idesc_bf16(kTileM, Cout);
+  const uint32_t base = tc::smem_addr(sm);
+  const int off0 = blockIdx.y * offs_per_split;
+  const int off1 = off0 + offs_per_split < 27 ? off0 + offs_per_split : 27;
+  const int nsteps = (off1 - off0 + group - 1) / group;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  for (int i = 0; i < nsteps && ok; ++i) {
+    const int sidx = i & 1;
+    const int oa = off0 + i * group;
+    const int ob = oa + group < off1 ? oa + group : off1;
+    const int nk = (ob - oa) * Cin;  // K extent of this step
+    if (i >= 2) {
+      // the MMAs of step i - 2 read this stage
+      const bool mine = tc::mbar_wait(bar_a[sidx], phase[sidx], kWaitCycles);
+      phase[sidx] ^= 1u;
+      ok = __syncthreads_and(mine) != 0;
+      if (!ok) break;
+    }
+    unsigned char* As = sm + sidx * stage_bytes;
+    unsigned char* Bs = As + a_bytes;
+    for (int off = oa; off < ob; ++off) {
+      const uint4* src = reinterpret_cast<const uint4*>(x + (long long)nb_of(g, me, off) * Cin);
+      const int kb = (off - oa) * Cin;
+      for (int c = 0; c < nvec; ++c) {
+        const uint4 v = valid ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(As + tc::kmajor_offset(tid, kb + 8 * c, KS)) = v;
       }
     }
-    __syncwarp();
-  }
-  float* C = Cs[warp];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    wmma::store_matrix_sync(C, acc[t], 16, wmma::mem_row_major);
-    __syncwarp();
-    for (int e = lane; e < 256; e += 32) {
-      const int r = e >> 4, co = t * 16 + (e & 15);
-      const long long o = (long long)(m0 + r) * Cout + co;
-      float val = C[e];
-      if (bias) val += bias[co];
-      if (skip) val += __bfloat162float(skip[o]);
-      if (relu) val = fmaxf(val, 0.f);
-      if (y) y[o] = __float2bfloat16_rn(val);
-      if (yf) yf[o] = accum ? yf[o] + val : val;
+    const int nv = nk / 8;
+    for (int q = tid; q < Cout * nv; q += kTileM) {
+      const int co = q / nv, c = q - co * nv;
+      *reinterpret_cast<uint4*>(Bs + tc::kmajor_offset(co, 8 * c, KS)) =
+          *reinterpret_cast<const uint4*>(w + ((long long)co * 27 + oa) * Cin + 8 * c);
     }
-    __syncwarp();
+    tc::fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t a_s = base + sidx * stage_bytes, b_s = a_s + a_bytes;
+      for (int kk = 0; kk < nk / 16; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc(a_s + 256u * kk, 128u, kbytes), tc::smem_desc(b_s + 256u * kk, 128u, kbytes),
+                     idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      tc::commit(bar_a[sidx]);
+    }
+  }
+  // the last one or two stages in flight (their completion also covers every earlier MMA of the CTA)
+  if (ok) {
+    for (int sidx = 0; sidx < 2; ++sidx) {
+      const int issued = (nsteps + 1 - sidx) / 2;  // commits made on this stage's barrier
+      if (issued > 0) {
+        const bool mine = tc::mbar_wait(bar_a[sidx], phase[sidx], kWaitCycles);
+        phase[sidx] ^= 1u;
+        ok = ok && mine;
+      }
+    }
+    ok = __syncthreads_and(ok) != 0;
+  }
+  tc::fence_after();
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_nn_error, 1);
+    tc::mbar_wait(bar_a[0], phase[0], kWaitCycles);  // whatever is still in flight, bounded
+    tc::mbar_wait(bar_a[1], phase[1], kWaitCycles);
+  } else {
+    const int r = m0 + 32 * warp + lane;  // this lane's accumulator row
+    for (int c0 = 0; c0 < Cout; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+      if (r < g.M) {
+        if (part) {
+          float* dst = part + ((long long)blockIdx.y * g.M + r) * Cout + c0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) dst[j] = v[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int co = c0 + j;
+            const long long o = (long long)r * Cout + co;
+            float val = v[j];
+            if (bias) val += bias[co];
+            if (skip) val += __bfloat162float(skip[o]);
+            if (relu) val = fmaxf(val, 0.f);
+            if (y) y[o] = __float2bfloat16_rn(val);
+            if (yf) yf[o] = accum ? yf[o] + val : val;
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// split-K epilogue: out[m][co] = act(sum_s part[s][m][co] (s in order) + bias + skip)
+__global__ void k_conv3_reduce(const float* __restrict__ part, int nsplit, const float* __restrict__ bias,
+                               const bf16* __restrict__ skip, bf16* __restrict__ y, float* __restrict__ yf, int accum,
+                               long long count, int Cout, int relu) {
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < count;
+       o += (long long)gridDim.x * blockDim.x) {
+    float val = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) val += part[(long long)sp * count + o];
+    const int co = (int)(o % Cout);
+    if (bias) val += bias[co];
+    if (skip) val += __bfloat162float(skip[o]);
+    if (relu) val = fmaxf(val, 0.f);
+    if (y) y[o] = __float2bfloat16_rn(val);
+    if (yf) yf[o] = accum ? yf[o] + val : val;
   }
 }
 
-// Partial weight gradients of one voxel chunk (grid.y): warp task (ct, off, it) accumulates the 16 x 16 block
-// dw[ct*16.., off, it*16..] over the chunk's 16-voxel tiles.
-__global__ void __launch_bounds__(128) k_conv3_wgrad(const bf16* __restrict__ dz, const bf16* __restrict__ x,
-                                                     float* __restrict__ part, Geo g, int Cin, int Cout,
-                                                     int chunk) {
-  __shared__ __align__(128) bf16 Bs[4][256];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncit = Cin / 16;
-  const int ntask = (Cout / 16) * 27 * ncit;
-  const int task = blockIdx.x * 4 + warp;
-  if (task >= ntask) return;
-  const int ct = task / (27 * ncit);
-  const int rem = task - ct * 27 * ncit;
-  const int off = rem / ncit, it = rem - off * ncit;
-  const int j = lane >> 1, h = lane & 1;
-  bf16* Bt = Bs[warp];
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
-  wmma::fill_fragment(acc, 0.0f);
+// Partial weight gradients on tcgen05. CTA (offset group og = blockIdx.x, voxel chunk blockIdx.y) handles the
+// G = group offsets off = og G + j (those below 27) at once: the 128 x Cout accumulator row j Cin + ci holds
+//   D[j Cin + ci, co] = sum over the chunk's voxels m of x[nb(m, off), ci] dz[m, co]
+// (rows past the group's last offset stay zero), built in K steps of 64 voxels, then written to
+// part[chunk][co][off][ci]. Both operands are staged as they lie in memory, channel index contiguous, i.e.
+// MN-major: tile A holds 8-channel x 8-voxel core matrices at (row / 8) * 128 + (k / 8) * 2048 bytes, tile B
+// likewise with the Cout channels of dz; thread t copies the 16-byte channel groups of voxel t % 64 (half t / 64
+// of them). In the unswizzled MN-major layout the descriptor's leading offset steps along K (8-voxel groups) and
+// its stride offset along M / N. Two stages with one mbarrier each: the loads of step s + 1 overlap the MMAs of s.
+__global__ void __launch_bounds__(128, 1) k_conv3_wgrad_tc(const bf16* __restrict__ dz, const bf16* __restrict__ x,
+                                                           float* __restrict__ part, Geo g, int Cin, int Cout,
+                                                           int group, int chunk) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
+  constexpr uint32_t a_bytes = kTileM * kTileK * 2;  // 16 KB
+  const uint32_t b_bytes = (uint32_t)Cout * kTileK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + 2 * stage_bytes);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int off_first = blockIdx.x * group;
+  const int ng = 27 - off_first < group ? 27 - off_first : group;  // offsets of this group
+  const uint32_t ncols = tc::tmem_cols(Cout);
+  const uint32_t bar_a[2] = {tc::smem_addr(bar), tc::smem_addr(bar + 1)};
+  // rows past ng Cin of A are zero for every step: clear both A tiles once
+  for (int s = 0; s < 2; ++s)
+    for (int q = tid; q < (int)(a_bytes / 16); q += kTileM)
+      reinterpret_cast<uint4*>(sm + s * stage_bytes)[q] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
+  if (tid == 0) {
+    tc::mbar_init(bar_a[0], 1);
+    tc::mbar_init(bar_a[1], 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *slot;
+  // MN-major operands: bit 15 (A) and bit 16 (B) of the instruction descriptor
+  const uint32_t idesc = tc::idesc_bf16(kTileM, Cout) | (1u << 15) | (1u << 16);
+  const uint32_t base = tc::smem_addr(sm);
+  const uint32_t a_kgroup = 16u * kTileM, b_kgroup = 16u * (uint32_t)Cout;  // bytes between 8-voxel groups
+  const int k = tid & (kTileK - 1), half = tid >> 6;
   const int c0 = blockIdx.y * chunk;
   const int c1 = (long long)c0 + chunk < g.M ? c0 + chunk : (int)g.M;
-  for (int m0 = c0; m0 < c1; m0 += 16) {
-    const Vox me = vox_of(g, m0 + j);
-    *reinterpret_cast<uint4*>(Bt + j * 16 + h * 8) =
-        *reinterpret_cast<const uint4*>(x + (long long)nb_of(g, me, off) * Cin + it * 16 + h * 8);
-    __syncwarp();
-    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> a;  // (co, m) = dz[m][co]
-    wmma::load_matrix_sync(a, dz + (long long)m0 * Cout + ct * 16, (unsigned)Cout);
-    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> bm;  // (m, ci)
-    wmma::load_matrix_sync(bm, Bt, 16);
-    wmma::mma_sync(acc, a, bm, acc);
-    __syncwarp();
+  const int nsteps = (c1 - c0 + kTileK - 1) / kTileK;
+  const uint32_t kpos = (uint32_t)(k & 7) * 16u;  // K row of the voxel inside its core matrix
+  const int cvec = Cin / 8, nva = ng * cvec, nvb = Cout / 8;  // 16-byte vectors of one voxel
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  for (int s = 0; s < nsteps && ok; ++s) {
+    const int sidx = s & 1;
+    const int mv = c0 + s * kTileK + k;
+    const bool valid = mv < c1;
+    const Vox me = vox_of(g, valid ? mv : c0);
+    // issue this step's loads before waiting for the stage
+    uint4 va[8], vb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int v = half + 2 * q;
+      va[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (valid && v < nva) {
+        const int j = v / cvec, cv = v - j * cvec;
+        va[q] = *reinterpret_cast<const uint4*>(x + (long long)nb_of(g, me, off_first + j) * Cin + 8 * cv);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int v = half + 2 * q;
+      vb[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (valid && v < nvb) vb[q] = *reinterpret_cast<const uint4*>(dz + (long long)mv * Cout + 8 * v);
+    }
+    if (s >= 2) {
+      // the MMAs of step s - 2 read this stage
+      const bool mine = tc::mbar_wait(bar_a[sidx], phase[sidx], kWaitCycles);
+      phase[sidx] ^= 1u;
+      ok = __syncthreads_and(mine) != 0;
+      if (!ok) break;
+    }
+    unsigned char* As = sm + sidx * stage_bytes;
+    unsigned char* Bs = As + a_bytes;
+    const uint32_t koff_a = (uint32_t)(k >> 3) * a_kgroup + kpos, koff_b = (uint32_t)(k >> 3) * b_kgroup + kpos;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int v = half + 2 * q;
+      if (v < nva) {
+        const int j = v / cvec, cv = v - j * cvec;
+        *reinterpret_cast<uint4*>(As + ((j * Cin + 8 * cv) >> 3) * 128 + koff_a) = va[q];
+      }
+      if (v < nvb) *reinterpret_cast<uint4*>(Bs + v * 128 + koff_b) = vb[q];
+    }
+    tc::fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t a_s = base + sidx * stage_bytes, b_s = a_s + a_bytes;
+      for (int kk = 0; kk < kTileK / 16; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc(a_s + 2u * a_kgroup * kk, a_kgroup, 128u),
+                     tc::smem_desc(b_s + 2u * b_kgroup * kk, b_kgroup, 128u), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+      tc::commit(bar_a[sidx]);
+    }
   }
-  const long long ldo = 27LL * Cin;
-  float* dst = part + (long long)blockIdx.y * Cout * ldo + (long long)(ct * 16) * ldo + off * Cin + it * 16;
-  wmma::store_matrix_sync(dst, acc, (unsigned)ldo, wmma::mem_row_major);
+  if (ok) {
+    for (int sidx = 0; sidx < 2; ++sidx) {
+      if ((nsteps + 1 - sidx) / 2 > 0) {  // one commit on this stage's barrier is still unwaited
+        const bool mine = tc::mbar_wait(bar_a[sidx], phase[sidx], kWaitCycles);
+        phase[sidx] ^= 1u;
+        ok = ok && mine;
+      }
+    }
+    ok = __syncthreads_and(ok) != 0;
+  }
+  tc::fence_after();
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_nn_error, 1);
+    tc::mbar_wait(bar_a[0], phase[0], kWaitCycles);  // whatever is still in flight, bounded
+    tc::mbar_wait(bar_a[1], phase[1], kWaitCycles);
+  } else if (nsteps > 0) {
+    const int r = 32 * warp + lane;  // accumulator row j Cin + ci
+    const int j = r / Cin, ci = r - j * Cin;
+    float* dst = part + (long long)blockIdx.y * Cout * 27 * Cin + (long long)(off_first + j) * Cin + ci;
+    for (int n0 = 0; n0 < Cout; n0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)n0, v);
+      if (j < ng) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) dst[(long long)(n0 + jj) * 27 * Cin] = v[jj];
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
 // dst[i] = sum_c part[c][i], c in order
@@ -337,59 +533,105 @@ inline unsigned nblocks(long long n) {
   return (unsigned)(b < 4864 ? (b > 0 ? b : 1) : 4864);
 }
 
-// chunk of the weight-gradient split: about 8 resident CTAs per SM over all chunks, whole 16-voxel tiles
-inline int wgrad_chunk(const Geo& g, int Cin, int Cout) {
-  const long long ctas = ((long long)(Cout / 16) * 27 * (Cin / 16) + 3) / 4;
-  long long nchunks = (1216 + ctas - 1) / ctas;
-  const long long tiles = g.M / 16;
-  if (nchunks > tiles) nchunks = tiles;
-  if (nchunks < 1) nchunks = 1;
-  const long long per = (tiles + nchunks - 1) / nchunks;
-  return (int)(per * 16);
+// offsets per CTA of the weight gradient: as many as fill the 128 accumulator rows (G Cin <= 128), at most 27
+inline int wgrad_group(int Cin) {
+  const int G = kTileM / Cin;
+  return G > 27 ? 27 : (G < 1 ? 1 : G);
 }
+// voxels per CTA of the weight gradient: about two CTAs per SM over the offset groups x chunks, whole K steps
+inline int wgrad_chunk(const Geo& g, int Cin) {
+  const long long ngroups = (27 + wgrad_group(Cin) - 1) / wgrad_group(Cin);
+  const long long target = (2 * 152 + ngroups - 1) / ngroups;
+  long long per = (g.M + target - 1) / target;
+  per = (per + kTileK - 1) / kTileK * kTileK;
+  return (int)(per < kTileK ? kTileK : per);
+}
+// neighbour offsets per K step of the forward convolution: a step spans at least 64 channels when Cin allows
+inline int fwd_group(int Cin) { return Cin < 64 ? (64 / Cin > 0 ? 64 / Cin : 1) : 1; }
+
+inline size_t fwd_smem(int Cin, int Cout) {
+  const size_t KS = size_t(fwd_group(Cin)) * Cin;
+  return 1024 + 2 * (size_t(kTileM) * KS * 2 + size_t(Cout) * KS * 2) + 32;
+}
+// neighbour offsets per CTA of the forward convolution: all 27, or a split over blockIdx.y (partial sums reduced by
+// k_conv3_reduce) when a batch of 8 of these grids has fewer voxel tiles than about two CTAs per SM. The choice
+// depends on the grid, not on the batch size, so a sample's result does not depend on the batch it is in.
+inline int fwd_offsets_per_split(const Geo& g) {
+  const long long per_sample = g.M / g.B;
+  const long long tiles = (8 * per_sample + kTileM - 1) / kTileM;
+  if (tiles >= 2 * 152) return 27;
+  long long split = (2 * 152 + tiles - 1) / tiles;
+  if (split > 27) split = 27;
+  return (int)((27 + split - 1) / split);
+}
+inline size_t wgrad_smem(int Cout) { return 1024 + 2 * (size_t(kTileM) * kTileK * 2 + size_t(Cout) * kTileK * 2) + 32; }
 
 }  // namespace
 
+size_t fwd_work_elems(const Geo& g, int Cout) {
+  const int per = fwd_offsets_per_split(g);
+  const int nsplit = (27 + per - 1) / per;
+  return nsplit > 1 ? size_t(nsplit) * size_t(g.M) * size_t(Cout) : 0;
+}
+
 cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf16* skip, bf16* y, float* yf,
-                      int accum, const Geo& g, int Cin, int Cout, int relu, cudaStream_t st) {
-  const unsigned grid = (unsigned)((g.M / 16 + 3) / 4);
-#define CL_CONV_CASE(NT)                                                                                         \
-  case NT:                                                                                                       \
-    k_conv3_fwd<NT><<<grid, 128, 0, st>>>(x, w, bias, skip, y, yf, accum, g, Cin, Cout, relu);                   \
-    break;
-  switch (Cout / 16) {
-    CL_CONV_CASE(1)
-    CL_CONV_CASE(2)
-    CL_CONV_CASE(3)
-    CL_CONV_CASE(4)
-    CL_CONV_CASE(5)
-    CL_CONV_CASE(6)
-    CL_CONV_CASE(7)
-    CL_CONV_CASE(8)
-    default: return cudaErrorInvalidValue;
+                      int accum, const Geo& g, int Cin, int Cout, int relu, float* work, cudaStream_t st) {
+  static const cudaError_t attr = cudaFuncSetAttribute(k_conv3_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)fwd_smem(kMaxC, kMaxC));
+  if (attr != cudaSuccess) return attr;
+  const unsigned tiles = (unsigned)((g.M + kTileM - 1) / kTileM);
+  const int per = work ? fwd_offsets_per_split(g) : 27;
+  const int nsplit = (27 + per - 1) / per;
+  if (nsplit == 1) {
+    k_conv3_fwd_tc<<<dim3(tiles, 1u), kTileM, fwd_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf, accum, g, Cin,
+                                                                         Cout, relu, 27, fwd_group(Cin), nullptr);
+    return cudaGetLastError();
   }
-#undef CL_CONV_CASE
+  k_conv3_fwd_tc<<<dim3(tiles, (unsigned)nsplit), kTileM, fwd_smem(Cin, Cout), st>>>(x, w, nullptr, nullptr, nullptr,
+                                                                                      nullptr, 0, g, Cin, Cout, 0,
+                                                                                      per, fwd_group(Cin), work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long count = g.M * Cout;
+  k_conv3_reduce<<<nblocks(count), 256, 0, st>>>(work, nsplit, bias, skip, y, yf, accum, count, Cout, relu);
   return cudaGetLastError();
 }
 
 size_t wgrad_work_elems(const Geo& g, int Cin, int Cout) {
-  const long long chunk = wgrad_chunk(g, Cin, Cout);
+  const long long chunk = wgrad_chunk(g, Cin);
   const long long nchunks = (g.M + chunk - 1) / chunk;
   return size_t(nchunks) * size_t(Cout) * 27 * size_t(Cin);
 }
 
 cudaError_t conv3_wgrad(const bf16* dz, const bf16* x, float* dw, float* work, const Geo& g, int Cin, int Cout,
                         cudaStream_t st) {
-  const int chunk = wgrad_chunk(g, Cin, Cout);
+  static const cudaError_t attr = cudaFuncSetAttribute(k_conv3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)wgrad_smem(kMaxC));
+  if (attr != cudaSuccess) return attr;
+  const int group = wgrad_group(Cin);
+  const int chunk = wgrad_chunk(g, Cin);
   const int nchunks = (int)((g.M + chunk - 1) / chunk);
-  const int ntask = (Cout / 16) * 27 * (Cin / 16);
-  k_conv3_wgrad<<<dim3((unsigned)((ntask + 3) / 4), (unsigned)nchunks), 128, 0, st>>>(dz, x, work, g, Cin, Cout,
-                                                                                        chunk);
+  const unsigned ngroups = (unsigned)((27 + group - 1) / group);
+  k_conv3_wgrad_tc<<<dim3(ngroups, (unsigned)nchunks), kTileM, wgrad_smem(Cout), st>>>(dz, x, work, g, Cin, Cout,
+                                                                                       group, chunk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long count = 27LL * Cin * Cout;
   k_sum_chunks<<<nblocks(count), 256, 0, st>>>(work, nchunks, count, dw);
   return cudaGetLastError();
+}
+
+cudaError_t status(cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  int flag = 0, zero = 0;
+  e = cudaMemcpyFromSymbol(&flag, g_nn_error, sizeof(int));
+  if (e != cudaSuccess) return e;
+  if (flag) {
+    cudaMemcpyToSymbol(g_nn_error, &zero, sizeof(int));
+    return cudaErrorLaunchTimeout;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t weight_flip(const bf16* w, bf16* wt, int Cin, int Cout, cudaStream_t st) {
@@ -484,15 +726,24 @@ inline bool pool_args(int B, int n1, int n2, int n3) {
 
 extern "C" {
 
+claire_status claire_nn_status(void* stream) { return st_of(status((cudaStream_t)stream)); }
+
+size_t claire_nn_fwd_workspace_bytes(int B, int n1, int n2, int n3, int Cout) {
+  if (!geo_args(B, n1, n2, n3) || !conv_chan_ok(Cout)) return 0;
+  const Geo g = mkgeo(B, n1, n2, n3);
+  if (!conv_geo_ok(g)) return 0;
+  return fwd_work_elems(g, Cout) * sizeof(float);
+}
+
 claire_status claire_nn_conv3_fwd(const void* x, const void* w, const float* bias, const void* skip, void* y,
                                   float* yf, int accum, int B, int n1, int n2, int n3, int Cin, int Cout, int relu,
-                                  void* stream) {
+                                  float* work, void* stream) {
   if (!x || !w || (!y && !yf) || !geo_args(B, n1, n2, n3)) return CLAIRE_EINVAL;
   const Geo g = mkgeo(B, n1, n2, n3);
   if (!conv_geo_ok(g) || !conv_chan_ok(Cin) || !conv_chan_ok(Cout)) return CLAIRE_EINVAL;
   return st_of(conv3_fwd(static_cast<const bf16*>(x), static_cast<const bf16*>(w), bias,
                          static_cast<const bf16*>(skip), static_cast<bf16*>(y), yf, accum ? 1 : 0, g, Cin, Cout,
-                         relu ? 1 : 0, (cudaStream_t)stream));
+                         relu ? 1 : 0, work, (cudaStream_t)stream));
 }
 
 size_t claire_nn_wgrad_workspace_bytes(int B, int n1, int n2, int n3, int Cin, int Cout) {

@@ -1,5 +1,6 @@
 // Layer kernels of the learned warm start (nn.cu) and the shapes they share with the network runtime
 // (warmstart.cu). Not part of the paper's method: the network only proposes the initial velocity of Alg. 1.
+// The convolutions run on the tcgen05 tensor cores (tc.cuh).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -25,8 +26,10 @@ inline bool conv_chan_ok(int C) { return C >= 16 && C <= 128 && C % 16 == 0; }
 
 // y = act(conv3x3x3_periodic(x, w) + bias + skip). x, skip, y BF16 [M][Cin|Cout]; w BF16 [Cout][27][Cin];
 // yf (optional) FP32 [M][Cout], overwritten (accum = 0) or added to (accum = 1). relu applies to y and yf.
+// work (fwd_work_elems floats, may be null: no split) holds the split-K partial sums of grids with few voxel tiles.
+size_t fwd_work_elems(const Geo& g, int Cout);
 cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf16* skip, bf16* y, float* yf,
-                      int accum, const Geo& g, int Cin, int Cout, int relu, cudaStream_t st);
+                      int accum, const Geo& g, int Cin, int Cout, int relu, float* work, cudaStream_t st);
 // dw[Cout][27][Cin] = sum_m dz[m][co] x[nb(m, off)][ci] (FP32), computed in fixed-size voxel chunks reduced in a
 // fixed order; work holds wgrad_work_elems() floats.
 size_t wgrad_work_elems(const Geo& g, int Cin, int Cout);
@@ -60,6 +63,9 @@ cudaError_t unpack(const float* src, float* dst, long long M, int ncomp, int C, 
 // planar FP32 [ncomp][M] -> channels-last FP32 [M][ncomp], scaled by s
 cudaError_t interleave(const float* src, float* dst, long long M, int ncomp, float s, cudaStream_t st);
 cudaError_t add(const float* a, float* b, long long count, cudaStream_t st);
+// synchronises st, then reports (and clears) a timed-out tensor-core wait of the convolution kernels
+// (cudaErrorLaunchTimeout)
+cudaError_t status(cudaStream_t st);
 cudaError_t to_bf16(const float* a, bf16* b, long long count, cudaStream_t st);
 
 }  // namespace nn

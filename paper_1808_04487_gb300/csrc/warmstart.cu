@@ -230,7 +230,7 @@ claire_status forward(claire_ws* w, const float* images, const int* idx, int nb,
       const Layer& l = w->layers[op.layer];
       WS_CUDA(w, nn::conv3_fwd(w->T[l.in].y, w->Pb + l.woff, w->P + l.boff, l.skip >= 0 ? w->T[l.skip].y : nullptr,
                                l.out >= 0 ? w->T[l.out].y : nullptr, l.out >= 0 ? nullptr : w->pred, 0,
-                               w->geo(l.level, nb), l.cin, l.cout, l.relu, st));
+                               w->geo(l.level, nb), l.cin, l.cout, l.relu, w->work, st));
     } else if (op.kind == 1) {
       const Tensor& ti = w->T[op.in];
       WS_CUDA(w, nn::pool_fwd(ti.y, w->T[op.out].y, w->geo(ti.level, nb), ti.C, st));
@@ -244,7 +244,7 @@ claire_status forward(claire_ws* w, const float* images, const int* idx, int nb,
 
 claire_status read_loss(claire_ws* w, double* loss, cudaStream_t st) {
   WS_CUDA(w, cudaMemcpyAsync(w->hpart, w->part, sizeof(double) * claire_ws::kParts, cudaMemcpyDeviceToHost, st));
-  WS_CUDA(w, cudaStreamSynchronize(st));
+  WS_CUDA(w, nn::status(st));
   double s = 0.0;
   for (int i = 0; i < claire_ws::kParts; ++i) s += w->hpart[i];
   *loss = s;
@@ -277,7 +277,7 @@ claire_status loss_grad(claire_ws* w, const float* images, const float* targets,
         if (l.in != 0) {
           WS_CUDA(w, nn::weight_flip(w->Pb + l.woff, w->Wt + l.woff, l.cin, l.cout, st));
           WS_CUDA(w, nn::conv3_fwd(w->dzb, w->Wt + l.woff, nullptr, nullptr, nullptr, w->T[l.in].g,
-                                   written[l.in], g, l.cout, l.cin, 0, st));
+                                   written[l.in], g, l.cout, l.cin, 0, w->work, st));
           written[l.in] = 1;
         }
         if (l.skip >= 0) {
@@ -337,6 +337,8 @@ claire_status claire_ws_create(int batch, int n1, int n2, int n3, float vscale, 
     const nn::Geo g = w->geo(l.level, batch);
     work = std::max(work, nn::wgrad_work_elems(g, l.cin, l.cout));
     work = std::max(work, nn::bias_work_elems(l.cout));
+    work = std::max(work, nn::fwd_work_elems(g, l.cout));  // forward split-K partials
+    work = std::max(work, nn::fwd_work_elems(g, l.cin));   // input-gradient (adjoint convolution) partials
     dmax = std::max(dmax, size_t(g.M) * l.cout);
   }
   for (Tensor& t : w->T) {
@@ -493,6 +495,7 @@ claire_status claire_ws_predict_f32(claire_ws* w, claire_ctx* ctx, const float* 
   CL_TRY(resample(ctx, w->net, mR, w->img + N0, 1, false, 0, st));
   CL_TRY(forward(w, w->img, nullptr, 1, st));
   WS_CUDA(w, nn::unpack(w->pred, w->vnet, N0, 3, 16, 1.f / w->vscale, st));
+  WS_CUDA(w, nn::status(st));
   return resample(w->net, ctx, w->vnet, v, 3, ctx->o.divfree != 0, kmax, st);
 }
 

@@ -47,8 +47,11 @@ def conv3_fwd(x, w, bias=None, skip=None, relu=False, y=None, yf=None, accum=Fal
     """y / yf = act(conv3(x, w) + bias + skip); x [B, n1, n2, n3, Cin] bf16, w [Cout, 27, Cin] bf16."""
     B, n1, n2, n3, cin = x.shape
     cout = w.shape[0]
+    nbytes = lib().claire_nn_fwd_workspace_bytes(B, n1, n2, n3, cout)
+    work = _torch().empty(nbytes // 4, dtype=_torch().float32, device="cuda") if nbytes else None
     _ok(lib().claire_nn_conv3_fwd(_ptr(x), _ptr(w), _ptr(bias), _ptr(skip), _ptr(y), _ptr(yf), int(bool(accum)), B,
-                                  n1, n2, n3, cin, cout, int(bool(relu)), _stream()), "claire_nn_conv3_fwd")
+                                  n1, n2, n3, cin, cout, int(bool(relu)), _ptr(work), _stream()), "claire_nn_conv3_fwd")
+    _ok(lib().claire_nn_status(_stream()), "claire_nn_conv3_fwd: tensor-core wait timed out")
     return y, yf
 
 
@@ -61,6 +64,7 @@ def conv3_wgrad(dz, x):
     dw = torch.empty((cout, 27, cin), dtype=torch.float32, device="cuda")
     _ok(lib().claire_nn_conv3_wgrad(_ptr(dz), _ptr(x), _ptr(dw), _ptr(work), B, n1, n2, n3, cin, cout, _stream()),
         "claire_nn_conv3_wgrad")
+    _ok(lib().claire_nn_status(_stream()), "claire_nn_conv3_wgrad: tensor-core wait timed out")
     return dw
 
 
