@@ -7,12 +7,12 @@
 // run as implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma, BF16 operands staged in shared memory,
 // FP32 accumulators in tensor memory; tc.cuh):
 //   forward  y[m, co] = sum_{off, ci} x[nb(m, off), ci] w[co, off, ci]      (M = voxels, N = Cout, K = 27 Cin):
-//            a CTA owns 128 voxels; per neighbour offset it stages the 128 neighbour rows and the offset's
-//            Cout x Cin weight slice, and one thread issues Cin/16 MMAs into the 128 x Cout accumulator
+//            a CTA owns 128 voxels; per K step it stages the 128 neighbour rows of a group of offsets and the
+//            matching Cout x (G Cin) weight slice, and one thread issues the MMAs into the 128 x Cout accumulator
 //   dgrad    the forward kernel applied to dz with w^T[ci, 26 - off, co] = w[co, off, ci]
-//   wgrad    dw[co, off, ci] = sum_m dz[m, co] x[nb(m, off), ci]           (M = Cout padded to 128, N = Cin,
-//            K = voxels): a CTA owns one offset and one chunk of voxels; chunks are summed in a fixed order,
-//            so results do not depend on scheduling
+//   wgrad    dw[co, off, ci] = sum_m x[nb(m, off), ci] dz[m, co]           (M = G Cin rows for a group of G
+//            offsets, N = Cout, K = voxels): a CTA owns one offset group and one chunk of voxels; chunks are
+//            summed in a fixed order, so results do not depend on scheduling
 // Every wait on the tensor core is bounded (about a second); a timeout sets an error flag that
 // claire_nn_status reports, and the CTA still waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
@@ -42,18 +42,33 @@ struct Vox {
 };
 __device__ __forceinline__ Vox vox_of(const Geo& g, int m) {
   Vox v;
-  v.i3 = m % g.n3;
-  int t = m / g.n3;
-  v.i2 = t % g.n2;
-  t /= g.n2;
-  v.i1 = t % g.n1;
-  v.b = t / g.n1;
+  const unsigned t = g.by_n3.div((unsigned)m);
+  v.i3 = m - (int)t * g.n3;
+  const unsigned t2 = g.by_n2.div(t);
+  v.i2 = (int)t - (int)t2 * g.n2;
+  v.b = (int)g.by_n1.div(t2);
+  v.i1 = (int)t2 - v.b * g.n1;
   return v;
 }
-// flattened index of the periodic neighbour of v at offset off = 9 (o1 + 1) + 3 (o2 + 1) + (o3 + 1)
-__device__ __forceinline__ int nb_of(const Geo& g, const Vox& v, int off) {
-  const int o1 = off / 9 - 1, o2 = (off / 3) % 3 - 1, o3 = off % 3 - 1;
-  return ((v.b * g.n1 + pw(v.i1 + o1, g.n1)) * g.n2 + pw(v.i2 + o2, g.n2)) * g.n3 + pw(v.i3 + o3, g.n3);
+// The periodic neighbours of one voxel: per axis the three wrapped coordinates (axis 1 already scaled to its slab
+// of n2 rows), so the flattened index of the neighbour at offset off = 9 (o1 + 1) + 3 (o2 + 1) + (o3 + 1) is two
+// selects per axis and one multiply-add.
+struct Nbr {
+  int r1[3], r2[3], r3[3];
+};
+__device__ __forceinline__ Nbr nbr_of(const Geo& g, const Vox& v) {
+  Nbr n;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    n.r1[k] = (v.b * g.n1 + pw(v.i1 + k - 1, g.n1)) * g.n2;
+    n.r2[k] = pw(v.i2 + k - 1, g.n2);
+    n.r3[k] = pw(v.i3 + k - 1, g.n3);
+  }
+  return n;
+}
+__device__ __forceinline__ int sel3(const int* a, int k) { return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]); }
+__device__ __forceinline__ int nb_of(const Geo& g, const Nbr& n, int off) {
+  return (sel3(n.r1, off / 9) + sel3(n.r2, (off / 3) % 3)) * g.n3 + sel3(n.r3, off % 3);
 }
 
 // Forward convolution on tcgen05: 128 threads; thread r stages row r (voxel m0 + r). Offsets [off0, off1) of the
@@ -92,7 +107,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict_
   const int m0 = blockIdx.x * kTileM;
   const int m = m0 + tid;
   const bool valid = m < g.M;
-  const Vox me = vox_of(g, valid ? m : 0);
+  const Nbr nb = nbr_of(g, vox_of(g, valid ? m : 0));
   const int nvec = Cin / 8;
   const uint32_t kbytes = 16u * (uint32_t)KS;  // row-group stride of both tiles
   const uint32_t idesc = tc::idesc_bf16(kTileM, Cout);
@@ -117,7 +132,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict_
     unsigned char* As = sm + sidx * stage_bytes;
     unsigned char* Bs = As + a_bytes;
     for (int off = oa; off < ob; ++off) {
-      const uint4* src = reinterpret_cast<const uint4*>(x + (long long)nb_of(g, me, off) * Cin);
+      const uint4* src = reinterpret_cast<const uint4*>(x + (long long)nb_of(g, nb, off) * Cin);
       const int kb = (off - oa) * Cin;
       for (int c = 0; c < nvec; ++c) {
         const uint4 v = valid ? src[c] : make_uint4(0u, 0u, 0u, 0u);
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3_wgrad_tc(const bf16* __restric
     const int sidx = s & 1;
     const int mv = c0 + s * kTileK + k;
     const bool valid = mv < c1;
-    const Vox me = vox_of(g, valid ? mv : c0);
+    const Nbr nb = nbr_of(g, vox_of(g, valid ? mv : c0));
     // issue this step's loads before waiting for the stage
     uint4 va[8], vb[8];
 #pragma unroll
@@ -268,7 +283,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3_wgrad_tc(const bf16* __restric
       va[q] = make_uint4(0u, 0u, 0u, 0u);
       if (valid && v < nva) {
         const int j = v / cvec, cv = v - j * cvec;
-        va[q] = *reinterpret_cast<const uint4*>(x + (long long)nb_of(g, me, off_first + j) * Cin + 8 * cv);
+        va[q] = *reinterpret_cast<const uint4*>(x + (long long)nb_of(g, nb, off_first + j) * Cin + 8 * cv);
       }
     }
 #pragma unroll
@@ -538,10 +553,11 @@ inline int wgrad_group(int Cin) {
   const int G = kTileM / Cin;
   return G > 27 ? 27 : (G < 1 ? 1 : G);
 }
-// voxels per CTA of the weight gradient: about two CTAs per SM over the offset groups x chunks, whole K steps
+// voxels per CTA of the weight gradient: about five CTAs per SM (its occupancy limit) over the offset groups x
+// chunks, whole K steps
 inline int wgrad_chunk(const Geo& g, int Cin) {
   const long long ngroups = (27 + wgrad_group(Cin) - 1) / wgrad_group(Cin);
-  const long long target = (2 * 152 + ngroups - 1) / ngroups;
+  const long long target = (5 * 152 + ngroups - 1) / ngroups;
   long long per = (g.M + target - 1) / target;
   per = (per + kTileK - 1) / kTileK * kTileK;
   return (int)(per < kTileK ? kTileK : per);

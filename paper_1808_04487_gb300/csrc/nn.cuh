@@ -7,6 +7,8 @@
 
 #include <cstddef>
 
+#include "common.cuh"
+
 namespace claire {
 namespace nn {
 
@@ -16,8 +18,12 @@ typedef __nv_bfloat16 bf16;
 struct Geo {
   int B, n1, n2, n3;
   long long M;
+  FastDiv by_n3, by_n2, by_n1;  // voxel-index decoding without hardware division
 };
-inline Geo mkgeo(int B, int n1, int n2, int n3) { return Geo{B, n1, n2, n3, (long long)B * n1 * n2 * n3}; }
+inline Geo mkgeo(int B, int n1, int n2, int n3) {
+  return Geo{B, n1, n2, n3, (long long)B * n1 * n2 * n3, FastDiv((unsigned)n3), FastDiv((unsigned)n2),
+             FastDiv((unsigned)n1)};
+}
 // shape rules of the tensor-core convolution: whole 16-voxel tiles, 32-bit voxel indices
 inline bool conv_geo_ok(const Geo& g) {
   return g.B > 0 && g.n1 > 0 && g.n2 > 0 && g.n3 > 0 && g.M % 16 == 0 && g.M < (1LL << 31);
