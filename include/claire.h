@@ -256,11 +256,15 @@ claire_status claire_ifft_f64(claire_ctx* ctx, const double* spec, double* f, vo
 
 /* Kernel launches the library has made on this context (and its coarse context) since claire_create, and the
  * gather schedule of the cached linearisation: the brick halo (voxels) of the shared-memory tiled gathers along X
- * (state, incremental state) and Y (adjoints), or -1 where the plain gathers run (chosen per grid by timing both
- * once; the environment variable CLAIRE_GATHER=plain or =tiled overrides the choice). */
+ * (state, incremental state) and Y (adjoints), or -1 where the plain gathers run. Chosen per grid by timing both
+ * once, separately for the light kernels (halo_x, halo_y: incremental state steps, store/accumulate adjoint steps,
+ * state interpolation) and the heavy ones (halo_x_heavy, halo_y_heavy: last incremental step, adjoint steps with
+ * the fused inner product or the div v source); the environment variable CLAIRE_GATHER=plain or =tiled overrides
+ * the choice. */
 typedef struct {
     long long launches;
     int halo_x, halo_y;
+    int halo_x_heavy, halo_y_heavy;
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 

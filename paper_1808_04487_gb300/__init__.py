@@ -57,7 +57,8 @@ class PairF32(ctypes.Structure):
 
 
 class Counters(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong), ("halo_x", ctypes.c_int), ("halo_y", ctypes.c_int)]
+    _fields_ = [("launches", ctypes.c_longlong), ("halo_x", ctypes.c_int), ("halo_y", ctypes.c_int),
+                ("halo_x_heavy", ctypes.c_int), ("halo_y_heavy", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p
@@ -428,10 +429,12 @@ class Context:
         return int(c.launches)
 
     def gather_schedule(self):
-        """{"halo_x", "halo_y"}: brick halos of the tiled gathers of the cached linearisation (-1: plain)."""
+        """{"halo_x", "halo_y", "halo_x_heavy", "halo_y_heavy"}: brick halos of the tiled gathers of the cached
+        linearisation for the light and the heavy kernels (-1: plain)."""
         c = Counters()
         lib().claire_get_counters(self._h, ctypes.byref(c))
-        return {"halo_x": int(c.halo_x), "halo_y": int(c.halo_y)}
+        return {"halo_x": int(c.halo_x), "halo_y": int(c.halo_y), "halo_x_heavy": int(c.halo_x_heavy),
+                "halo_y_heavy": int(c.halo_y_heavy)}
 
     def resample_to(self, dst, f, project=False, out=None, kmax=0):
         """f ([ncomp,] n) on this grid -> dst's grid by Fourier truncation / zero padding (FP32 contexts)."""

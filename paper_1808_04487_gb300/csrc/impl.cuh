@@ -73,7 +73,8 @@ struct claire_ctx {
   bool lin_valid = false;
   bool gm16_on = false;        // gradient history stored in BF16 (claire_opts.bf16_mask bit 0)
   bool gm_ready = false;       // the gradient history holds finite values (used as autotuning input)
-  int haloX = -1, haloY = -1;  // brick halo of the cached departure points (-1: unknown, plain gathers)
+  int haloX = -1, haloY = -1;    // brick halo of the cached departure points (-1: plain gathers), light kernels
+  int haloXh = -1, haloYh = -1;  // the same for the heavy kernels (last incremental step, fused-product/div steps)
   long long dot_blocks = 0;    // partials written by the last dot-fused adjoint step
   double* hscal = nullptr;  // pinned host mirror of Work::scal
   // optional per-launch CUDA-event timing (off by default): one event pair per kernel launch, summed per name

@@ -171,17 +171,21 @@ __device__ __forceinline__ T gather(const T* __restrict__ f, const Stencil<T>& s
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Shared-memory bricks. A CTA of 32 x 8 threads handles a tile of 32 (i3) x 8 (i2) x 4 (i1) nodes. With every
+// Shared-memory bricks. A CTA of 16 x 16 threads handles a tile of 16 (i3) x 16 (i2) x 4 (i1) nodes. With every
 // displacement bounded by D voxels (measured after the departure points are computed), all stencils of the tile
 // lie in the brick of nodes [tile - H, tile + H] per axis, H = ceil(D) + 1 below and one more above. The brick is
-// loaded once with coalesced periodic-wrapped reads; each of the 64 taps then is one conflict-free shared-memory
-// wavefront per warp instead of two L1 lines. A stencil outside the brick (never, when D is exact) falls back to
-// the global gather.
-constexpr int kTX = 32, kTY = 8, kTZ = 4;
+// loaded once with coalesced periodic-wrapped reads; each of the 64 taps then is a shared-memory read instead of
+// L1 lines. A warp holds 16 (i3) x 2 (i2) nodes, and the brick's row pitch px is 16 modulo 32 words (as is its
+// plane pitch), so the two half-warps -- and lanes whose stencils sit one row or plane apart -- read disjoint
+// bank ranges: with 32 nodes along one row, stencil spans over 32 words made two-way bank conflicts (measured:
+// 56% extra wavefronts). A stencil outside the brick (never, when D is exact) falls back to the global gather.
+constexpr int kTX = 16, kTY = 16, kTZ = 4;
 
 template <int H> struct TileGeom {
   static constexpr int ex = kTX + 2 * H + 1, ey = kTY + 2 * H + 1, ez = kTZ + 2 * H + 1;
-  static constexpr int vol = ex * ey * ez;
+  static constexpr int px = ex + (16 - ex % 32 + 32) % 32;  // row pitch: >= ex, 16 mod 32
+  static constexpr int vol = px * ey * ez;
+  static_assert(px % 32 == 16 && (px * ey) % 32 == 16, "row and plane pitch 16 mod 32 words");
 };
 
 struct Tile {
@@ -229,8 +233,8 @@ __device__ __forceinline__ void load_bricks(T* sm, const T* __restrict__ f0, con
       const int goff = z * d.n2 * d.n3 + y * d.n3;
 #pragma unroll
       for (int x = threadIdx.x; x < G::ex; x += kTX) {
-        cp_async_elem<T>(sm + row * G::ex + x, g0 + goff + x);
-        if (f1) cp_async_elem<T>(sm + G::vol + row * G::ex + x, g1 + goff + x);
+        cp_async_elem<T>(sm + row * G::px + x, g0 + goff + x);
+        if (f1) cp_async_elem<T>(sm + G::vol + row * G::px + x, g1 + goff + x);
       }
     }
   } else {
@@ -240,8 +244,8 @@ __device__ __forceinline__ void load_bricks(T* sm, const T* __restrict__ f0, con
       const int base = (gz * d.n2 + gy) * d.n3;
       for (int x = threadIdx.x; x < G::ex; x += kTX) {
         const int gx = wrapc(tl.x0 - H + x, d.n3);
-        cp_async_elem<T>(sm + row * G::ex + x, f0 + base + gx);
-        if (f1) cp_async_elem<T>(sm + G::vol + row * G::ex + x, f1 + base + gx);
+        cp_async_elem<T>(sm + row * G::px + x, f0 + base + gx);
+        if (f1) cp_async_elem<T>(sm + G::vol + row * G::px + x, f1 + base + gx);
       }
     }
   }
@@ -262,14 +266,14 @@ __device__ __forceinline__ bool in_brick(const Stencil<T>& s, const Tile& tl, in
 template <class T, int H>
 __device__ __forceinline__ T gather_brick(const T* sb, int lz, int ly, int lx, const Stencil<T>& s) {
   using G = TileGeom<H>;
-  const T* corner = sb + (lz * G::ey + ly) * G::ex + lx;
+  const T* corner = sb + (lz * G::ey + ly) * G::px + lx;
   T acc = T(0);
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     T a1 = T(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const T* row = corner + (p * G::ey * G::ex + q * G::ex);
+      const T* row = corner + (p * G::ey * G::px + q * G::px);
       T a2 = s.w3[0] * row[0];
       a2 = fma(s.w3[1], row[1], a2);
       a2 = fma(s.w3[2], row[2], a2);
@@ -351,11 +355,16 @@ template <int H> __device__ __forceinline__ Tile tile_or_empty(const Dims& d) {
   }
 }
 
-// Launch bounds of the gather kernels: 8 resident CTAs (32 registers) for the FP32 one-field gathers -- measured
-// 4-10% faster at 256^3 than the compiler's own 40-48 registers, since their long-scoreboard stalls want more warps;
-// 4 CTAs (64 registers) for FP64 and for the variants with more live state (RHO, last step), which spill at 32.
+// Launch bounds of the gather kernels: 8 resident CTAs (32 registers) for the FP32 one-field global gathers --
+// measured 4-10% faster at 256^3 than the compiler's own 40-48 registers, since their long-scoreboard stalls want
+// more warps; 4 CTAs (64 registers) for FP64 and for the variants with more live state (RHO, last step), which
+// spill at 32. The brick-tiled gathers are bound by the L1 data pipe, not by latency: 5 CTAs (48 registers), since
+// spills cost L1 wavefronts (measured at 32 registers: 15% of them; 40 registers still spill).
+template <class T, int H, bool HEAVY> constexpr int gather_min_ctas() {
+  return sizeof(T) != 4 || HEAVY ? 4 : (H >= 0 ? 5 : 8);
+}
 template <class T, int H>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4)
+__global__ void __launch_bounds__(256, gather_min_ctas<T, H, false>())
     k_interp(const T* __restrict__ f, const T* __restrict__ disp, T* __restrict__ out, Dims d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(256) k_adj_terminal(const T* __restrict__ mR, 
 //   a = lam^{j+1}(Y); with the div source: c = (rho lam^{j+1})(Y), lam^j = a + dt/2 (c + rho(x)(a + dt c)).
 // Epilogue: optional store of lam^j and rho lam^j, and b += w_j lam^j grad m^j.
 template <class T, bool RHO, bool STORE, bool ACC, bool DOT, int H, class G>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RHO) ? 8 : 4)
+__global__ void __launch_bounds__(256, gather_min_ctas<T, H, RHO>())
     k_adj_step(const T* __restrict__ lam_next, const T* __restrict__ rl_next,
                                                   const T* __restrict__ rho, const T* __restrict__ dY,
                                                   T* __restrict__ lam, T* __restrict__ rl, T* __restrict__ b,
@@ -465,7 +474,7 @@ __global__ void __launch_bounds__(256) k_inc_init(const T* __restrict__ vt, cons
 // m~^{j+1}(x) = q^j(X) + dt/2 f^{j+1}(x); not last: q^{j+1} = m~^{j+1} + dt/2 f^{j+1}.
 // last: lam~ = -m~(1) (Eq. (9) final condition), rl = rho lam~, b = w lam~ grad m^{nt}.
 template <class T, bool LAST, bool RHO, int H, class G>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && !LAST) ? 8 : 4)
+__global__ void __launch_bounds__(256, gather_min_ctas<T, H, LAST>())
     k_inc_step(const T* __restrict__ q, const T* __restrict__ dX,
                                                   const T* __restrict__ vt, const G* __restrict__ gm,
                                                   T* __restrict__ qout, const T* __restrict__ rho,

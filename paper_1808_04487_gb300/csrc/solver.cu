@@ -181,66 +181,81 @@ template <class T> inline const void* gm_at(claire_ctx* c, int j) {
   return W.gm + off;
 }
 
-// Autotuner of the gather schedule: for a grid and brick halo, time the brick-tiled and the plain incremental
-// state step once (on scratch buffers) and keep the faster; the choice is cached for the process.
+// Autotuner of the gather schedule: for a grid and brick halo, time the brick-tiled and the plain gathers once (on
+// scratch buffers) for two classes of kernels and keep the faster of each; the choice is cached for the process.
+// Light: the one-field steps compiled for 8 resident CTAs (incremental state step, store/accumulate adjoint step,
+// state interpolation), timed on the incremental state step. Heavy: the steps with more live state and 4 CTAs
+// (last incremental step, adjoint step with the fused <s, b~> or the div v source), timed on the adjoint step
+// with the fused product -- the shared-memory taps gain most where few warps are resident.
+struct Schedule {
+  bool light = true, heavy = true;  // tiled
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, bool> g_tune;
+std::map<std::tuple<int, int, int, int, int>, Schedule> g_tune;
 
-template <class T> claire_status tune_tiling(claire_ctx* c, int H, bool* tiled, cudaStream_t st) {
-  if (const char* force = std::getenv("CLAIRE_GATHER")) {
-    if (std::strcmp(force, "plain") == 0 || std::strcmp(force, "tiled") == 0) {
-      *tiled = force[0] == 't';
-      return CLAIRE_OK;
-    }
-  }
+template <class T> claire_status tune_tiling(claire_ctx* c, int H, Schedule* out, cudaStream_t st) {
   const auto key = std::make_tuple(c->d.n1, c->d.n2, c->d.n3, H, c->gm16_on ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      *tiled = it->second;
+      *out = it->second;
       return CLAIRE_OK;
     }
   }
   Work<T>& W = c->work<T>();
-  cudaEvent_t e[3];
+  cudaEvent_t e[2];
   for (auto& x : e) CL_CUDA(c, cudaEventCreate(&x));
-  float ms[2] = {0.f, 0.f};
-  for (int variant = 0; variant < 2; ++variant) {
-    const int h = variant == 0 ? H : -1;
-    CL_TRY(sl_incstate_step<T>(c, W.la, W.dX, W.s, gm_at<T>(c, 0), c->gm16_on, W.lb, false, nullptr, nullptr,
-                               nullptr, T(0), st, h));  // warm-up
-    CL_CUDA(c, cudaEventRecord(e[0], st));
-    for (int r = 0; r < 3; ++r)
-      CL_TRY(sl_incstate_step<T>(c, W.la, W.dX, W.s, gm_at<T>(c, 0), c->gm16_on, W.lb, false, nullptr, nullptr,
-                                 nullptr, T(0), st, h));
-    CL_CUDA(c, cudaEventRecord(e[1], st));
-    CL_CUDA(c, cudaEventSynchronize(e[1]));
-    CL_CUDA(c, cudaEventElapsedTime(&ms[variant], e[0], e[1]));
+  float ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [class][tiled, plain]
+  for (int cls = 0; cls < 2; ++cls) {
+    for (int variant = 0; variant < 2; ++variant) {
+      const int h = variant == 0 ? H : -1;
+      auto run = [&]() -> claire_status {
+        if (cls == 0)
+          return sl_incstate_step<T>(c, W.la, W.dX, W.s, gm_at<T>(c, 0), c->gm16_on, W.lb, false, nullptr, nullptr,
+                                     nullptr, T(0), st, h);
+        return sl_adjoint_step<T>(c, W.la, nullptr, nullptr, W.dX, nullptr, nullptr, W.b, gm_at<T>(c, 0), c->gm16_on,
+                                  T(0), st, W.s, W.bigpart, h);
+      };
+      CL_TRY(run());  // warm-up
+      CL_CUDA(c, cudaEventRecord(e[0], st));
+      for (int r = 0; r < 3; ++r) CL_TRY(run());
+      CL_CUDA(c, cudaEventRecord(e[1], st));
+      CL_CUDA(c, cudaEventSynchronize(e[1]));
+      CL_CUDA(c, cudaEventElapsedTime(&ms[cls][variant], e[0], e[1]));
+    }
   }
   for (auto& x : e) cudaEventDestroy(x);
-  *tiled = ms[0] <= ms[1];
+  out->light = ms[0][0] <= ms[0][1];
+  out->heavy = ms[1][0] <= ms[1][1];
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[key] = *tiled;
+  g_tune[key] = *out;
   return CLAIRE_OK;
 }
 
-// Brick halo for the tiled gathers: max |displacement| D in voxels over the field -> H = ceil(D) + 1 (or -1 when
-// the autotuner found the plain gathers faster on this grid)
-template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* halo, cudaStream_t st) {
+// Brick halo for the tiled gathers: max |displacement| D in voxels over the field -> H = ceil(D) + 1, per kernel
+// class (light, heavy), or -1 where the plain gathers run (the autotuner's choice on this grid, or
+// CLAIRE_GATHER=plain; CLAIRE_GATHER=tiled forces the bricks wherever a halo exists)
+template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* halo, int* halo_heavy,
+                                             cudaStream_t st) {
   Work<T>& W = c->work<T>();
   CL_TRY(absmax_partial<T>(c, disp, 3 * c->d.N, W.partials, st));
   CL_TRY(max_final(c, W.partials, kReduceBlocks, W.scal + 12, st));
   double D;
   CL_TRY(read_scalar(c, W.scal + 12, &D, st));
-  *halo = (std::isfinite(D) && D < 64.0) ? (int)std::ceil(D + 1e-3) + 1 : -1;
+  const int H = (std::isfinite(D) && D < 64.0) ? (int)std::ceil(D + 1e-3) + 1 : -1;
+  *halo = *halo_heavy = H;
+  if (H < 0) return CLAIRE_OK;
   const char* force = std::getenv("CLAIRE_GATHER");
-  if (*halo >= 0 && force && std::strcmp(force, "plain") == 0) {
-    *halo = -1;
-  } else if (*halo >= 0 && sizeof(T) == 4 && c->gm_ready) {
-    bool tiled = true;
-    CL_TRY(tune_tiling<T>(c, *halo < 2 ? 2 : *halo, &tiled, st));
-    if (!tiled) *halo = -1;
+  if (force && std::strcmp(force, "plain") == 0) {
+    *halo = *halo_heavy = -1;
+  } else if (force && std::strcmp(force, "tiled") == 0) {
+    // bricks wherever a halo exists
+  } else if (sizeof(T) == 4 && c->gm_ready) {
+    Schedule sch;
+    CL_TRY(tune_tiling<T>(c, H < 2 ? 2 : H, &sch, st));
+    if (!sch.light) *halo = -1;
+    if (!sch.heavy) *halo_heavy = -1;
   }
   return CLAIRE_OK;
 }
@@ -260,7 +275,7 @@ template <class T> claire_status finish_linearization(claire_ctx* c, const T* v,
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
   CL_TRY(sl_departure<T>(c, v, -1, W.dY, st));
-  CL_TRY(update_halo<T>(c, W.dY, &c->haloY, st));
+  CL_TRY(update_halo<T>(c, W.dY, &c->haloY, &c->haloYh, st));
   for (int j = 0; j <= c->o.nt; ++j) {
     if (c->gm16_on) {
       // FP32 gradient into the b scratch, then stored in BF16
@@ -281,7 +296,7 @@ template <class T> claire_status linearize(claire_ctx* c, const T* mT, const T* 
   Work<T>& W = c->work<T>();
   c->lin_valid = false;
   CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
-  CL_TRY(update_halo<T>(c, W.dX, &c->haloX, st));
+  CL_TRY(update_halo<T>(c, W.dX, &c->haloX, &c->haloXh, st));
   CL_TRY(state_history<T>(c, mT, st));
   return finish_linearization<T>(c, v, st);
 }
@@ -305,7 +320,7 @@ template <class T> claire_status adjoint_integral(claire_ctx* c, const T* mR, cu
     CL_TRY(sl_adjoint_step<T>(c, lam[cur], rho ? rl[cur] : nullptr, rho, W.dY, store ? lam[1 - cur] : nullptr,
                               (store && rho) ? rl[1 - cur] : nullptr, W.b, gm_at<T>(c, j), c->gm16_on,
                               T(tweight(j, nt)), st,
-                              nullptr, nullptr, c->haloY));
+                              nullptr, nullptr, rho ? c->haloYh : c->haloY));
     cur = 1 - cur;
   }
   return CLAIRE_OK;
@@ -360,7 +375,7 @@ template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStrea
   for (int j = 0; j < nt; ++j) {
     const bool last = j == nt - 1;
     CL_TRY(sl_incstate_step<T>(c, buf[cur], W.dX, vt, gm_at<T>(c, j + 1), c->gm16_on, buf[1 - cur], last, rho,
-                               rl[1 - cur], W.b, T(tweight(nt, nt)), st, c->haloX));
+                               rl[1 - cur], W.b, T(tweight(nt, nt)), st, last ? c->haloXh : c->haloX));
     cur = 1 - cur;
   }
   for (int j = nt - 1; j >= 0; --j) {
@@ -369,7 +384,7 @@ template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStrea
                               (store && rho) ? rl[1 - cur] : nullptr, W.b, gm_at<T>(c, j), c->gm16_on,
                               T(tweight(j, nt)),
                               st, (dot && j == 0) ? vt : nullptr, (dot && j == 0) ? W.bigpart : nullptr,
-                              c->haloY));
+                              ((dot && j == 0) || rho) ? c->haloYh : c->haloY));
     cur = 1 - cur;
   }
   return CLAIRE_OK;
@@ -389,7 +404,7 @@ template <class T> claire_status state_mismatch(claire_ctx* c, const T* mT, cons
   const long long N = c->d.N;
   c->lin_valid = false;
   CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
-  CL_TRY(update_halo<T>(c, W.dX, &c->haloX, st));
+  CL_TRY(update_halo<T>(c, W.dX, &c->haloX, &c->haloXh, st));
   CL_TRY(state_history<T>(c, mT, st));
   CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
   return reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal + slot, st);
@@ -666,7 +681,7 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
       if (!accepted) {
         status = CLAIRE_ELINESEARCH;
         CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
-        CL_TRY(update_halo<T>(c, W.dX, &c->haloX, st));
+        CL_TRY(update_halo<T>(c, W.dX, &c->haloX, &c->haloXh, st));
         CL_TRY(state_history<T>(c, mT, st));
         break;
       }
@@ -708,7 +723,7 @@ template <class T> claire_status transport_dev(claire_ctx* c, const T* m0, const
   const long long N = c->d.N;
   const int nt = c->o.nt;
   c->lin_valid = false;
-  c->haloX = c->haloY = -1;
+  c->haloX = c->haloY = c->haloXh = c->haloYh = -1;
   T* buf[2] = {W.la, W.lb};
   if (dir > 0) {
     CL_TRY(sl_departure<T>(c, v, +1, W.dX, st));
@@ -1154,6 +1169,8 @@ claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   out->launches = c->counters.launches + (c->coarse ? c->coarse->counters.launches : 0);
   out->halo_x = c->haloX;
   out->halo_y = c->haloY;
+  out->halo_x_heavy = c->haloXh;
+  out->halo_y_heavy = c->haloYh;
   return CLAIRE_OK;
 }
 

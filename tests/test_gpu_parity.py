@@ -203,6 +203,39 @@ def test_objective_gradient_hessvec(n, prec, case):
         assert abs(c.objective(dev(lin.m[-1], prec), dev(mR, prec), dev(v, prec)) - J_ref) <= TOL[prec] * J_ref
 
 
+@pytest.mark.parametrize("schedule", ["plain", "tiled"])
+def test_gather_schedules_match_the_oracle(schedule, monkeypatch):
+    """Both FP32 gather schedules -- taps read from global memory, and taps read from shared-memory bricks of
+    16 x 16 x 4-node tiles -- on a 40 x 36 x 42 grid, whose i2 and i3 extents end in partial tiles, with
+    displacements that need a brick halo of 2 or more; the schedule is forced with CLAIRE_GATHER and read back
+    from the context."""
+    monkeypatch.setenv("CLAIRE_GATHER", schedule)
+    n = (40, 36, 42)
+    case = dict(regnorm=2, divfree=True, nt=4)
+    p = O.Problem(n, beta=1e-2, **case)
+    mT = rounded(I.trig_image(n, 20), "f32")
+    mR = rounded(I.trig_image(n, 21), "f32")
+    v = rounded(I.random_velocity(n, seed=22, kmax=4, max_disp_voxels=6.0, divfree=True), "f32")
+    vt = rounded(I.random_velocity(n, seed=23, kmax=4, amplitude=1.0, divfree=True), "f32")
+    lin = O.linearize(p, mT, v)
+    g_ref = O.reduced_gradient(p, lin, mR)
+    h_ref = O.hessvec(p, lin, vt)
+    bnd = lambda x: reg_noise_bound("f32", n, p.beta, 2, x)
+    err = lambda a, b: float(np.linalg.norm(a.cpu().double().numpy() - b))
+    with ctx(n, "f32", beta=1e-2, **case) as c:
+        g = c.gradient(dev(mT, "f32"), dev(mR, "f32"), dev(v, "f32"))
+        sched = c.gather_schedule()
+        if schedule == "tiled":
+            assert min(sched.values()) >= 2
+        else:
+            assert set(sched.values()) == {-1}
+        assert err(g, g_ref) <= TOL["f32"] * np.linalg.norm(g_ref) + bnd(v)
+        h = c.hessvec_cached(dev(vt, "f32"))
+        assert err(h, h_ref) <= TOL["f32"] * np.linalg.norm(h_ref) + bnd(vt)
+        m1 = c.transport(dev(mT, "f32"), dev(v, "f32"), +1)
+        assert rel(m1, lin.m[-1]) < TOL["f32"]
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_inner_product_fp64_accumulation(prec):
     n = (40, 36, 42)
