@@ -179,6 +179,38 @@ __global__ void __launch_bounds__(LPC * cmax<R1, R2>()) k_fft2_z_r2c(const T* __
     }
     rdft<T, -1, R2, L>(u, W);
   }
+  if constexpr (R1 == TT && 32 % TT == 0) {
+    // Thread t holds Z[k], k = t + q R1; the mirrored Z[L - k] is Z[(R1 - t) + (R2 - 1 - q) R1] of thread R1 - t
+    // (for t = 0: its own Z[(R2 - q) R1], and Z[0] for k = 0 and k = L), fetched by warp shuffle -- a line's R1
+    // threads are consecutive lanes of one warp -- instead of a shared-memory round trip.
+    const int lane = tid & 31;
+    const int partner = (lane - t) + (R1 - t) % R1;
+    cplx<T> zm[R2];
+#pragma unroll
+    for (int q = 0; q < R2; ++q) {
+      const cplx<T> sent = u[R2 - 1 - q];
+      const cplx<T> got = mk<T>(__shfl_sync(0xffffffffu, sent.x, partner), __shfl_sync(0xffffffffu, sent.y, partner));
+      zm[q] = t == 0 ? u[(R2 - q) % R2] : got;
+    }
+    if (ok) {
+      cplx<T>* dst = out + line * (L + 1);
+#pragma unroll
+      for (int q = 0; q < R2; ++q) {
+        const int k = t + q * R1;
+        const cplx<T> zk = u[q], zc = cconj<T>(zm[q]);
+        const cplx<T> sum = cadd<T>(zk, zc), dif = csub<T>(zk, zc);
+        const cplx<T> wd = cmul<T>(W2[k], dif);
+        dst[k] = mk<T>(T(0.5) * (sum.x + wd.y), T(0.5) * (sum.y - wd.x));
+      }
+      if (t == 0) {
+        const cplx<T> zk = u[0], zc = cconj<T>(u[0]);
+        const cplx<T> sum = cadd<T>(zk, zc), dif = csub<T>(zk, zc);
+        const cplx<T> wd = cmul<T>(W2[L], dif);
+        dst[L] = mk<T>(T(0.5) * (sum.x + wd.y), T(0.5) * (sum.y - wd.x));
+      }
+    }
+    return;
+  }
   __syncthreads();
   if (t < R1) {
 #pragma unroll
@@ -199,7 +231,7 @@ __global__ void __launch_bounds__(LPC * cmax<R1, R2>()) k_fft2_z_r2c(const T* __
 
 // Contiguous axis, inverse: half spectra of L + 1 -> real lines of 2L, times scale.
 template <class T, int R1, int R2, int LPC>
-__global__ void __launch_bounds__(LPC * cmax<R1, R2>()) k_fft2_z_c2r(const cplx<T>* __restrict__ in,
+__global__ void __launch_bounds__(LPC * cmax<R1, R2>(), 4) k_fft2_z_c2r(const cplx<T>* __restrict__ in,
                                                                       T* __restrict__ out, long long nlines,
                                                                       const cplx<T>* __restrict__ Wn3, T scale) {
   constexpr int L = R1 * R2;
@@ -217,10 +249,34 @@ __global__ void __launch_bounds__(LPC * cmax<R1, R2>()) k_fft2_z_c2r(const cplx<
   cplx<T>* Yl = Y + l * S;
   __syncthreads();
   // Z'[k] = (X[k] + conj X[L-k]) + i exp(+2 pi i k / n3) (X[k] - conj X[L-k]) for the stage-1 inputs k = t + r R2,
-  // read straight from global memory (the mirrored read X[L-k] of one thread is another thread's X[k]: L1 hits)
+  // read straight from global memory. When a line's threads are consecutive lanes of one warp, the mirrored
+  // X[L - k] = X[(R2 - t) + (R1 - 1 - r) R2] comes from thread R2 - t by warp shuffle (for t = 0: its own
+  // X[(R1 - r) R2], and X[L] for r = 0); otherwise it is read again (another thread's X[k]: an L1 hit).
   cplx<T> v[R1];
-  if (t < R2) {
-    const cplx<T>* src = in + line * (L + 1);
+  const cplx<T>* src = in + line * (L + 1);
+  if constexpr (32 % TT == 0) {
+    cplx<T> xs[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) xs[r] = (ok && t < R2) ? src[t + r * R2] : mk<T>(T(0), T(0));
+    const cplx<T> xL = (ok && t == 0) ? src[L] : mk<T>(T(0), T(0));
+    const int lane = tid & 31;
+    const int partner = (lane - t) + (t < R2 ? (R2 - t) % R2 : t);
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const cplx<T> sent = xs[R1 - 1 - r];
+      const cplx<T> got = mk<T>(__shfl_sync(0xffffffffu, sent.x, partner), __shfl_sync(0xffffffffu, sent.y, partner));
+      const cplx<T> xk = xs[r];
+      const cplx<T> xc = cconj<T>(t == 0 ? (r == 0 ? xL : xs[R1 - r]) : got);
+      const cplx<T> sum = cadd<T>(xk, xc), dif = csub<T>(xk, xc);
+      const cplx<T> wd = cmulc<T>(dif, W2[t < R2 ? t + r * R2 : 0]);
+      v[r] = mk<T>(sum.x - wd.y, sum.y + wd.x);
+    }
+    if (t < R2) {
+      rdft<T, +1, R1, L>(v, W);
+#pragma unroll
+      for (int q = 0; q < R1; ++q) Yl[padi<R1>(t * R1 + q)] = v[q];
+    }
+  } else if (t < R2) {
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
       const int k = t + r * R2;
@@ -265,18 +321,21 @@ void launch_strided(int sign, const cplx<T>* src, cplx<T>* dst, long long inner,
     k_fft2_strided<T, +1, R1, R2, TI><<<grid, block, 0, st>>>(src, dst, inner, W);
 }
 
-template <class T, int R1, int R2>
+// (R1, R2) of the forward pass; the inverse pass may use another split (C1, C2) of the same length
+template <class T, int R1, int R2, int C1 = R1, int C2 = R2>
 void launch_z(int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3, T scale, cudaStream_t st) {
-  constexpr int TT = cmax<R1, R2>();
-  constexpr int LPC = z_lpc<T, TT>();
-  dim3 grid((unsigned)((nlines + LPC - 1) / LPC));
-  dim3 block(TT, LPC);
-  if (sign < 0)
-    k_fft2_z_r2c<T, R1, R2, LPC><<<grid, block, 0, st>>>(static_cast<const T*>(in), static_cast<cplx<T>*>(out),
-                                                         nlines, Wn3);
-  else
-    k_fft2_z_c2r<T, R1, R2, LPC><<<grid, block, 0, st>>>(static_cast<const cplx<T>*>(in), static_cast<T*>(out),
-                                                         nlines, Wn3, scale);
+  static_assert(R1 * R2 == C1 * C2, "one line length");
+  if (sign < 0) {
+    constexpr int TT = cmax<R1, R2>();
+    constexpr int LPC = z_lpc<T, TT>();
+    k_fft2_z_r2c<T, R1, R2, LPC><<<dim3((unsigned)((nlines + LPC - 1) / LPC)), dim3(TT, LPC), 0, st>>>(
+        static_cast<const T*>(in), static_cast<cplx<T>*>(out), nlines, Wn3);
+  } else {
+    constexpr int TT = cmax<C1, C2>();
+    constexpr int LPC = z_lpc<T, TT>();
+    k_fft2_z_c2r<T, C1, C2, LPC><<<dim3((unsigned)((nlines + LPC - 1) / LPC)), dim3(TT, LPC), 0, st>>>(
+        static_cast<const cplx<T>*>(in), static_cast<T*>(out), nlines, Wn3, scale);
+  }
 }
 
 }  // namespace
@@ -315,7 +374,8 @@ bool fft2_z(int L, int sign, const void* in, void* out, long long nlines, const 
     case 72: launch_z<T, 8, 9>(sign, in, out, nlines, Wn3, scale, st); return true;
     case 80: launch_z<T, 8, 10>(sign, in, out, nlines, Wn3, scale, st); return true;
     case 96: launch_z<T, 8, 12>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 128: launch_z<T, 16, 8>(sign, in, out, nlines, Wn3, scale, st); return true;
+    // inverse 8 x 16: its first stage, which also applies the Hermitian split, runs on all 16 threads of a line
+    case 128: launch_z<T, 16, 8, 8, 16>(sign, in, out, nlines, Wn3, scale, st); return true;
     default: return false;
   }
 }
