@@ -33,9 +33,10 @@ template <class T, class F> static void with_gm(const void* gm, bool g16, F&& f)
 
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-// 3D launch shape of the gather kernels: 256 threads, x along i3 (up to 64 wide), y along i2, z = i1
+// 3D launch shape of the gather kernels: 256 threads, x along i3 (32 wide: one warp per row), y along i2 (8 rows,
+// whose stencils share 3 of their 4 tap rows in L1), z = i1. Measured at 256^3 against 64 x 4: 2-3% faster.
 Launch3 launch3(const Dims& d) {
-  const int bx = d.n3 >= 64 ? 64 : (d.n3 >= 32 ? 32 : 16);
+  const int bx = d.n3 >= 32 ? 32 : 16;
   const int by = 256 / bx;
   Launch3 L;
   L.block = dim3(bx, by, 1);
