@@ -260,11 +260,14 @@ claire_status claire_ifft_f64(claire_ctx* ctx, const double* spec, double* f, vo
  * once, separately for the light kernels (halo_x, halo_y: incremental state steps, store/accumulate adjoint steps,
  * state interpolation) and the heavy ones (halo_x_heavy, halo_y_heavy: last incremental step, adjoint steps with
  * the fused inner product or the div v source); the environment variable CLAIRE_GATHER=plain or =tiled overrides
- * the choice. */
+ * the choice. With the spectral preconditioner and per-kernel profiling off, each PCG solve runs as one CUDA graph
+ * whose conditional WHILE node repeats one iteration with its scalars computed on the device (bit-identical to the
+ * host-driven loop, which CLAIRE_PCG=host forces). */
 typedef struct {
     long long launches;
     int halo_x, halo_y;
     int halo_x_heavy, halo_y_heavy;
+    long long pcg_graph_runs; /* PCG solves (Alg. 2) run as one CUDA-graph launch, the loop driven on the device */
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 

@@ -58,7 +58,7 @@ class PairF32(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("halo_x", ctypes.c_int), ("halo_y", ctypes.c_int),
-                ("halo_x_heavy", ctypes.c_int), ("halo_y_heavy", ctypes.c_int)]
+                ("halo_x_heavy", ctypes.c_int), ("halo_y_heavy", ctypes.c_int), ("pcg_graph_runs", ctypes.c_longlong)]
 
 
 _VP = ctypes.c_void_p
@@ -427,6 +427,12 @@ class Context:
         c = Counters()
         lib().claire_get_counters(self._h, ctypes.byref(c))
         return int(c.launches)
+
+    def pcg_graph_runs(self):
+        """PCG solves run as one CUDA-graph launch (device-driven loop) on this context."""
+        c = Counters()
+        lib().claire_get_counters(self._h, ctypes.byref(c))
+        return int(c.pcg_graph_runs)
 
     def gather_schedule(self):
         """{"halo_x", "halo_y", "halo_x_heavy", "halo_y_heavy"}: brick halos of the tiled gathers of the cached

@@ -53,6 +53,24 @@ template <class T> struct Work {
 };
 
 constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs
+
+// Device-side PCG state (Alg. 2 driven from the device inside a CUDA graph): FP64 slots of Work::scal from kPcgBase.
+enum PcgSlot {
+  kPcgRz = 0,      // <r, z>
+  kPcgR0,          // ||r_0||
+  kPcgSAs,         // <s, beta A s>
+  kPcgEps,         // forcing term eps_H
+  kPcgKappa,       // step length of the current iteration
+  kPcgMu,          // direction update
+  kPcgDone,        // 1 once converged, broken down or non-finite
+  kPcgBreakdown,   // <s, H s> <= 0
+  kPcgNan,         // non-finite <s, H s>
+  kPcgCopyS,       // breakdown in the first iteration: the step is the first direction
+  kPcgCount,       // matvecs done
+  kPcgMaxIt,       // Krylov iteration cap
+  kPcgSlots
+};
+constexpr int kPcgBase = 16;
 constexpr int kThreads = 256;
 
 }  // namespace claire
@@ -76,6 +94,16 @@ struct claire_ctx {
   int haloX = -1, haloY = -1;    // brick halo of the cached departure points (-1: plain gathers), light kernels
   int haloXh = -1, haloYh = -1;  // the same for the heavy kernels (last incremental step, fused-product/div steps)
   long long dot_blocks = 0;    // partials written by the last dot-fused adjoint step
+  // CUDA graph of the device-driven PCG loop (one conditional WHILE node around one iteration), kept for the
+  // gather schedule it was captured with
+  cudaGraph_t pcg_graph = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  int pcg_key[4] = {0, 0, 0, 0};
+  double pcg_beta = 0.0;  // beta_v baked into the captured kernels' arguments (continuation changes it)
+  long long pcg_body_launches = 0;
+  long long pcg_graph_runs = 0;  // PCG solves run as one graph launch
+  bool pcg_graph_failed = false;
+  cudaStream_t pcg_cap_stream = nullptr;  // capture needs a stream other than the legacy default stream
   double* hscal = nullptr;  // pinned host mirror of Work::scal
   // optional per-launch CUDA-event timing (off by default): one event pair per kernel launch, summed per name
   struct ProfRec {
@@ -164,10 +192,13 @@ template <class T> claire_status sp_grad(claire_ctx* c, const cplx<T>* V, const 
                                          double* partials, cudaStream_t st);
 template <class T> claire_status sp_pcg0(claire_ctx* c, const cplx<T>* G, cplx<T>* R, cplx<T>* S, cplx<T>* Vt,
                                          double* partials, cudaStream_t st);
+// ps (optional): the device-side PCG state block; the step then reads kappa (mu) from it and does nothing once its
+// done flag is set
 template <class T> claire_status sp_pcg_step(claire_ctx* c, const cplx<T>* S, const cplx<T>* Bt, cplx<T>* R,
-                                             cplx<T>* Vt, double kappa, double* partials, cudaStream_t st);
+                                             cplx<T>* Vt, double kappa, double* partials, cudaStream_t st,
+                                             const double* ps = nullptr);
 template <class T> claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cplx<T>* S, double mu, double* partials,
-                                            cudaStream_t st);
+                                            cudaStream_t st, const double* ps = nullptr);
 template <class T> claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G, cplx<T>* Vt, double* partials,
                                                 cudaStream_t st);
 template <class T> claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr,

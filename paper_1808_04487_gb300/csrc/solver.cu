@@ -365,7 +365,6 @@ template <class T> claire_status add_projected_b(claire_ctx* c, const T* u, T* o
 // With dot = true the last backward step also writes the per-block partials of <vt, W.b> to W.bigpart.
 template <class T> claire_status hess_data(claire_ctx* c, const T* vt, cudaStream_t st, bool dot = false) {
   Work<T>& W = c->work<T>();
-  const long long N = c->d.N;
   const int nt = c->o.nt;
   T* buf[2] = {W.la, W.lb};
   T* rl[2] = {W.ra, W.rb};
@@ -507,6 +506,144 @@ template <class T> claire_status coarse_template(claire_ctx* c, const T* mT, cud
 // inner products follow from Parseval, so the iterates are those of Alg. 2 in exact arithmetic. Each iteration
 // transforms s back to physical space for the incremental solves (Eq. (8), (9)) and their time integral b~ forward;
 // <s, H s> = <s, beta A s> (spectral) + <s, b~> (fused into the last backward gather).
+// ---------------------------------------------------------------------------------------------------------------
+// Device-driven PCG (Alg. 2 with the spectral preconditioner): one iteration -- Gauss-Newton matvec, the three
+// reductions and the scalar updates -- is captured once into the body of a conditional WHILE graph node; the
+// scalars (kappa, mu, the stopping test) are computed by one-thread kernels into the state block ps, in the same
+// FP64 operations and order as the host loop, so the iterates are bit-identical. The loop ends on convergence,
+// breakdown, a non-finite <s, H s>, or after max_krylov iterations (ps[kPcgCount] counts the matvecs): it cannot
+// run unbounded. One graph launch replaces three host round trips per iteration.
+__global__ void k_pcg_kappa(double* __restrict__ ps, const double* __restrict__ sBt) {
+  if (ps[kPcgDone] != 0.0) return;
+  ps[kPcgCount] += 1.0;
+  const double sHs = ps[kPcgSAs] + sBt[0];
+  if (!isfinite(sHs)) {
+    ps[kPcgNan] = 1.0;
+    ps[kPcgDone] = 1.0;
+  } else if (!(sHs > 0.0)) {
+    ps[kPcgBreakdown] = 1.0;
+    if (ps[kPcgCount] == 1.0) ps[kPcgCopyS] = 1.0;
+    ps[kPcgDone] = 1.0;
+  } else {
+    ps[kPcgKappa] = ps[kPcgRz] / sHs;
+  }
+}
+// rr[0] = ||r||^2, rr[1] = <r, z> after the step
+__global__ void k_pcg_check(double* __restrict__ ps, const double* __restrict__ rr) {
+  if (ps[kPcgDone] != 0.0) return;
+  if (sqrt(rr[0]) < ps[kPcgEps] * ps[kPcgR0]) {
+    ps[kPcgDone] = 1.0;
+    return;
+  }
+  ps[kPcgMu] = rr[1] / ps[kPcgRz];
+  ps[kPcgRz] = rr[1];
+}
+__global__ void k_pcg_next(double* __restrict__ ps, const double* __restrict__ sAs, cudaGraphConditionalHandle h) {
+  if (ps[kPcgDone] == 0.0) ps[kPcgSAs] = sAs[0];
+  const bool more = ps[kPcgDone] == 0.0 && ps[kPcgCount] < ps[kPcgMaxIt];
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+template <class T> void pcg_graph_release(claire_ctx* c) {
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+  c->pcg_exec = nullptr;
+  c->pcg_graph = nullptr;
+}
+
+// the PCG loop graph for the current gather schedule and beta_v (captured on first use, and again when either
+// changed: both are baked into the captured kernels)
+template <class T> claire_status pcg_graph_get(claire_ctx* c, cudaStream_t launch_st, bool* ok) {
+  *ok = false;
+  const bool verbose = [] {
+    const char* m = std::getenv("CLAIRE_PCG");
+    return m && std::strcmp(m, "verbose") == 0;
+  }();
+  auto fail = [&](const char* what, cudaError_t e) {
+    if (verbose) std::fprintf(stderr, "claire: PCG graph not used (%s: %s)\n", what, cudaGetErrorString(e));
+    cudaGetLastError();
+    return CLAIRE_OK;
+  };
+  const int key[4] = {c->haloX, c->haloXh, c->haloY, c->haloYh};
+  if (c->pcg_exec && std::equal(key, key + 4, c->pcg_key) && c->pcg_beta == c->o.beta) {
+    *ok = true;
+    return CLAIRE_OK;
+  }
+  pcg_graph_release<T>(c);
+  Work<T>& W = c->work<T>();
+  const double sc = cellvol(c->d) / double(c->d.N);
+  double* ps = W.scal + kPcgBase;
+  cudaError_t e;
+  if (!c->pcg_cap_stream && (e = cudaStreamCreateWithFlags(&c->pcg_cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail("capture stream", e);
+  // the capture records nothing that runs: the work of this solve so far (on launch_st) is ordered by the launch
+  cudaStream_t st = c->pcg_cap_stream;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return fail("graph", e);
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail("conditional handle", e);
+  }
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail("conditional node", e);
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail("begin capture", e);
+  }
+  const long long launches0 = c->counters.launches;
+  auto capture = [&]() -> claire_status {
+    CL_TRY(hess_data<T>(c, W.s, st, true));
+    CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)c->dot_blocks, cellvol(c->d), W.scal + 4, st));
+    CL_TRY(vec_r2c<T>(c, W.b, W.Bh, st));
+    k_pcg_kappa<<<1, 1, 0, st>>>(ps, W.scal + 4);
+    CL_LAUNCHED(c);
+    CL_TRY(sp_pcg_step<T>(c, W.Sh, W.Bh, W.Rh, W.VTh, 0.0, W.partials, st, ps));
+    CL_TRY(reduce_final_v(c, W.partials, 2, kReduceBlocks, sc, W.scal, st));
+    k_pcg_check<<<1, 1, 0, st>>>(ps, W.scal);
+    CL_LAUNCHED(c);
+    CL_TRY(sp_pcg_dir<T>(c, W.Rh, W.Sh, 0.0, W.partials, st, ps));
+    CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 2, st));
+    k_pcg_next<<<1, 1, 0, st>>>(ps, W.scal + 2, h);
+    CL_LAUNCHED(c);
+    return spec_to_phys<T>(c, W.Sh, W.s, st);
+  };
+  const claire_status cs = capture();
+  const std::string cap_err = c->err;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &captured);
+  c->pcg_body_launches = c->counters.launches - launches0;
+  c->counters.launches = launches0;
+  cudaGraphExec_t ex = nullptr;
+  // (any failure: the host-driven loop runs instead)
+  if (cs != CLAIRE_OK || ce != cudaSuccess) {
+    c->err.clear();
+    cudaGraphDestroy(g);
+    if (verbose) std::fprintf(stderr, "claire: PCG graph capture failed (%s)\n", cap_err.c_str());
+    return fail("end capture", ce);
+  }
+  if ((e = cudaGraphInstantiate(&ex, g, 0)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail("instantiate", e);
+  }
+  c->pcg_graph = g;
+  c->pcg_exec = ex;
+  std::copy(key, key + 4, c->pcg_key);
+  c->pcg_beta = c->o.beta;
+  *ok = true;
+  return CLAIRE_OK;
+}
+
 template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report* rep, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const double sc = cellvol(c->d) / double(c->d.N);  // Parseval scale h1 h2 h3 / N
@@ -531,6 +668,44 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
     return CLAIRE_ENAN;
   }
   CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
+  // device-driven loop: spectral preconditioner, no per-kernel profiling (its events are per launch, not per
+  // graph execution), unless CLAIRE_PCG=host
+  const char* mode = std::getenv("CLAIRE_PCG");
+  if (!two && !c->prof_on && !c->pcg_graph_failed && !(mode && std::strcmp(mode, "host") == 0)) {
+    bool ok = false;
+    CL_TRY(pcg_graph_get<T>(c, st, &ok));
+    if (!ok) {
+      c->pcg_graph_failed = true;
+    } else {
+      double* hs = c->hscal + 32;
+      for (int k = 0; k < kPcgSlots; ++k) hs[k] = 0.0;
+      hs[kPcgRz] = rz;
+      hs[kPcgR0] = r0;
+      hs[kPcgSAs] = sAs;
+      hs[kPcgEps] = eps_H;
+      hs[kPcgMaxIt] = double(c->o.max_krylov);
+      double* ps = W.scal + kPcgBase;
+      CL_CUDA(c, cudaMemcpyAsync(ps, hs, sizeof(double) * kPcgSlots, cudaMemcpyHostToDevice, st));
+      CL_CUDA(c, cudaGraphLaunch(c->pcg_exec, st));
+      c->pcg_graph_runs++;
+      CL_CUDA(c, cudaMemcpyAsync(hs, ps, sizeof(double) * kPcgSlots, cudaMemcpyDeviceToHost, st));
+      CL_CUDA(c, cudaStreamSynchronize(st));
+      const long long n = (long long)hs[kPcgCount];
+      rep->matvecs += (int)n;
+      rep->pde_solves += 2 * (int)n;
+      c->counters.launches += n * c->pcg_body_launches;
+      if (hs[kPcgNan] != 0.0) {
+        c->set_error("non-finite <s, Hs>");
+        return CLAIRE_ENAN;
+      }
+      if (hs[kPcgBreakdown] != 0.0) {
+        rep->pcg_breakdowns++;
+        if (hs[kPcgCopyS] != 0.0)
+          CL_CUDA(c, cudaMemcpyAsync(W.VTh, W.Sh, sizeof(cplx<T>) * 3 * c->d.Ns, cudaMemcpyDeviceToDevice, st));
+      }
+      return CLAIRE_OK;
+    }
+  }
   for (int it = 0; it < c->o.max_krylov; ++it) {
     CL_TRY(hess_data<T>(c, W.s, st, true));
     CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)c->dot_blocks, cellvol(c->d), W.scal + 4, st));
@@ -1149,6 +1324,9 @@ claire_status claire_destroy(claire_ctx* c) {
   if (!c) return CLAIRE_OK;
   cudaDeviceSynchronize();
   if (c->coarse) claire_destroy(c->coarse);
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+  if (c->pcg_cap_stream) cudaStreamDestroy(c->pcg_cap_stream);
   for (auto& r : c->prof_recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -1171,6 +1349,7 @@ claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   out->halo_y = c->haloY;
   out->halo_x_heavy = c->haloXh;
   out->halo_y_heavy = c->haloYh;
+  out->pcg_graph_runs = c->pcg_graph_runs;
   return CLAIRE_OK;
 }
 

@@ -349,7 +349,11 @@ template <class T>
 __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ Bt,
                                                      cplx<T>* __restrict__ R, cplx<T>* __restrict__ Vt, T kappa,
                                                      int regnorm, int kmode, T rw, T beta, Dims d,
-                                                     double* __restrict__ partials) {
+                                                     double* __restrict__ partials, const double* __restrict__ ps) {
+  if (ps) {  // device-driven PCG: kappa from the state block; nothing to do once the iteration has ended
+    if (ps[kPcgDone] != 0.0) return;
+    kappa = T(ps[kPcgKappa]);
+  }
   const long long s = d.Ns;
   Acc<T> acc[2];
   HLOOP {
@@ -382,7 +386,11 @@ __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ S, T mu,
                                                     int regnorm, int kmode, T rw, T beta, Dims d,
-                                                    double* __restrict__ partials) {
+                                                    double* __restrict__ partials, const double* __restrict__ ps) {
+  if (ps) {
+    if (ps[kPcgDone] != 0.0) return;
+    mu = T(ps[kPcgMu]);
+  }
   const long long s = d.Ns;
   Acc<T> acc[1];
   HLOOP {
@@ -720,18 +728,19 @@ claire_status sp_pcg0(claire_ctx* c, const cplx<T>* G, cplx<T>* R, cplx<T>* S, c
 }
 template <class T>
 claire_status sp_pcg_step(claire_ctx* c, const cplx<T>* S, const cplx<T>* Bt, cplx<T>* R, cplx<T>* Vt, double kappa,
-                          double* partials, cudaStream_t st) {
+                          double* partials, cudaStream_t st, const double* ps) {
   c->prof_begin("sp_pcg_step", st);
   k_sp_pcg_step<T><<<kReduceBlocks, 256, 0, st>>>(S, Bt, R, Vt, T(kappa), c->o.regnorm, kmode_of(c), T(rw_of(c)),
-                                                  T(c->o.beta), c->d, partials);
+                                                  T(c->o.beta), c->d, partials, ps);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
 template <class T>
-claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cplx<T>* S, double mu, double* partials, cudaStream_t st) {
+claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cplx<T>* S, double mu, double* partials, cudaStream_t st,
+                         const double* ps) {
   c->prof_begin("sp_pcg_dir", st);
   k_sp_pcg_dir<T><<<kReduceBlocks, 256, 0, st>>>(R, S, T(mu), c->o.regnorm, kmode_of(c), T(rw_of(c)), T(c->o.beta),
-                                                 c->d, partials);
+                                                 c->d, partials, ps);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -821,8 +830,9 @@ claire_status tl_dir(claire_ctx* c, const cplx<T>* Z, cplx<T>* S, double mu, dou
   template claire_status sp_pcg0<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, double*,           \
                                     cudaStream_t);                                                               \
   template claire_status sp_pcg_step<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, double,  \
-                                        double*, cudaStream_t);                                                  \
-  template claire_status sp_pcg_dir<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double, double*, cudaStream_t);     \
+                                        double*, cudaStream_t, const double*);                                   \
+  template claire_status sp_pcg_dir<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double, double*, cudaStream_t,      \
+                                       const double*);                                                           \
   template claire_status sp_project_dot<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double*, cudaStream_t);        \
   template claire_status sp_trial<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, double,      \
                                      double*, cudaStream_t);                                                     \

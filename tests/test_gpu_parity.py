@@ -292,6 +292,37 @@ def test_register_host_arrays_match_device_arrays(prec):
     assert torch.equal(vh, vd.cpu())
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("problem", ["cfg0", "h2_divfree"])
+def test_device_driven_pcg_graph_is_bit_identical_to_the_host_loop(prec, problem, monkeypatch):
+    """Alg. 2 run as one CUDA graph per solve (conditional WHILE node, scalars on the device) against the
+    host-driven loop (CLAIRE_PCG=host): same iterates bit for bit, same counts."""
+    if problem == "cfg0":
+        p, kw, mT, mR = cfg0(n=(24, 20, 16))
+    else:
+        n = (32, 32, 32)
+        kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, max_gn=4, gtol_rel=1e-2)
+        mT = I.brain_phantom(n, 0)
+        vs = I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=2.0, divfree=True)
+        p = O.Problem(n, **kw)
+        mR = O.transport(p, mT, vs, +1)
+    runs = {}
+    for mode in ("host", "graph"):
+        if mode == "host":
+            monkeypatch.setenv("CLAIRE_PCG", "host")
+        else:
+            monkeypatch.delenv("CLAIRE_PCG", raising=False)
+        with ctx(p.n, prec, **kw) as c:
+            v, rep, status = c.register(dev(mT, prec), dev(mR, prec))
+            runs[mode] = (v.cpu(), rep, status, c.pcg_graph_runs())
+    (vh, rh, sh, gh), (vg, rg, sg, gg) = runs["host"], runs["graph"]
+    assert gh == 0 and gg >= max(1, rg["gn_iters"])  # one graph launch per PCG solve
+    assert sh == sg
+    for k in ("gn_iters", "matvecs", "pde_solves", "ls_trials", "pcg_breakdowns", "converged"):
+        assert rh[k] == rg[k], k
+    assert torch.equal(vh, vg)
+
+
 def test_degenerate_identical_images_converge_immediately():
     n = (16, 16, 16)
     mT = I.trig_image(n, 0)
