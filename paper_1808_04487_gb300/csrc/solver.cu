@@ -553,7 +553,7 @@ template <class T> void pcg_graph_release(claire_ctx* c) {
 
 // the PCG loop graph for the current gather schedule and beta_v (captured on first use, and again when either
 // changed: both are baked into the captured kernels)
-template <class T> claire_status pcg_graph_get(claire_ctx* c, cudaStream_t launch_st, bool* ok) {
+template <class T> claire_status pcg_graph_get(claire_ctx* c, bool* ok) {
   *ok = false;
   const bool verbose = [] {
     const char* m = std::getenv("CLAIRE_PCG");
@@ -576,7 +576,7 @@ template <class T> claire_status pcg_graph_get(claire_ctx* c, cudaStream_t launc
   cudaError_t e;
   if (!c->pcg_cap_stream && (e = cudaStreamCreateWithFlags(&c->pcg_cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return fail("capture stream", e);
-  // the capture records nothing that runs: the work of this solve so far (on launch_st) is ordered by the launch
+  // captured launches do not run, so capturing on a stream of its own needs no ordering against the solve's stream
   cudaStream_t st = c->pcg_cap_stream;
   cudaGraph_t g = nullptr;
   if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return fail("graph", e);
@@ -673,7 +673,7 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
   const char* mode = std::getenv("CLAIRE_PCG");
   if (!two && !c->prof_on && !c->pcg_graph_failed && !(mode && std::strcmp(mode, "host") == 0)) {
     bool ok = false;
-    CL_TRY(pcg_graph_get<T>(c, st, &ok));
+    CL_TRY(pcg_graph_get<T>(c, &ok));
     if (!ok) {
       c->pcg_graph_failed = true;
     } else {
