@@ -173,8 +173,9 @@ __device__ __forceinline__ T gather(const T* __restrict__ f, const Stencil<T>& s
 // ---------------------------------------------------------------------------------------------------------------
 // Shared-memory bricks. A CTA of 16 x 16 threads handles a tile of 16 (i3) x 16 (i2) x 4 (i1) nodes. With every
 // displacement bounded by D voxels (measured after the departure points are computed), all stencils of the tile
-// lie in the brick of nodes [tile - H, tile + H] per axis, H = ceil(D) + 1 below and one more above. The brick is
-// loaded once with coalesced periodic-wrapped reads; each of the 64 taps then is a shared-memory read instead of
+// lie in the brick of nodes [tile - H, tile + H] per axis, H = ceil(D) + 1 below and one more above (along i3 widened
+// to 16-byte boundaries). The brick is loaded once with coalesced periodic-wrapped reads (whole 16-byte copies away
+// from the box's faces); each of the 64 taps then is a shared-memory read instead of
 // L1 lines. A warp holds 16 (i3) x 2 (i2) nodes, and the brick's row pitch px is 16 modulo 32 words (as is its
 // plane pitch), so the two half-warps -- and lanes whose stencils sit one row or plane apart -- read disjoint
 // bank ranges: with 32 nodes along one row, stencil spans over 32 words made two-way bank conflicts (measured:
@@ -182,7 +183,10 @@ __device__ __forceinline__ T gather(const T* __restrict__ f, const Stencil<T>& s
 constexpr int kTX = 16, kTY = 16, kTZ = 4;
 
 template <int H> struct TileGeom {
-  static constexpr int ex = kTX + 2 * H + 1, ey = kTY + 2 * H + 1, ez = kTZ + 2 * H + 1;
+  // along i3 the brick starts xa nodes left of the tile, on a 16-byte boundary, and its width ex (a multiple of 4)
+  // covers [x0 - H, x0 + kTX + H]: rows load as whole 16-byte copies
+  static constexpr int xa = (H + 3) / 4 * 4;
+  static constexpr int ex = kTX + xa + (H + 4) / 4 * 4, ey = kTY + 2 * H + 1, ez = kTZ + 2 * H + 1;
   static constexpr int px = ex + (16 - ex % 32 + 32) % 32;  // row pitch: >= ex, 16 mod 32
   static constexpr int vol = px * ey * ez;
   static_assert(px % 32 == 16 && (px * ey) % 32 == 16, "row and plane pitch 16 mod 32 words");
@@ -199,7 +203,7 @@ template <int H> __device__ __forceinline__ Tile tile_of(const Dims& d) {
   t.x0 = blockIdx.x * kTX;
   t.y0 = blockIdx.y * kTY;
   t.z0 = blockIdx.z * kTZ;
-  t.interior = t.x0 - H >= 0 && t.x0 - H + G::ex <= d.n3 && t.y0 - H >= 0 && t.y0 - H + G::ey <= d.n2 &&
+  t.interior = t.x0 - G::xa >= 0 && t.x0 - G::xa + G::ex <= d.n3 && t.y0 - H >= 0 && t.y0 - H + G::ey <= d.n2 &&
                t.z0 - H >= 0 && t.z0 - H + G::ez <= d.n1;
   return t;
 }
@@ -211,6 +215,10 @@ template <class T> __device__ __forceinline__ void cp_async_elem(T* sdst, const 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -224,9 +232,21 @@ __device__ __forceinline__ void load_bricks(T* sm, const T* __restrict__ f0, con
                                             const Dims& d) {
   using G = TileGeom<H>;
   constexpr int rows = G::ey * G::ez;
-  if (tl.interior) {
-    const T* g0 = f0 + ((tl.z0 - H) * d.n2 + (tl.y0 - H)) * d.n3 + (tl.x0 - H);
-    const T* g1 = f1 ? f1 + ((tl.z0 - H) * d.n2 + (tl.y0 - H)) * d.n3 + (tl.x0 - H) : nullptr;
+  const T* g0 = f0 + ((tl.z0 - H) * d.n2 + (tl.y0 - H)) * d.n3 + (tl.x0 - G::xa);
+  const T* g1 = f1 ? f1 + ((tl.z0 - H) * d.n2 + (tl.y0 - H)) * d.n3 + (tl.x0 - G::xa) : nullptr;
+  // 16-byte copies: FP32, rows of a multiple of 4 words, fields on 16-byte boundaries
+  const bool vec = sizeof(T) == 4 && (d.n3 & 3) == 0 && ((reinterpret_cast<uintptr_t>(f0) | reinterpret_cast<uintptr_t>(f1)) & 15) == 0;
+  if (tl.interior && vec) {
+    constexpr int nv = G::ex * (int)sizeof(T) / 16;  // 16-byte vectors per row
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    for (int q = tid; q < rows * nv; q += kTX * kTY) {
+      const int row = q / nv, v = q - row * nv;
+      const int z = row / G::ey, y = row - z * G::ey;
+      const int goff = z * d.n2 * d.n3 + y * d.n3 + 4 * v;
+      cp_async_16(sm + row * G::px + 4 * v, g0 + goff);
+      if (f1) cp_async_16(sm + G::vol + row * G::px + 4 * v, g1 + goff);
+    }
+  } else if (tl.interior) {
 #pragma unroll 2
     for (int row = threadIdx.y; row < rows; row += kTY) {
       const int z = row / G::ey, y = row - z * G::ey;
@@ -243,7 +263,7 @@ __device__ __forceinline__ void load_bricks(T* sm, const T* __restrict__ f0, con
       const int gz = wrapc(tl.z0 - H + z, d.n1), gy = wrapc(tl.y0 - H + y, d.n2);
       const int base = (gz * d.n2 + gy) * d.n3;
       for (int x = threadIdx.x; x < G::ex; x += kTX) {
-        const int gx = wrapc(tl.x0 - H + x, d.n3);
+        const int gx = wrapc(tl.x0 - G::xa + x, d.n3);
         cp_async_elem<T>(sm + row * G::px + x, f0 + base + gx);
         if (f1) cp_async_elem<T>(sm + G::vol + row * G::px + x, f1 + base + gx);
       }
@@ -257,7 +277,7 @@ __device__ __forceinline__ bool in_brick(const Stencil<T>& s, const Tile& tl, in
   using G = TileGeom<H>;
   lz = s.b1 - (tl.z0 - H);
   ly = s.b2 - (tl.y0 - H);
-  lx = s.b3 - (tl.x0 - H);
+  lx = s.b3 - (tl.x0 - G::xa);
   return (unsigned)lz <= (unsigned)(G::ez - 4) && (unsigned)ly <= (unsigned)(G::ey - 4) &&
          (unsigned)lx <= (unsigned)(G::ex - 4);
 }

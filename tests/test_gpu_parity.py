@@ -204,13 +204,13 @@ def test_objective_gradient_hessvec(n, prec, case):
 
 
 @pytest.mark.parametrize("schedule", ["plain", "tiled"])
-def test_gather_schedules_match_the_oracle(schedule, monkeypatch):
+@pytest.mark.parametrize("n", [(40, 36, 42), (24, 40, 64)])
+def test_gather_schedules_match_the_oracle(schedule, n, monkeypatch):
     """Both FP32 gather schedules -- taps read from global memory, and taps read from shared-memory bricks of
-    16 x 16 x 4-node tiles -- on a 40 x 36 x 42 grid, whose i2 and i3 extents end in partial tiles, with
-    displacements that need a brick halo of 2 or more; the schedule is forced with CLAIRE_GATHER and read back
-    from the context."""
+    16 x 16 x 4-node tiles -- with displacements that need a brick halo of 2 or more: on 40 x 36 x 42, whose i2 and
+    i3 extents end in partial tiles (bricks loaded word by word), and on 24 x 40 x 64, whose interior tiles load
+    their bricks as 16-byte copies; the schedule is forced with CLAIRE_GATHER and read back from the context."""
     monkeypatch.setenv("CLAIRE_GATHER", schedule)
-    n = (40, 36, 42)
     case = dict(regnorm=2, divfree=True, nt=4)
     p = O.Problem(n, beta=1e-2, **case)
     mT = rounded(I.trig_image(n, 20), "f32")
