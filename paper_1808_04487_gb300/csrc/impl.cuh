@@ -52,7 +52,8 @@ template <class T> struct Work {
   double* scal = nullptr;      // device scalars
 };
 
-constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs
+constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: the FP32 kernels on this grid are compiled for 8 resident
+                                     // CTAs (32 registers), so the grid is one wave (two waves cost up to 1.5x)
 
 // Device-side PCG state (Alg. 2 driven from the device inside a CUDA graph): FP64 slots of Work::scal from kPcgBase.
 enum PcgSlot {

@@ -288,7 +288,7 @@ __device__ __forceinline__ void block_reduce_v(const Acc<T> (&accs)[V], double* 
 
 // G = beta a V + K B (V may be null: v = 0); partial ||G||^2
 template <class T>
-__global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ B,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_sp_grad(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ B,
                                                  cplx<T>* __restrict__ G, int regnorm, int kmode, T rw, T beta,
                                                  Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_sp_grad(const cplx<T>* __restrict__ V, 
 
 // PCG start (Alg. 2): R = -G, S = Z = M^-1 R, Vt = 0; partials <K^-1 R, Z>, ||R||^2, <K^-1 S, beta A S>
 template <class T>
-__global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ R,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_sp_pcg0(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ R,
                                                  cplx<T>* __restrict__ S, cplx<T>* __restrict__ Vt, int regnorm,
                                                  int kmode, T rw, T beta, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) k_sp_pcg0(const cplx<T>* __restrict__ G, 
 
 // PCG update: H S = beta a S + K Bt; R -= kappa H S; Vt += kappa S; partials ||R||^2, <K^-1 R, M^-1 R>
 template <class T>
-__global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ Bt,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_sp_pcg_step(const cplx<T>* __restrict__ S, const cplx<T>* __restrict__ Bt,
                                                      cplx<T>* __restrict__ R, cplx<T>* __restrict__ Vt, T kappa,
                                                      int regnorm, int kmode, T rw, T beta, Dims d,
                                                      double* __restrict__ partials, const double* __restrict__ ps) {
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) k_sp_pcg_step(const cplx<T>* __restrict__
 
 // PCG direction: S = M^-1 R + mu S; partial <K^-1 S, beta A S>
 template <class T>
-__global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ S, T mu,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_sp_pcg_dir(const cplx<T>* __restrict__ R, cplx<T>* __restrict__ S, T mu,
                                                     int regnorm, int kmode, T rw, T beta, Dims d,
                                                     double* __restrict__ partials, const double* __restrict__ ps) {
   if (ps) {
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(256) k_sp_pcg_dir(const cplx<T>* __restrict__ 
 
 // projection Vt = K Vt under div v = 0 (kmode 1), then partial <K^-1 G, Vt> (the slope of J along Vt)
 template <class T>
-__global__ void __launch_bounds__(256) k_sp_project_dot(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Vt,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_sp_project_dot(const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Vt,
                                                         int kmode, T rw, Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
   Acc<T> acc[1];
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(256) k_tl_scale(const cplx<T>* __restrict__ P,
 
 // HP = P + R^-1/2 K Bt (Bt: transform of the data term at U = R^-1/2 P); partial <K^-1 HP, P>
 template <class T>
-__global__ void __launch_bounds__(256) k_tl_apply(const cplx<T>* __restrict__ P, const cplx<T>* __restrict__ Bt,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_tl_apply(const cplx<T>* __restrict__ P, const cplx<T>* __restrict__ Bt,
                                                   cplx<T>* __restrict__ HP, Dims dc, int regnorm, T beta, int kmode,
                                                   T rw, double* __restrict__ partials) {
   Acc<T> acc[1];
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(256) k_tl_apply(const cplx<T>* __restrict__ P,
 
 // X += alpha P, Rr -= alpha HP; partials ||Rr||^2 and <K^-1 Rr, Rr>
 template <class T>
-__global__ void __launch_bounds__(256) k_tl_update(cplx<T>* __restrict__ X, cplx<T>* __restrict__ Rr,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_tl_update(cplx<T>* __restrict__ X, cplx<T>* __restrict__ Rr,
                                                    const cplx<T>* __restrict__ P, const cplx<T>* __restrict__ HP,
                                                    T alpha, Dims dc, int kmode, T rw, double* __restrict__ partials) {
   Acc<T> acc[2];
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(256) k_tl_dir2(const cplx<T>* __restrict__ Rr,
 
 // fine Z = R^-1/2 (y with its coarse modes replaced by scale * X), y = R^-1/2 R; partial <K^-1 R, Z>
 template <class T>
-__global__ void __launch_bounds__(256) k_tl_prolong(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ X,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_tl_prolong(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ X,
                                                     cplx<T>* __restrict__ Z, Dims df, Dims dc, int regnorm, T beta,
                                                     int kmode, T rw, T scale, double* __restrict__ partials) {
   Acc<T> acc[1];
