@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--ws-steps", type=int, default=4000, help="warmstart: Adam steps")
     ap.add_argument("--ws-batch", type=int, default=8, help="warmstart: minibatch")
     ap.add_argument("--ws-lr", type=float, default=1e-3)
+    ap.add_argument("--ws-net", type=int, default=64, help="warmstart: grid of the network (per axis)")
     ap.add_argument("--ws-eval", type=int, default=16, help="warmstart: held-out pairs on the training grid")
     ap.add_argument("--ws-eval256", type=int, default=4, help="warmstart: held-out pairs at 256^3")
     ap.add_argument("--ws-fp64", type=int, default=4, help="warmstart: held-out pairs also solved in FP64")
@@ -406,8 +407,9 @@ def batch_study(args):
 def warmstart_study(args):
     """Learned warm start: a training set of (m_T, m_R, v) triples made by the plain solver on ws_solve^3 (seeded
     phantoms, divergence-free band-limited v*, |k| <= 6, the 8-voxels-at-256^3 amplitude), the network trained on
-    their 32^3 spectral truncations, then held-out pairs (unseen phantom seeds and velocities) solved from v = 0
-    and from the network's prediction with the same stopping rule ||g|| <= 1e-2 ||g(v=0)||."""
+    their spectral truncations to the network grid (--ws-net, 64^3 by default), then held-out pairs (unseen phantom
+    seeds and velocities) solved from v = 0 and from the network's prediction with the same stopping rule
+    ||g|| <= 1e-2 ||g(v=0)||."""
     import numpy as np
     import torch
 
@@ -420,7 +422,7 @@ def warmstart_study(args):
     def log(msg):
         print(msg, file=sys.stderr, flush=True)
 
-    n_net = (32, 32, 32)
+    n_net = (args.ws_net,) * 3
     n_tr = (args.ws_solve,) * 3
     t0 = time.perf_counter()
     images, targets, gen = WS.make_training_set(args.ws_count, n_solve=n_tr, n_net=n_net, seed=0, phantoms=64,
@@ -467,7 +469,7 @@ def warmstart_study(args):
             (vz, rz, sz), tz = timed(lambda: ctx.register(mT, mR))
             row = {"zero": {"status": sz, "seconds": tz, **{k: rz[k] for k in ("gn_iters", "matvecs", "pde_solves")},
                             "rel_mismatch": rz["mismatch"] / rz["mismatch0"], "rel_grad": rz["gnorm"] / rz["gnorm0"]}}
-            # the best a network on the 32^3 grid can do: the zero-start solution itself, truncated to that grid
+            # the best a network on its grid can do: the zero-start solution itself, truncated to that grid
             vt = ctx_net.resample_to(ctx, ctx.resample_to(ctx_net, vz), project=SOLVER_KW["divfree"])
             (_, rt, st_), tt = timed(lambda: ctx.register(mT, mR, vt.clone()))
             row["truncated_solution"] = {"status": st_, "seconds": tt,
