@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--ws-batch", type=int, default=8, help="warmstart: minibatch")
     ap.add_argument("--ws-lr", type=float, default=1e-3)
     ap.add_argument("--ws-net", type=int, default=64, help="warmstart: grid of the network (per axis)")
+    ap.add_argument("--ws-augment", type=int, default=1, help="warmstart: random cube symmetries of the minibatches")
     ap.add_argument("--ws-eval", type=int, default=16, help="warmstart: held-out pairs on the training grid")
     ap.add_argument("--ws-eval256", type=int, default=4, help="warmstart: held-out pairs at 256^3")
     ap.add_argument("--ws-fp64", type=int, default=4, help="warmstart: held-out pairs also solved in FP64")
@@ -439,7 +440,8 @@ def warmstart_study(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = WS.train(ws, tr_img, tr_tgt, args.ws_steps, lr=args.ws_lr, lr_final=args.ws_lr / 30.0, seed=0,
-                      val=(va_img, va_tgt), log=log, log_every=max(1, args.ws_steps // 10))
+                      val=(va_img, va_tgt), log=log, log_every=max(1, args.ws_steps // 10),
+                      augment=bool(args.ws_augment))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     val1 = WS.evaluate(ws, va_img, va_tgt)
@@ -527,6 +529,7 @@ def warmstart_study(args):
                                        "converged": gen["converged"], "mean_gn": float(np.mean(gen["gn_iters"])),
                                        "mean_matvecs": float(np.mean(gen["matvecs"]))},
                       "training": {"steps": args.ws_steps, "seconds": t_train, "lr": args.ws_lr,
+                                   "augment": bool(args.ws_augment),
                                    "val_loss_initial": val0, "val_loss_final": val1, "train_loss_final": train1,
                                    "curve": losses[:: max(1, len(losses) // 20)]},
                       "solver": SOLVER_KW, "eval": evals}), flush=True)

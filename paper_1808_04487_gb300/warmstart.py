@@ -309,19 +309,50 @@ def make_training_set(count, n_solve=(128, 128, 128), n_net=(32, 32, 32), seed=0
     return images, targets, stats
 
 
-def train(ws, images, targets, steps, lr=1e-3, lr_final=3e-5, seed=0, val=None, log=None, log_every=200):
+def cube_symmetry(images, targets, flips, perm):
+    """One symmetry of the periodic cube applied to a minibatch (a data transform, no arithmetic of the method): the
+    reflection x_a -> -x_a (index i -> (n - i) mod n) for each axis a with flips[a], then the axis permutation
+    (new axis c = old axis perm[c]). Images [B, C, n, n, n] transform as scalars; a velocity [B, 3, n, n, n] as a
+    vector: a reflected axis negates its component, a permutation reorders the components. The registration
+    problem (periodic domain, isotropic regularisation, Leray projection) is equivariant under these maps, so the
+    transformed pair's solution is the transformed solution."""
+    torch = _torch()
+    for a in range(3):
+        if flips[a]:
+            d = 2 + a
+            images = torch.roll(torch.flip(images, [d]), 1, d)
+            targets = torch.roll(torch.flip(targets, [d]), 1, d)
+            targets[:, a] = -targets[:, a]
+    order = (0, 1) + tuple(2 + p for p in perm)
+    images = images.permute(order).contiguous()
+    targets = targets.permute(order)[:, list(perm)].contiguous()
+    return images, targets
+
+
+def train(ws, images, targets, steps, lr=1e-3, lr_final=3e-5, seed=0, val=None, log=None, log_every=200,
+          augment=False):
     """Adam with a cosine learning-rate schedule over random minibatches of ws.batch rows.
 
-    val = (images, targets) is evaluated every log_every steps. Returns the per-step training losses."""
+    augment: each minibatch goes through a random symmetry of the periodic cube (cube_symmetry; permutations only
+    on cubic grids). val = (images, targets) is evaluated every log_every steps. Returns the per-step training
+    losses."""
     rng = np.random.default_rng(seed)
     S = images.shape[0]
+    cubic = len(set(images.shape[2:])) == 1
     losses = []
     t0 = time.time()
     for it in range(steps):
         idx = rng.choice(S, size=min(ws.batch, S), replace=False)
         a = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * it / max(1, steps)))
         want = (it % 20 == 0) or it == steps - 1
-        l = ws.train_step(images, targets, idx, a, want_loss=want)
+        if augment:
+            flips = rng.integers(0, 2, size=3)
+            perm = tuple(rng.permutation(3)) if cubic else (0, 1, 2)
+            ti = _torch().as_tensor(idx, device=images.device)
+            bi, bt = cube_symmetry(images.index_select(0, ti), targets.index_select(0, ti), flips, perm)
+            l = ws.train_step(bi, bt, np.arange(len(idx)), a, want_loss=want)
+        else:
+            l = ws.train_step(images, targets, idx, a, want_loss=want)
         if want:
             losses.append((it, l))
         if log and (it % log_every == 0 or it == steps - 1):
