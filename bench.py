@@ -18,6 +18,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -161,7 +162,9 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+        # raw samples (the JSON line carries their summary): CLAIRE_CLOCKS_DIR, else the system's temporary folder
+        folder = os.environ.get("CLAIRE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, "claire_clocks_rank%d.csv" % device_index)
 
     def start(self):
         try:
