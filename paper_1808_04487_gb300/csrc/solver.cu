@@ -544,7 +544,7 @@ __global__ void k_pcg_next(double* __restrict__ ps, const double* __restrict__ s
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
-template <class T> void pcg_graph_release(claire_ctx* c) {
+void pcg_graph_release(claire_ctx* c) {
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
   c->pcg_exec = nullptr;
@@ -569,7 +569,7 @@ template <class T> claire_status pcg_graph_get(claire_ctx* c, bool* ok) {
     *ok = true;
     return CLAIRE_OK;
   }
-  pcg_graph_release<T>(c);
+  pcg_graph_release(c);
   Work<T>& W = c->work<T>();
   const double sc = cellvol(c->d) / double(c->d.N);
   double* ps = W.scal + kPcgBase;
