@@ -3,8 +3,9 @@
 // Memory-reduced Gauss-Newton (Sec. 3.5): the state history m^j and its spectral gradients are kept per
 // linearisation (departure points are computed once per v, Sec. 3.4); the adjoint and incremental adjoint are
 // never stored in time, their time integrals are accumulated during the backward sweeps. The host drives the
-// outer (Alg. 1) and inner (Alg. 2) loops; every scalar it needs (objective, norms, PCG scalars, Armijo test)
-// is reduced in FP64 on the device and read back once per use.
+// outer loop (Alg. 1); every scalar it needs (objective, norms, Armijo test) is reduced in FP64 on the device and
+// read back once per use. The inner loop (Alg. 2) runs either on the host the same way or, with the spectral
+// preconditioner and per-kernel profiling off, as one CUDA graph launch whose scalars stay on the device.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
