@@ -79,3 +79,24 @@ def test_radix_support_matches_the_batched_grids():
             while m % r == 0:
                 m //= r
         assert m == 1 and (n // 2) * 2 == n
+
+
+def test_convolution_workspaces_follow_the_batch_invariant_split_rule(L):
+    """Host-only sizing of the convolution workspaces (no device call). The forward split-K over the 27 neighbour
+    offsets is chosen from the per-sample grid alone, so a sample's result does not depend on its batch: the
+    partial-sum workspace is zero for grids with enough 128-voxel tiles and otherwise scales exactly with the batch.
+    Invalid shapes (channels not a multiple of 16, more than 128) size to 0."""
+    f = L.claire_nn_fwd_workspace_bytes
+    f.restype = ctypes.c_size_t
+    f.argtypes = [ctypes.c_int] * 5
+    assert f(1, 64, 64, 64, 16) == 0          # 8 x 64^3 / 128 tiles: no split
+    assert f(1, 32, 32, 32, 16) == 0          # 8 x 32^3 / 128 = 2048 tiles: no split
+    small = f(1, 8, 8, 8, 64)
+    assert small > 0                           # 8 x 8^3 / 128 = 32 tiles: split
+    for B in (2, 3, 8):
+        assert f(B, 8, 8, 8, 64) == B * small
+    assert f(1, 8, 8, 8, 24) == 0 and f(1, 8, 8, 8, 144) == 0 and f(0, 8, 8, 8, 64) == 0
+    w = L.claire_nn_wgrad_workspace_bytes
+    w.restype = ctypes.c_size_t
+    w.argtypes = [ctypes.c_int] * 6
+    assert w(8, 32, 32, 32, 16, 16) > 0 and w(8, 32, 32, 32, 16, 24) == 0
