@@ -25,8 +25,14 @@
  *             and return without synchronising, except where a host scalar or report is returned: those calls
  *             synchronise that stream before returning.
  * Errors      no exception crosses the ABI; every call returns a claire_status. On failure the context keeps a
- *             message readable with claire_last_error(). Inputs are not validated for NaN on the device, but
- *             a non-finite objective, gradient norm or PCG scalar makes the solver return CLAIRE_ENAN.
+ *             message readable with claire_last_error(). claire_register_* scans m_T, m_R and the initial v on the
+ *             device and returns CLAIRE_ENAN if any value is NaN or infinite (nothing else runs, v is unchanged);
+ *             a non-finite objective, gradient norm or PCG scalar during the solve also returns CLAIRE_ENAN. The
+ *             operator calls (transport, gradient, matvec, ...) do not scan their inputs.
+ * Faults      for tests of the failure paths only, the environment variable CLAIRE_FAULT (a comma-separated list)
+ *             fakes a failure on the host where the library reads a device result: "pcg_breakdown" makes the
+ *             first <s, H s> of every PCG solve read as non-positive (the host-driven loop then runs),
+ *             "nn_timeout" makes claire_nn_status report an expired tensor-core wait. Unset in normal use.
  * Threads     a context is not thread safe; use one context per host thread (or serialise calls).
  * Discrete    inner product <a, b> = h1 h2 h3 sum a*b; forward FFT unnormalised, inverse scaled by 1/N;
  * readings    first-order spectral symbols use k' (Nyquist set to 0), even-order symbols the full k; RK2 (Heun)
@@ -51,7 +57,10 @@ typedef enum {
     CLAIRE_ENAN = 4,         /* a non-finite objective, gradient norm or PCG scalar was produced */
     CLAIRE_ENOTCONV = 5,     /* register: max_gn Gauss-Newton iterations reached; v holds the last iterate */
     CLAIRE_ELINESEARCH = 6,  /* register: Armijo failed after max_ls trials; v holds the last accepted iterate */
-    CLAIRE_EBREAKDOWN = 7    /* PCG: <s, H s> <= 0 (reported in the report's flags; the solve continues) */
+    CLAIRE_EBREAKDOWN = 7,   /* PCG: <s, H s> <= 0 (counted in claire_report.pcg_breakdowns; the solve continues,
+                                no call returns this status) */
+    CLAIRE_ETIMEOUT = 8      /* a bounded device wait expired (the warm-start network's tensor-core waits, about
+                                a second each); the kernel released its resources and the context stays usable */
 } claire_status;
 
 typedef enum { CLAIRE_F32 = 0, CLAIRE_F64 = 1 } claire_precision;
@@ -160,6 +169,14 @@ claire_status claire_hessvec_cached_f64(claire_ctx* ctx, const double* vt, doubl
  * recurrence. vt and out must not alias. */
 claire_status claire_hessvec_data_f32(claire_ctx* ctx, const float* vt, float* out, void* stream);
 claire_status claire_hessvec_data_f64(claire_ctx* ctx, const double* vt, double* out, void* stream);
+/* Data term of the reduced gradient alone, out = K[int_0^1 lambda grad m dt] (Eq. (5) without beta A v), at
+ * (mT, mR, v); the linearisation at v stays cached as after claire_gradient_*. If J is not NULL the objective J(v)
+ * is written to *J (host double; the call then synchronises). With beta A v known in closed form (it is a Fourier
+ * multiplier, see claire_symbol_*), this is the part of the gradient that the transport solves produce. */
+claire_status claire_gradient_data_f32(claire_ctx* ctx, const float* mT, const float* mR, const float* v, float* out,
+                                       double* J, void* stream);
+claire_status claire_gradient_data_f64(claire_ctx* ctx, const double* mT, const double* mR, const double* v,
+                                       double* out, double* J, void* stream);
 /* Cache the linearisation at (mT, v) without computing anything else. */
 claire_status claire_linearize_f32(claire_ctx* ctx, const float* mT, const float* v, void* stream);
 claire_status claire_linearize_f64(claire_ctx* ctx, const double* mT, const double* v, void* stream);
@@ -174,8 +191,10 @@ claire_status claire_precond_f64(claire_ctx* ctx, const double* r, double* z, vo
  * v is in/out: on entry the initial guess (zeros = the plain method), on return the solution. With div v = 0 a
  * nonzero guess is first Leray-projected (Sec. 2.2). The relative stopping test always uses ||g(v = 0)||
  * (Sec. 2.3.2), also for a nonzero initial guess. rep (host) may be NULL.
- * Returns CLAIRE_OK on convergence, CLAIRE_ENOTCONV when max_gn is reached, CLAIRE_ELINESEARCH when Armijo
- * fails (v = last accepted iterate), CLAIRE_ENAN on a non-finite objective or gradient. Synchronises stream. */
+ * Returns CLAIRE_OK on convergence, CLAIRE_ENOTCONV when max_gn is reached (v = the last iterate, a valid
+ * solution of lower accuracy), CLAIRE_ELINESEARCH when Armijo fails (v = the last accepted iterate), CLAIRE_ENAN
+ * when m_T, m_R or the initial v hold a NaN or an infinity (checked on the device before anything else runs; v is
+ * left unchanged) or the objective or gradient becomes non-finite. Synchronises stream. */
 claire_status claire_register_f32(claire_ctx* ctx, const float* mT, const float* mR, float* v, claire_report* rep,
                                   void* stream);
 claire_status claire_register_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
@@ -246,6 +265,15 @@ claire_status claire_dot_f32(claire_ctx* ctx, const float* a, const float* b, lo
 claire_status claire_dot_f64(claire_ctx* ctx, const double* a, const double* b, long long count, double* out,
                              void* stream);
 
+/* A diagonal Fourier symbol of the method applied to ncomp (1..3) half spectra (layout of claire_fft_*, component
+ * stride n1*n2*(n3/2+1) complex values; in and out may alias): op 0: out = beta a(k) in, the regularisation
+ * operator beta A of Eq. (2) (a = |k|^2 for H1, |k|^4 for H2, full k); op 1: out = M^-1 in, the spectral
+ * preconditioner (beta A)^-1 with the zero eigenvalue replaced by 1 (Sec. 2.3.3); op 2 (ncomp = 3): out = K in,
+ * the context's K of Eq. (5) (identity, the Leray projection of Sec. 2.2, or the H1-div operator). These are the
+ * exact diagonal multiplies the solver applies to its Fourier-domain vectors. Bad op/ncomp: CLAIRE_EINVAL. */
+claire_status claire_symbol_f32(claire_ctx* ctx, int op, const float* in, float* out, int ncomp, void* stream);
+claire_status claire_symbol_f64(claire_ctx* ctx, int op, const double* in, double* out, int ncomp, void* stream);
+
 /* Unnormalised forward 3D real FFT of a scalar (Sec. 2.3.1): spec is the half spectrum [n1][n2][n3/2+1] of
  * interleaved (re, im) pairs, i.e. 2*n1*n2*(n3/2+1) values. claire_ifft_* is the inverse, scaled by 1/N; it
  * reads spec as a Hermitian half spectrum and does not modify it. */
@@ -272,8 +300,10 @@ typedef struct {
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 
 /* Inner product that allocates nothing (the paper has no counterpart; this is a service for callers).
- * *out (a DEVICE pointer to one double, written on `stream`) = scale * sum_i a[i] * b[i] over `count` floats,
- * accumulated in FP64 with the same kernels and summation order as claire_dot_f32 (pass scale = h1 h2 h3 to get
+ * *out (a DEVICE pointer to one double, written on `stream`) = scale * sum_i a[i] * b[i] over `count` floats. It
+ * runs the reduction kernels of claire_dot_f32 -- per-thread float-float (FP64-class) accumulation, FP64 block
+ * and final sums -- but on a grid of ceil(count / 2048) blocks instead of that call's fixed grid, so the summation
+ * order differs and the result equals claire_dot_f32's up to rounding, not bitwise (pass scale = h1 h2 h3 to get
  * that call's <a, b>). No context is needed, and the call makes no cudaMalloc/cudaFree and calls no allocating
  * library: it is meant for callers that must not allocate device memory, e.g. code running inside a fixed
  * memory budget or a framework allocator that owns the device, or a loop that cannot afford cudaMalloc's implicit
@@ -283,7 +313,8 @@ claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
  * CLAIRE_ECUDA). The array is shared by every call in the process: calls whose kernels overlap on the GPU (two
  * streams, or two host threads) race on it and must be serialised by the caller; nothing in it needs clearing
  * between calls. The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. */
+ * that device current and keeps it; make that first call before any stream capture, and do not use the call
+ * across a reset of the device (cudaDeviceReset), which invalidates the kept address. */
 claire_status claire_dot_noalloc_f32(const float* a, const float* b, long long count, double scale, double* out,
                                      void* stream);
 
@@ -392,8 +423,8 @@ claire_status claire_nn_mse(const float* pred, const float* target, float* grad,
 claire_status claire_nn_adam(float* p, const float* g, float* m1, float* m2, void* pb, long long count, float lr,
                              float b1, float b2, float eps, int step, void* stream);
 /* Synchronises the stream, then reports whether a convolution's bounded tensor-core wait timed out since the last
- * call (CLAIRE_ECUDA; the flag is cleared) or CLAIRE_OK. claire_ws_loss_f32 / _train_step_f32 (with a loss) and
- * claire_ws_predict_f32 check it themselves. */
+ * call (CLAIRE_ETIMEOUT; the flag is cleared), a CUDA error (CLAIRE_ECUDA) or CLAIRE_OK. claire_ws_loss_f32 /
+ * _train_step_f32 (with a loss) and claire_ws_predict_f32 check it themselves and return the same statuses. */
 claire_status claire_nn_status(void* stream);
 
 #ifdef __cplusplus

@@ -18,8 +18,8 @@ __all__ = ["Context", "ClaireError", "Report", "lib", "LIB_PATH", "STATUS", "reg
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libclaire_gb.so")
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN", 5: "ENOTCONV", 6: "ELINESEARCH",
-          7: "EBREAKDOWN"}
-OK, EINVAL, ENOMEM, ECUDA, ENAN, ENOTCONV, ELINESEARCH, EBREAKDOWN = range(8)
+          7: "EBREAKDOWN", 8: "ETIMEOUT"}
+OK, EINVAL, ENOMEM, ECUDA, ENAN, ENOTCONV, ELINESEARCH, EBREAKDOWN, ETIMEOUT = range(9)
 
 
 class ClaireError(RuntimeError):
@@ -71,6 +71,8 @@ _LL = ctypes.c_longlong
 _TYPED = {
     "claire_transport": [_VP, _VP, _I, _VP, _VP],
     "claire_gradient": [_VP, _VP, _VP, _VP, _PD, _VP],
+    "claire_gradient_data": [_VP, _VP, _VP, _VP, _PD, _VP],
+    "claire_symbol": [_I, _VP, _VP, _I, _VP],
     "claire_hessvec": [_VP, _VP, _VP, _VP, _VP, _VP],
     "claire_hessvec_cached": [_VP, _VP, _VP],
     "claire_hessvec_data": [_VP, _VP, _VP],
@@ -301,6 +303,29 @@ class Context:
         self._call("claire_gradient", self._s(mT, "mT"), self._s(mR, "mR"), self._v(v, "v"), self._v(out, "g"),
                    ctypes.byref(J) if objective else None, self._stream())
         return (out, J.value) if objective else out
+
+    def gradient_data(self, mT, mR, v, out=None, objective=False):
+        """K[int lambda grad m dt]: the reduced gradient without beta A v (Eq. (5))."""
+        out = self.empty_vector() if out is None else out
+        J = ctypes.c_double(0.0)
+        self._call("claire_gradient_data", self._s(mT, "mT"), self._s(mR, "mR"), self._v(v, "v"),
+                   self._v(out, "out"), ctypes.byref(J) if objective else None, self._stream())
+        return (out, J.value) if objective else out
+
+    SYMBOL_OPS = {"betaA": 0, "precond": 1, "K": 2}
+
+    def symbol(self, op, spec, out=None):
+        """A diagonal Fourier symbol ("betaA", "precond" or "K") on half spectra of shape
+        (ncomp, n1, n2, n3//2 + 1, 2) (interleaved re/im, as returned by fft)."""
+        torch = _torch()
+        shp = (self.n[0], self.n[1], self.n[2] // 2 + 1, 2)
+        if (spec.device.type != "cuda" or spec.dtype != self.dtype or spec.dim() != 5 or tuple(spec.shape[1:]) != shp
+                or not spec.is_contiguous()):
+            raise ValueError("symbol: a contiguous CUDA tensor of shape (ncomp,) + %s required" % (shp,))
+        out = torch.empty_like(spec) if out is None else out
+        self._call("claire_symbol", self.SYMBOL_OPS[op], ctypes.c_void_p(spec.data_ptr()),
+                   ctypes.c_void_p(out.data_ptr()), int(spec.shape[0]), self._stream())
+        return out
 
     def linearize(self, mT, v):
         self._call("claire_linearize", self._s(mT, "mT"), self._v(v, "v"), self._stream())

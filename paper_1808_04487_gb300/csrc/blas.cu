@@ -42,6 +42,19 @@ __global__ void __launch_bounds__(256) k_diffsq(const T* __restrict__ a, const T
   block_partial(acc.value(), partials);
 }
 
+// number of non-finite values (NaN or +-Inf) in a[0..na) and b[0..nb), one partial per block
+template <class T>
+__global__ void __launch_bounds__(256) k_nonfinite(const T* __restrict__ a, long long na, const T* __restrict__ b,
+                                                   long long nb, double* __restrict__ partials) {
+  double cnt = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
+    const T x = i < na ? a[i] : b[i - na];
+    if (!isfinite(x)) cnt += 1.0;
+  }
+  block_partial(cnt, partials);
+}
+
 __global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partials, int np, double scale,
                                                        double* __restrict__ out) {
   __shared__ double red[32];
@@ -164,6 +177,14 @@ claire_status reduce_final(claire_ctx* c, const double* partials, double scale, 
   return CLAIRE_OK;
 }
 template <class T>
+claire_status nonfinite_partial(claire_ctx* c, const T* a, long long na, const T* b, long long nb, double* partials,
+                                cudaStream_t st) {
+  c->prof_begin("nonfinite", st);
+  k_nonfinite<T><<<kReduceBlocks, 256, 0, st>>>(a, na, b, nb, partials);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+template <class T>
 claire_status absmax_partial(claire_ctx* c, const T* a, long long n, double* partials, cudaStream_t st) {
   c->prof_begin("absmax", st);
   k_absmax<T><<<kReduceBlocks, 256, 0, st>>>(a, n, partials);
@@ -219,7 +240,8 @@ constexpr long long kNoAllocChunk = 256LL * 8;    // values reduced per block
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocBlocks];
 
 // Host-side address of g_noalloc_partials on each device, looked up once per device (the host symbol itself is
-// only a stand-in and must never be passed to a kernel).
+// only a stand-in and must never be passed to a kernel). The cached address belongs to the device's primary context:
+// after a reset of that context (cudaDeviceReset) it is stale, so the call must not be used across a device reset.
 static double* noalloc_scratch_on_current_device(claire_status* st) {
   static std::mutex mu;
   static double* addr[256] = {nullptr};
@@ -243,6 +265,8 @@ static double* noalloc_scratch_on_current_device(claire_status* st) {
 
 #define INST(T)                                                                                                   \
   template claire_status absmax_partial<T>(claire_ctx*, const T*, long long, double*, cudaStream_t);              \
+  template claire_status nonfinite_partial<T>(claire_ctx*, const T*, long long, const T*, long long, double*,    \
+                                              cudaStream_t);                                                     \
   template claire_status dot_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);       \
   template claire_status diffsq_partial<T>(claire_ctx*, const T*, const T*, long long, double*, cudaStream_t);    \
   template claire_status axpy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);                     \
@@ -259,8 +283,9 @@ extern "C" claire_status claire_dot_noalloc_f32(const float* a, const float* b, 
                                                 double* out, void* stream) {
   using namespace claire;
   if (!a || !b || !out || count < 0) return CLAIRE_EINVAL;
+  // the size check comes before any arithmetic on count, so that no count can overflow the block computation
+  if (count > (long long)kNoAllocBlocks * kNoAllocChunk) return CLAIRE_EINVAL;
   const long long blocks = (count + kNoAllocChunk - 1) / kNoAllocChunk;
-  if (blocks > kNoAllocBlocks) return CLAIRE_EINVAL;
   claire_status st = CLAIRE_OK;
   double* partials = noalloc_scratch_on_current_device(&st);
   if (st != CLAIRE_OK) return st;

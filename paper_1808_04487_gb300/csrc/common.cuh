@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <string>
 
 #include "claire.h"
@@ -104,6 +106,23 @@ struct RadixPlan {
 struct Counters {
   long long launches = 0;
 };
+
+// Host-side fault injection for tests of the failure paths: the environment variable CLAIRE_FAULT holds a
+// comma-separated list of fault names, and the host code that reads a device result consults it where a named
+// fault can be faked (the device work itself is unchanged; nothing faults, traps or hangs on the GPU).
+inline bool fault_injected(const char* name) {
+  const char* f = std::getenv("CLAIRE_FAULT");
+  if (!f || !*f) return false;
+  const size_t n = std::strlen(name);
+  for (const char* p = f; *p;) {
+    const char* e = std::strchr(p, ',');
+    const size_t len = e ? size_t(e - p) : std::strlen(p);
+    if (len == n && std::strncmp(p, name, n) == 0) return true;
+    if (!e) break;
+    p = e + 1;
+  }
+  return false;
+}
 
 }  // namespace claire
 

@@ -90,6 +90,8 @@ struct claire_ctx {
   claire::Work<float> wf{};
   claire::Work<double> wd{};
   bool lin_valid = false;
+  bool f64_plan = false;       // FP32 context with an FP64 FFT plan (stand-alone operators that apply a growing
+                               // symbol to a physical field transform it in FP64)
   bool gm16_on = false;        // gradient history stored in BF16 (claire_opts.bf16_mask bit 0)
   bool gm_ready = false;       // the gradient history holds finite values (used as autotuning input)
   int haloX = -1, haloY = -1;    // brick halo of the cached departure points (-1: plain gathers), light kernels
@@ -185,6 +187,12 @@ template <class T> claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp
                                             double beta, cudaStream_t st);
 // B = beta a(k) V + K^ B (K^ = I or Leray)
 template <class T> claire_status spec_combine(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st);
+// B = V + K^ B (V already multiplied by its symbol)
+template <class T> claire_status spec_addk(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st);
+// FP32 context, FP64 transform: fd = f as FP64, Sd = its half spectrum (FP64 plan), V = f(k) Sd rounded once to
+// FP32 with f = scale a(k) (mode 0) or -|k|^2 (mode 2). fd needs N doubles, Sd Ns complex doubles.
+claire_status symbol_r2c_f64(claire_ctx* c, const float* f, double* fd, cplx<double>* Sd, cplx<float>* V, int mode,
+                             double scale, cudaStream_t st);
 // partial sums of sum_c sum_{half k} w(k3) a(k) |V_c(k)|^2 into partials[kReduceBlocks]
 template <class T> claire_status spec_reg_partial(claire_ctx* c, const cplx<T>* V, double* partials, cudaStream_t st);
 
@@ -262,6 +270,9 @@ template <class T> claire_status dot_partial(claire_ctx* c, const T* a, const T*
 // partials[kReduceBlocks] of max |a_i| (as double)
 template <class T> claire_status absmax_partial(claire_ctx* c, const T* a, long long n, double* partials,
                                                 cudaStream_t st);
+// partials[kReduceBlocks] of the number of non-finite values in a[0..na) and b[0..nb)
+template <class T> claire_status nonfinite_partial(claire_ctx* c, const T* a, long long na, const T* b, long long nb,
+                                                   double* partials, cudaStream_t st);
 // out = max(partials[0..np))
 claire_status max_final(claire_ctx* c, const double* partials, int np, double* out, cudaStream_t st);
 // partials of sum (a - b)^2

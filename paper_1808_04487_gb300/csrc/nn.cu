@@ -647,6 +647,8 @@ cudaError_t status(cudaStream_t st) {
     cudaMemcpyToSymbol(g_nn_error, &zero, sizeof(int));
     return cudaErrorLaunchTimeout;
   }
+  // host-side fake of an expired wait (CLAIRE_FAULT=nn_timeout), for tests of the status path
+  if (fault_injected("nn_timeout")) return cudaErrorLaunchTimeout;
   return cudaSuccess;
 }
 
@@ -733,7 +735,10 @@ cudaError_t to_bf16(const float* a, bf16* b, long long count, cudaStream_t st) {
 using namespace claire::nn;
 
 namespace {
-inline claire_status st_of(cudaError_t e) { return e == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA; }
+// an expired bounded tensor-core wait (reported by nn::status as cudaErrorLaunchTimeout) is CLAIRE_ETIMEOUT
+inline claire_status st_of(cudaError_t e) {
+  return e == cudaSuccess ? CLAIRE_OK : (e == cudaErrorLaunchTimeout ? CLAIRE_ETIMEOUT : CLAIRE_ECUDA);
+}
 inline bool geo_args(int B, int n1, int n2, int n3) { return B > 0 && n1 > 0 && n2 > 0 && n3 > 0; }
 inline bool pool_args(int B, int n1, int n2, int n3) {
   return geo_args(B, n1, n2, n3) && n1 % 2 == 0 && n2 % 2 == 0 && n3 % 2 == 0;

@@ -84,8 +84,10 @@ template <class T> size_t work_bytes(const claire_opts& o, const Dims& d) {
   const long long celems = 6 * Ns + 8 * 3 * Ns;
   const Launch3 L = launch3(d);
   const long long nbig = (long long)L.grid.x * L.grid.y * L.grid.z;
+  // FP32 contexts also hold FP64 twiddle tables (stand-alone operators transform some inputs in FP64)
+  const size_t tables = fft_table_bytes<T>(d) + (sizeof(T) == 4 ? fft_table_bytes<double>(d) : 0);
   return sizeof(T) * size_t(elems) + sizeof(cplx<T>) * size_t(celems) +
-         sizeof(double) * size_t(nbig + 4 * kReduceBlocks + 32) + fft_table_bytes<T>(d) + 64 * 256;
+         sizeof(double) * size_t(nbig + 4 * kReduceBlocks + 32) + tables + 64 * 256;
 }
 
 // Read scal[slot] to the host (synchronises the stream).
@@ -156,6 +158,22 @@ template <class T> claire_status precond_apply(claire_ctx* c, const T* r, T* z, 
   return vec_c2r<T>(c, W.spec, z, st);
 }
 
+// S_k = f(k) F[x_k] for the three components of a physical FP32 field, with the transform in FP64 (f = scale a(k),
+// mode 0, or -|k|^2, mode 2). A symbol that grows with |k| multiplies the rounding error of an FP32 transform --
+// spread over all modes -- by up to its largest value (beta |k|^4 reaches 1e4 on a 40^3 grid at beta = 1e-2),
+// while the field itself may hold little at high k; the FP64 transform keeps that product at FP32 rounding. Uses
+// the trial-velocity array (N doubles) and the inverse-transform work array (Ns complex doubles) as scratch.
+claire_status symbol_vec_f64(claire_ctx* c, const float* x, cplx<float>* S, int ncomp, int mode, double scale,
+                             cudaStream_t st) {
+  Work<float>& W = c->work<float>();
+  double* fd = reinterpret_cast<double*>(W.vtrial);
+  cplx<double>* Sd = reinterpret_cast<cplx<double>*>(W.Sc);
+  for (int k = 0; k < ncomp; ++k)
+    CL_TRY(symbol_r2c_f64(c, x + (long long)k * c->d.N, fd, Sd, S + (long long)k * c->d.Ns, mode, scale, st));
+  return CLAIRE_OK;
+}
+template <class T> inline bool precise_symbols(const claire_ctx* c) { return sizeof(T) == 4 && c->f64_plan; }
+
 // out = beta A v + K b (the spectral tail of Eq. (5) and Eq. (7)); b is consumed
 template <class T> claire_status spectral_tail(claire_ctx* c, const T* v, const T* b, T* out, double* reg,
                                                cudaStream_t st) {
@@ -163,13 +181,21 @@ template <class T> claire_status spectral_tail(claire_ctx* c, const T* v, const 
   const long long Ns = c->d.Ns;
   cplx<T>* V = W.spec;
   cplx<T>* B = W.spec + 3 * Ns;
-  CL_TRY(vec_r2c<T>(c, v, V, st));
+  const bool precise = precise_symbols<T>(c);
+  if (!precise || reg) CL_TRY(vec_r2c<T>(c, v, V, st));
   if (reg) {
     // beta/2 sum_c <v_c, A v_c> by Parseval: h^3/N sum_k a(k) |v^(k)|^2
     CL_TRY(spec_reg_partial<T>(c, V, W.partials, st));
     CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(c->d.N), W.scal + 1, st));
   }
   CL_TRY(vec_r2c<T>(c, b, B, st));
+  if constexpr (sizeof(T) == 4) {
+    if (precise) {
+      CL_TRY(symbol_vec_f64(c, v, V, 3, 0, c->o.beta, st));
+      CL_TRY(spec_addk<T>(c, V, B, st));
+      return vec_c2r<T>(c, B, out, st);
+    }
+  }
   CL_TRY(spec_combine<T>(c, V, B, st));
   return vec_c2r<T>(c, B, out, st);
 }
@@ -669,10 +695,12 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
     return CLAIRE_ENAN;
   }
   CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
+  // host-side fake of a non-positive first <s, H s> (tests of the breakdown path; runs the host-driven loop)
+  const bool fake_breakdown = fault_injected("pcg_breakdown");
   // device-driven loop: spectral preconditioner, no per-kernel profiling (its events are per launch, not per
   // graph execution), unless CLAIRE_PCG=host
   const char* mode = std::getenv("CLAIRE_PCG");
-  if (!two && !c->prof_on && !c->pcg_graph_failed && !(mode && std::strcmp(mode, "host") == 0)) {
+  if (!two && !c->prof_on && !c->pcg_graph_failed && !fake_breakdown && !(mode && std::strcmp(mode, "host") == 0)) {
     bool ok = false;
     CL_TRY(pcg_graph_get<T>(c, &ok));
     if (!ok) {
@@ -715,7 +743,7 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
     rep->pde_solves += 2;
     double sBt;
     CL_TRY(read_scalars(c, W.scal + 4, 1, &sBt, st));
-    const double sHs = sAs + sBt;
+    const double sHs = (fake_breakdown && it == 0) ? -std::fabs(sAs + sBt) : sAs + sBt;
     if (!std::isfinite(sHs)) {
       c->set_error("non-finite <s, Hs>");
       return CLAIRE_ENAN;
@@ -766,9 +794,20 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
   CL_CUDA(c, cudaEventRecord(e0, st));
   claire_status status = CLAIRE_OK;
   do {
-    CL_TRY(diffsq_partial<T>(c, mT, mR, N, W.partials, st));
-    CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
-    CL_TRY(read_scalar(c, W.scal, &rep->mismatch0, st));
+    // non-finite inputs are rejected before anything else runs: counts of NaN/Inf in (m_T, m_R) and in v, and
+    // the initial mismatch sum, in one read
+    CL_TRY(nonfinite_partial<T>(c, mT, N, mR, N, W.partials, st));
+    CL_TRY(nonfinite_partial<T>(c, v, n3, (const T*)nullptr, 0, W.partials + kReduceBlocks, st));
+    CL_TRY(diffsq_partial<T>(c, mT, mR, N, W.partials + 2 * kReduceBlocks, st));
+    CL_TRY(reduce_final_v(c, W.partials, 3, kReduceBlocks, 1.0, W.scal + 13, st));
+    double in3[3];
+    CL_TRY(read_scalars(c, W.scal + 13, 3, in3, st));
+    if (in3[0] != 0.0 || in3[1] != 0.0) {
+      c->set_error(in3[0] != 0.0 ? "non-finite values in m_T or m_R" : "non-finite values in the initial v");
+      status = CLAIRE_ENAN;
+      break;
+    }
+    rep->mismatch0 = 0.5 * cellvol(c->d) * in3[2];
     // reference gradient at v = 0 (Sec. 2.3.2)
     double vv;
     CL_TRY(inner<T>(c, v, v, n3, &vv, st));
@@ -957,10 +996,22 @@ template <class T> claire_status spectral_dev(claire_ctx* c, int op, const T* in
     case 1: return div_spectral<T>(c, in, out, st);
     case 2: return leray_inplace<T>(c, in, out, st);
     case 3:
+      if constexpr (sizeof(T) == 4) {
+        if (precise_symbols<T>(c)) {
+          CL_TRY(symbol_vec_f64(c, in, S, 3, 0, 1.0, st));
+          return vec_c2r<T>(c, S, out, st);
+        }
+      }
       CL_TRY(vec_r2c<T>(c, in, S, st));
       CL_TRY(spec_scale<T>(c, S, 3, d.Ns, 0, 1.0, st));
       return vec_c2r<T>(c, S, out, st);
     case 4:
+      if constexpr (sizeof(T) == 4) {
+        if (precise_symbols<T>(c)) {
+          CL_TRY(symbol_vec_f64(c, in, S, 1, 2, 1.0, st));
+          return fft_c2r<T>(c, S, out, T(1.0 / double(d.N)), st);
+        }
+      }
       CL_TRY(fft_r2c<T>(c, in, S, st));
       CL_TRY(spec_scale<T>(c, S, 1, d.Ns, 2, 1.0, st));
       return fft_c2r<T>(c, S, out, T(1.0 / double(d.N)), st);
@@ -1008,6 +1059,52 @@ template <class T> claire_status api_gradient(claire_ctx* c, const T* mT, const 
   CHECK_PTR(c, g);
   CL_TRY(linearize<T>(c, mT, v, (cudaStream_t)s));
   return gradient_at_lin<T>(c, mR, v, g, J, (cudaStream_t)s);
+}
+// data term of the reduced gradient, K[int_0^1 lambda grad m dt] (Eq. (5) without beta A v); J optional
+template <class T> claire_status api_gradient_data(claire_ctx* c, const T* mT, const T* mR, const T* v, T* out,
+                                                   double* J, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, mT);
+  CHECK_PTR(c, mR);
+  CHECK_PTR(c, v);
+  CHECK_PTR(c, out);
+  cudaStream_t st = (cudaStream_t)s;
+  Work<T>& W = c->work<T>();
+  const long long N = c->d.N;
+  CL_TRY(linearize<T>(c, mT, v, st));
+  if (J) {
+    CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, mR, N, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(c->d), W.scal, st));
+    CL_TRY(vec_r2c<T>(c, v, W.spec, st));
+    CL_TRY(spec_reg_partial<T>(c, W.spec, W.partials, st));
+    CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(N), W.scal + 1, st));
+  }
+  CL_TRY(adjoint_integral<T>(c, mR, st));
+  CL_CUDA(c, cudaMemsetAsync(out, 0, sizeof(T) * 3 * N, st));
+  CL_TRY(add_projected_b<T>(c, out, out, st));
+  if (J) {
+    double r2[2];
+    CL_TRY(read_scalars(c, W.scal, 2, r2, st));
+    *J = r2[0] + r2[1];
+  }
+  return CLAIRE_OK;
+}
+// a diagonal Fourier symbol of the method on ncomp half spectra: 0 beta A, 1 M^-1, 2 K (ncomp = 3)
+template <class T> claire_status api_symbol(claire_ctx* c, int op, const T* in, T* out, int ncomp, void* s) {
+  CHECK_CTX(c, T);
+  CHECK_PTR(c, in);
+  CHECK_PTR(c, out);
+  if (op < 0 || op > 2 || ncomp < 1 || ncomp > 3 || (op == 2 && ncomp != 3)) {
+    c->set_error("claire_symbol: op must be 0, 1 or 2, 1 <= ncomp <= 3, and ncomp = 3 for K");
+    return CLAIRE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)s;
+  const long long Ns = c->d.Ns;
+  cplx<T>* V = reinterpret_cast<cplx<T>*>(out);
+  if ((const void*)in != (const void*)out)
+    CL_CUDA(c, cudaMemcpyAsync(out, in, sizeof(cplx<T>) * ncomp * Ns, cudaMemcpyDeviceToDevice, st));
+  if (op == 2) return spec_kop<T>(c, V, V + Ns, V + 2 * Ns, st);
+  return spec_scale<T>(c, V, ncomp, Ns, op == 0 ? 0 : 1, c->o.beta, st);
 }
 template <class T> claire_status api_linearize(claire_ctx* c, const T* mT, const T* v, void* s) {
   CHECK_CTX(c, T);
@@ -1258,6 +1355,12 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
     return CLAIRE_ENOMEM;
   }
   claire_status s = o.precision == CLAIRE_F32 ? fft_init<float>(c) : fft_init<double>(c);
+  if (s == CLAIRE_OK && o.precision == CLAIRE_F32) {
+    // an FP64 plan for the stand-alone operators; where the FP64 passes do not fit (very long axes), those
+    // operators transform in FP32 instead
+    c->f64_plan = fft_init<double>(c) == CLAIRE_OK;
+    if (!c->f64_plan) c->err.clear();
+  }
   if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? sl_init<float>(c) : sl_init<double>(c);
   if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? alloc_work<float>(c) : alloc_work<double>(c);
   if (s != CLAIRE_OK) {
@@ -1389,6 +1492,20 @@ claire_status claire_hessvec_data_f32(claire_ctx* c, const float* vt, float* out
 }
 claire_status claire_hessvec_data_f64(claire_ctx* c, const double* vt, double* out, void* s) {
   return api_hessvec_data<double>(c, vt, out, s);
+}
+claire_status claire_gradient_data_f32(claire_ctx* c, const float* mT, const float* mR, const float* v, float* out,
+                                       double* J, void* s) {
+  return api_gradient_data<float>(c, mT, mR, v, out, J, s);
+}
+claire_status claire_gradient_data_f64(claire_ctx* c, const double* mT, const double* mR, const double* v,
+                                       double* out, double* J, void* s) {
+  return api_gradient_data<double>(c, mT, mR, v, out, J, s);
+}
+claire_status claire_symbol_f32(claire_ctx* c, int op, const float* in, float* out, int ncomp, void* s) {
+  return api_symbol<float>(c, op, in, out, ncomp, s);
+}
+claire_status claire_symbol_f64(claire_ctx* c, int op, const double* in, double* out, int ncomp, void* s) {
+  return api_symbol<double>(c, op, in, out, ncomp, s);
 }
 claire_status claire_linearize_f32(claire_ctx* c, const float* mT, const float* v, void* s) {
   return api_linearize<float>(c, mT, v, s);

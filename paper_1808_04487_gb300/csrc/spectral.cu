@@ -202,6 +202,38 @@ __global__ void k_spec_combine(const cplx<T>* __restrict__ V, cplx<T>* __restric
   B[2 * s + idx] = mk<T>(f * v2.x + b2.x, f * v2.y + b2.y);
 }
 
+// B = V + K^ B (V already multiplied by its symbol)
+template <class T>
+__global__ void k_spec_addk(const cplx<T>* __restrict__ V, cplx<T>* __restrict__ B, int kmode, T rw, Dims d) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.Ns) return;
+  const Wave w = wavenumbers(idx, d);
+  const long long s = d.Ns;
+  cplx<T> b0 = B[idx], b1 = B[s + idx], b2 = B[2 * s + idx];
+  kop_apply<T>(kmode, rw, w, b0, b1, b2);
+  const cplx<T> v0 = V[idx], v1 = V[s + idx], v2 = V[2 * s + idx];
+  B[idx] = mk<T>(v0.x + b0.x, v0.y + b0.y);
+  B[s + idx] = mk<T>(v1.x + b1.x, v1.y + b1.y);
+  B[2 * s + idx] = mk<T>(v2.x + b2.x, v2.y + b2.y);
+}
+
+// V = f(k) S in FP64, rounded once to FP32: f = scale a(k) (mode 0) or -|k|^2 (mode 2)
+__global__ void k_symbol_f64_to_f32(const cplx<double>* __restrict__ S, cplx<float>* __restrict__ V, int mode,
+                                    int regnorm, double scale, Dims d) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.Ns) return;
+  const Wave w = wavenumbers(idx, d);
+  const double f = mode == 0 ? scale * reg_symbol<double>(w, regnorm)
+                             : -(double(w.k1) * w.k1 + double(w.k2) * w.k2 + double(w.k3) * w.k3);
+  const cplx<double> x = S[idx];
+  V[idx] = mk<float>(float(x.x * f), float(x.y * f));
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = double(x[i]);
+}
+
 // sum over the half spectrum with weight 1 on the k3 = 0 and k3 = n3/2 planes and 2 elsewhere (Parseval)
 template <class T>
 __global__ void __launch_bounds__(256) k_spec_reg_partial(const cplx<T>* __restrict__ V, int regnorm, int kmode,
@@ -694,6 +726,25 @@ claire_status spec_scale(claire_ctx* c, cplx<T>* V, int ncomp, long long cstride
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
+template <class T> claire_status spec_addk(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st) {
+  c->prof_begin("spec_addk", st);
+  k_spec_addk<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V, B, kmode_of(c), T(rw_of(c)), c->d);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
+claire_status symbol_r2c_f64(claire_ctx* c, const float* f, double* fd, cplx<double>* Sd, cplx<float>* V, int mode,
+                             double scale, cudaStream_t st) {
+  const long long n = c->d.N;
+  c->prof_begin("f32_to_f64", st);
+  const long long nb = (n + kThreads - 1) / kThreads;
+  k_f32_to_f64<<<(unsigned)(nb < 4864 ? nb : 4864), kThreads, 0, st>>>(f, fd, n);
+  CL_LAUNCHED(c);
+  CL_TRY(fft_r2c<double>(c, fd, Sd, st));
+  c->prof_begin("symbol_f64_to_f32", st);
+  k_symbol_f64_to_f32<<<blocks_for(c->d.Ns), kThreads, 0, st>>>(Sd, V, mode, c->o.regnorm, scale, c->d);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
 template <class T> claire_status spec_combine(claire_ctx* c, const cplx<T>* V, cplx<T>* B, cudaStream_t st) {
   c->prof_begin("spec_combine", st);
   k_spec_combine<T><<<blocks_for(c->d.Ns), kThreads, 0, st>>>(V, B, c->o.regnorm, kmode_of(c), T(rw_of(c)),
@@ -844,6 +895,7 @@ claire_status tl_dir(claire_ctx* c, const cplx<T>* Z, cplx<T>* S, double mu, dou
   template claire_status spec_kop<T>(claire_ctx*, cplx<T>*, cplx<T>*, cplx<T>*, cudaStream_t);                   \
   template claire_status spec_scale<T>(claire_ctx*, cplx<T>*, int, long long, int, double, cudaStream_t);        \
   template claire_status spec_combine<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cudaStream_t);                   \
+  template claire_status spec_addk<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cudaStream_t);                      \
   template claire_status spec_reg_partial<T>(claire_ctx*, const cplx<T>*, double*, cudaStream_t);                \
   template claire_status tl_restrict<T>(claire_ctx*, claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*,  \
                                         int, bool, double*, cudaStream_t);                                       \

@@ -140,7 +140,8 @@ struct claire_ws {
   claire_status cuda(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return CLAIRE_OK;
     err = std::string(what) + ": " + cudaGetErrorString(e);
-    return CLAIRE_ECUDA;
+    // nn::status reports an expired bounded tensor-core wait as cudaErrorLaunchTimeout
+    return e == cudaErrorLaunchTimeout ? CLAIRE_ETIMEOUT : CLAIRE_ECUDA;
   }
 };
 

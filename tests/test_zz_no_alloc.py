@@ -62,4 +62,8 @@ def test_noalloc_dot_rejects_sizes_beyond_its_static_scratch(L):
     st = L.claire_dot_noalloc_f32(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(a.data_ptr()), too_many, 1.0,
                                   ctypes.c_void_p(out.data_ptr()), None)
     assert st == 1  # CLAIRE_EINVAL, nothing launched
+    # the largest count: rejected before any arithmetic on it (no overflow into a small block count)
+    st = L.claire_dot_noalloc_f32(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(a.data_ptr()), 2 ** 63 - 1, 1.0,
+                                  ctypes.c_void_p(out.data_ptr()), None)
+    assert st == 1
     assert L.claire_dot_noalloc_f32(None, None, 4, 1.0, None, None) == 1
