@@ -6,9 +6,11 @@ itself warped by a band-limited divergence-free v* (|k| <= 6, max displacement 8
 beta = 1e-3, div v = 0 (Leray), n_t = 4, stop at ||g|| <= 1e-2 ||g(0)||, FP32 fields with FP64 reductions.
 The warped image m_R is made by this library's own transport of m_T along v*.
 
-Prints one JSON line (see the keys below). ``--impl reference`` times the FP64 CPU oracle instead (a bounded
-sample of the same workload, extrapolated by voxel count). Under torchrun each rank runs its own replica
-(no data-path collective); the timing is the max over ranks.
+Prints one JSON line (see the keys below). The headline is timed exactly as a user runs the solve (no per-kernel
+profiling; PCG as device-driven CUDA graphs); the per-kernel table and the roofline come from a separate pass with
+per-launch CUDA events. ``--impl reference`` times the FP64 CPU oracle instead (bounded per-operator samples,
+extrapolated to the grid by their measured growth and multiplied by the solve's operator counts). Under torchrun
+each rank runs its own replica (no data-path collective); the timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -40,11 +42,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the two-level preconditioner variant")
-    ap.add_argument("--study", default=None, choices=[None, "precision", "batch", "warmstart", "models"],
+    ap.add_argument("--large-check", type=int, default=256, help="large: grid of the BF16-vs-FP32 history check")
+    ap.add_argument("--study", default=None, choices=[None, "precision", "batch", "warmstart", "models", "large"],
                     help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path; batch: 64 "
                          "population-to-atlas pairs on uneven grids, batched vs sequential; warmstart: train the "
                          "warm-start network on solver outputs, then warm- vs zero-start solves; models: the H1-div "
-                         "model on the closed-form synthetic problem at several grids and continuation in beta "
+                         "model on the closed-form synthetic problem at several grids and continuation in beta; "
+                         "large: the synthetic problem at --size (e.g. 1024) with a BF16 gradient history "
                          "(own JSON lines)")
     ap.add_argument("--model-sizes", default="128,256,512", help="models: grids of the synthetic H1-div runs")
     ap.add_argument("--pairs", type=int, default=64)
@@ -120,7 +124,8 @@ def algorithmic_bytes(name, n, word=4):
 
 # the sources that define the semi-Lagrangian gather kernels (the dominant kernels of the bench): DRAM traffic
 # recorded in profiles/dram_traffic.txt is valid only for the digest of these files it was taken with
-GATHER_SOURCES = ("common.cuh", "sl_kernels.cuh", "sl.cu", "sl_h2.cu", "sl_h3.cu", "sl_h4.cu", "sl_h5.cu")
+GATHER_SOURCES = ("common.cuh", "sl_kernels.cuh", "sl.cu", "sl_h2.cu", "sl_h3.cu", "sl_h4.cu", "sl_h5.cu", "sl_tma.cu",
+                  "tma.cuh")
 
 
 def source_digest():
@@ -150,6 +155,29 @@ def traffic_from_profiles(kernel, n):
         return None
     b = rows.get((kernel, n[0]))
     return b
+
+
+def l1_from_profiles(kernel):
+    """L1 data-pipe wavefronts per grid node of a kernel (ncu l1tex__data_pipe_lsu_wavefronts.sum of one launch
+    divided by its node count) and the pipe-utilisation figures of that capture, from a committed summary taken on
+    the current kernel sources; None otherwise."""
+    p = os.path.join(PROFILES, "l1_wavefronts.txt")
+    if not os.path.exists(p):
+        return None
+    digest, rows = None, {}
+    for line in open(p):
+        line = line.strip()
+        if line.startswith("# source_digest:"):
+            digest = line.split(":", 1)[1].strip()
+        elif line and not line.startswith("#"):
+            parts = line.split()
+            if len(parts) >= 6:
+                rows[parts[0]] = {"n": int(parts[1]), "wavefronts_per_node": float(parts[2]),
+                                  "shared_taps_per_node": float(parts[3]), "l1_pct_of_peak": float(parts[4]),
+                                  "fma_pipe_pct": float(parts[5])}
+    if digest != source_digest():
+        return None
+    return rows.get(kernel)
 
 
 class ClockSampler:
@@ -221,52 +249,192 @@ def whole_job_seconds_per_registration(ms_max, steps, world):
     return ms_max / 1e3 / (steps * world)
 
 
-def cpu_baseline(n_target, seconds_budget=30.0):
-    """Oracle (FP64 numpy, as it stands) on a bounded sample: the same problem family at 32^3, extrapolated to the
-    target grid by voxel count (the solver's work per iteration is linear in N up to the FFT's log factor, and
-    PCG/GN counts are nearly mesh independent, Sec. 4.3)."""
+# Operator counts of one solve of the bench workload at 256^3 (FP32, 6 GN steps). The FP64 solve of the same
+# workload takes the same counts (precision study), and the FP64 parity tests show the GPU's FP64 counts equal to
+# the oracle's; the reference arm, which must not run the GPU, uses these for its extrapolation.
+REF_COUNTS_256 = {"gn_iters": 6, "matvecs": 67, "ls_trials": 6}
+
+
+def host_cpu():
+    """CPU model and core counts of this host (the oracle runs single-threaded: numpy, no BLAS)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except Exception:
+        avail = os.cpu_count()
+    return {"model": model, "nproc": os.cpu_count(), "available": avail}
+
+
+class pinned_to_one_core:
+    """Runs the enclosed code with the process's CPU affinity set to a single core (restored on exit)."""
+
+    def __enter__(self):
+        self.old = None
+        try:
+            self.old = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, {min(self.old)})
+        except Exception:
+            self.old = None
+        return self
+
+    def __exit__(self, *a):
+        if self.old is not None:
+            os.sched_setaffinity(0, self.old)
+
+
+def oracle_operator_seconds(n):
+    """Wall time of each oracle operator (FP64 numpy, as it stands) on grid n for the bench's problem family
+    (phantom, div-free v* of 8 voxels at 256^3 scaled to n, H2, beta 1e-3, div v = 0, n_t 4), at v = v*/2:
+    transport = one state solve (departure points + n_t gathers, what an Armijo trial costs), gradient = the
+    linearisation (both departure points, state history, its spectral gradients) + adjoint + spectral tail,
+    matvec = one Gauss-Newton matvec at that linearisation, precond = one application of (beta A)^-1."""
     import numpy as np
 
     import claire_inputs as I
     from oracle import claire_oracle as O
 
-    ns = (32, 32, 32)
+    p = O.Problem(n, beta=1e-3, nt=4, regnorm=2, divfree=True, gtol_rel=1e-2)
+    mT = I.brain_phantom(n, seed=0)
+    vs = I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=8.0 * max(n) / 256.0, divfree=True)
+    mR = O.transport(p, mT, vs, +1)
+    v = 0.5 * vs
+    vt = O.leray(p.grid, np.random.default_rng(3).normal(size=(3,) + tuple(n)))
+    t = {}
+    a = time.perf_counter()
+    O.transport(p, mT, v, +1)
+    t["transport"] = time.perf_counter() - a
+    a = time.perf_counter()
+    lin = O.linearize(p, mT, v)
+    g = O.reduced_gradient(p, lin, mR)
+    t["gradient"] = time.perf_counter() - a
+    a = time.perf_counter()
+    O.hessvec(p, lin, vt)
+    t["matvec"] = time.perf_counter() - a
+    a = time.perf_counter()
+    O.precond(p.grid, g, p.beta, p.regnorm)
+    t["precond"] = time.perf_counter() - a
+    return t
+
+
+def oracle_solve_estimate(per_op, counts):
+    """Seconds of the oracle's Alg. 1 with the given operator counts: (GN + 1) gradients (the first at v = 0),
+    the matvecs, one preconditioner application per matvec plus one per PCG solve, one transport per Armijo
+    trial -- the operators the oracle's register() calls, in those numbers."""
+    g, m, ls = counts["gn_iters"], counts["matvecs"], counts["ls_trials"]
+    return ((g + 1) * per_op["gradient"] + m * per_op["matvec"] + (m + g) * per_op["precond"] +
+            ls * per_op["transport"])
+
+
+def extrapolate(small, large, n_small, n_large, n_target):
+    """Per-operator seconds at n_target from two measured grids: t = t_large (N/N_large)^e with the growth
+    exponent e = log(t_large/t_small) / log(N_large/N_small) measured on the two grids (it carries the FFT's
+    log factor and the gathers' cache behaviour as they are on this host)."""
+    N = lambda n: float(n[0] * n[1] * n[2])
+    out, expo = {}, {}
+    for k in large:
+        e = math.log(max(large[k], 1e-9) / max(small[k], 1e-9)) / math.log(N(n_large) / N(n_small))
+        e = min(max(e, 1.0), 1.5)  # between linear and N^1.5 (guards a noisy timing of a tiny operator)
+        expo[k] = e
+        out[k] = large[k] * (N(n_target) / N(n_large)) ** e
+    return out, expo
+
+
+def cpu_baseline(n_target, counts, sizes=((32, 32, 32), (64, 64, 64))):
+    """Bounded sample of the oracle on this host (about 20 s): each operator timed on two grids of the bench's
+    problem family, on one core and on all available cores, extrapolated to n_target by its measured growth and
+    multiplied by the operator counts of the GPU solve; plus one measured full oracle solve at the smaller grid."""
+    import claire_inputs as I
+    from oracle import claire_oracle as O
+
+    cpu = host_cpu()
+    res = {}
+    for mode in ("one_core", "all_cores"):
+        if mode == "one_core":
+            with pinned_to_one_core():
+                small, large = oracle_operator_seconds(sizes[0]), oracle_operator_seconds(sizes[1])
+        else:
+            small, large = oracle_operator_seconds(sizes[0]), oracle_operator_seconds(sizes[1])
+        est, expo = extrapolate(small, large, sizes[0], sizes[1], n_target)
+        res[mode] = {"seconds": oracle_solve_estimate(est, counts), "per_op_target_s": est, "growth_exponent": expo,
+                     "per_op_measured_s": {"%d^3" % sizes[0][0]: small, "%d^3" % sizes[1][0]: large}}
+    # one measured full solve at the smaller grid (same family), on one core
+    ns = sizes[0]
     p = O.Problem(ns, beta=1e-3, nt=4, regnorm=2, divfree=True, gtol_rel=1e-2)
     mT = I.brain_phantom(ns, seed=0)
-    vs = I.random_velocity(ns, seed=1, kmax=6, max_disp_voxels=8.0 * 32 / 256.0, divfree=True)
+    vs = I.random_velocity(ns, seed=1, kmax=6, max_disp_voxels=8.0 * ns[0] / 256.0, divfree=True)
     mR = O.transport(p, mT, vs, +1)
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        v, rep = O.register(p, mT, mR)
-        reps += 1
-        if time.perf_counter() - t0 > seconds_budget / 3 or reps >= 3:
-            break
-    dt = (time.perf_counter() - t0) / reps
-    scale = float(np.prod(n_target)) / float(np.prod(ns))
-    return {"value": dt * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": "oracle register at 32^3 of the same phantom family (same physical v*, H2 beta=1e-3, "
-                      "div-free, nt=4, rel-grad 1e-2): %.2f s/solve x %d runs, %d GN / %d matvecs, scaled by "
-                      "voxel count x%d to %s" % (dt, reps, rep.gn_iters, rep.matvecs, int(scale), list(n_target))}
+    with pinned_to_one_core():
+        a = time.perf_counter()
+        _, rep = O.register(p, mT, mR)
+        full = time.perf_counter() - a
+    one = res["one_core"]
+    return {"value": one["seconds"], "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "oracle operators (transport, gradient, GN matvec, preconditioner) timed at %s and %s on one "
+                      "pinned core, extrapolated to %s by each operator's measured growth, times the GPU solve's "
+                      "counts (%d GN, %d matvecs, %d Armijo trials); extrapolated, not a measured %s solve"
+                      % ("%d^3" % sizes[0][0], "%d^3" % sizes[1][0], "x".join(map(str, n_target)),
+                         counts["gn_iters"], counts["matvecs"], counts["ls_trials"], "x".join(map(str, n_target))),
+            "all_cores_value": res["all_cores"]["seconds"],
+            "all_cores_note": "the oracle is single-threaded numpy, so all available cores give the one-core time",
+            "host": cpu, "counts": counts, "details": res,
+            "measured_full_solve": {"n": list(ns), "seconds": full, "gn_iters": rep.gn_iters,
+                                    "matvecs": rep.matvecs, "cores": 1}}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle (the paper ships no code to install). Each step is a bounded sample
+    of the workload -- the oracle's operators timed at 48^3 on one pinned core -- extrapolated to the bench's grid
+    with growth exponents measured once during the warm-up (32^3 and 64^3) and the operator counts REF_COUNTS_256.
+    value = the extrapolated seconds per 256^3 registration; ms_per_step = the measured wall time of one sample."""
     if rank != 0:
         return 0
     n = (args.size,) * 3
-    vals = []
-    for _ in range(args.warmup):
-        pass
-    samples = []
-    for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(n, seconds_budget=20.0)
-        samples.append(cb["value"])
-    val = sorted(samples)[len(samples) // 2]
-    cb["value"] = val
+    counts = dict(REF_COUNTS_256)
+    with pinned_to_one_core():
+        small, large = oracle_operator_seconds((32, 32, 32)), oracle_operator_seconds((64, 64, 64))
+        _, expo = extrapolate(small, large, (32, 32, 32), (64, 64, 64), n)
+        for _ in range(max(0, args.warmup - 1)):
+            oracle_operator_seconds((48, 48, 48))
+        vals, walls = [], []
+        t_all = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            a = time.perf_counter()
+            t48 = oracle_operator_seconds((48, 48, 48))
+            walls.append(time.perf_counter() - a)
+            est = {k: t48[k] * (float(n[0] * n[1] * n[2]) / 48.0 ** 3) ** expo[k] for k in t48}
+            vals.append(oracle_solve_estimate(est, counts))
+        total = time.perf_counter() - t_all
+    vals.sort()
+    val = vals[len(vals) // 2]
+    cfg = workload(n)
+    cfg["precision"] = "fp64 (the CPU oracle)"
+    cb = {"value": val, "unit": "s", "cores": 1, "kind": "oracle", "host": host_cpu(),
+          "sample": "per step: oracle transport, gradient, GN matvec and preconditioner at 48^3 on one pinned core, "
+                    "extrapolated to %s with growth exponents %s (32^3 -> 64^3), times %s; extrapolated"
+                    % ("x".join(map(str, n)), {k: round(e, 3) for k, e in expo.items()}, counts)}
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(n),
-            "cpu_baseline": cb, "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, args.steps),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "value is the extrapolated seconds of one oracle solve of the workload; ms_per_step is the "
+                    "measured wall time of one bounded sample"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -362,7 +530,8 @@ def batch_study(args):
     """Population-to-atlas batch: pairs with grids drawn uniformly (seeded) from BATCH_GRIDS; per grid one atlas
     phantom m_R, per pair a template m_T = the atlas warped by its own band-limited v* (|k| <= 5, same physical
     amplitude as 8 voxels at 256^3); H1, beta = 5e-3, n_t = 4, FP32 with FP64 reductions, to ||g|| <= 5e-2 ||g0||.
-    Times the batched call (concurrent workers) against the same pairs solved one after another."""
+    Times the batched call (every solve driven from the device; each context's share of a grid class in one CUDA
+    graph launch) against the same pairs solved one after another through the single-pair call."""
     import numpy as np
     import torch
 
@@ -386,22 +555,57 @@ def batch_study(args):
         pairs.append((mT, atlases[n], torch.zeros((3,) + n, dtype=torch.float32, device=dev)))
     voxels = float(sum(np.prod(p[0].shape) for p in pairs))
     res = {}
-    for nw in (1, 4, 8):
-        for _, _, v in pairs:
-            v.zero_()
-        pkg.register_batch(pairs[: min(4, len(pairs))], nworkers=nw, **kw)  # warm-up (contexts, autotuner)
-        for _, _, v in pairs:
-            v.zero_()
+
+    def timed(fn):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = pkg.register_batch(pairs, nworkers=nw, **kw)
+        out = fn()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        res["workers_%d" % nw] = {"seconds": dt, "pairs_per_s": len(pairs) / dt,
-                                  "converged": sum(1 for r, st in out if r["converged"]),
-                                  "matvecs": sum(r["matvecs"] for r, st in out)}
-    res["speedup_batched_vs_sequential"] = res["workers_1"]["seconds"] / min(
-        res["workers_4"]["seconds"], res["workers_8"]["seconds"])
+        return out, time.perf_counter() - t0
+
+    # sequential: one pair after another through the single-pair call (host-driven Gauss-Newton loop, one context
+    # per grid, created and warmed up before the timed region)
+    ctxs = {}
+    for mT, mR, v in pairs:
+        n = tuple(mT.shape)
+        if n not in ctxs:
+            ctxs[n] = pkg.Context(n, precision="f32", **kw)
+            ctxs[n].register(mT, mR)
+
+    def sequential():
+        out = []
+        for mT, mR, v in pairs:
+            v.zero_()
+            _, rep, st = ctxs[tuple(mT.shape)].register(mT, mR, v)
+            out.append((rep, st))
+        return out
+
+    seq_out, t_seq = timed(sequential)
+    v_seq = [p[2].clone() for p in pairs]
+    for c in ctxs.values():
+        c.close()
+    res["sequential"] = {"seconds": t_seq, "pairs_per_s": len(pairs) / t_seq,
+                         "matvecs": sum(r["matvecs"] for r, _ in seq_out)}
+    # batched: every pair's solve driven from the device, each context's share of a grid class in one graph launch
+    for nw in (1, 2, 4):
+        pkg.register_batch(pairs[: min(8, len(pairs))], nworkers=nw, **kw)  # warm-up (autotuner, module load)
+        for _, _, v in pairs:
+            v.zero_()
+        out, dt = timed(lambda: pkg.register_batch(pairs, nworkers=nw, **kw))
+        same = all(torch.equal(p[2], vs) for p, vs in zip(pairs, v_seq))
+        res["device_graph_contexts_per_grid_%d" % nw] = {
+            "seconds": dt, "pairs_per_s": len(pairs) / dt, "converged": sum(1 for r, st in out if r["converged"]),
+            "matvecs": sum(r["matvecs"] for r, st in out), "bit_identical_to_sequential": bool(same)}
+    # the earlier batched form for comparison: host worker threads, host-driven Gauss-Newton loops
+    os.environ["CLAIRE_GN"] = "host"
+    pkg.register_batch(pairs[: min(8, len(pairs))], nworkers=4, **kw)
+    for _, _, v in pairs:
+        v.zero_()
+    out, dt = timed(lambda: pkg.register_batch(pairs, nworkers=4, **kw))
+    del os.environ["CLAIRE_GN"]
+    res["host_worker_threads_4"] = {"seconds": dt, "pairs_per_s": len(pairs) / dt}
+    best = min(res[k]["seconds"] for k in res if k.startswith("device_graph"))
+    res["speedup_device_batch_vs_sequential"] = t_seq / best
     print(json.dumps({"study": "batch", "pairs": len(pairs), "grids": [list(g) for g in BATCH_GRIDS],
                       "grid_counts": {str(list(BATCH_GRIDS[k])): int((choice == k).sum()) for k in range(len(BATCH_GRIDS))},
                       "total_voxels": voxels, "solver": kw, "results": res}), flush=True)
@@ -656,6 +860,95 @@ def models_study(args):
     return 0
 
 
+def paper_synthetic_on_device(n, dev):
+    """The closed-form problem of Sec. 4.2 (claire_inputs.paper_synthetic) composed on the GPU from its 1D factors
+    in FP64 and stored in FP32: m_T = (sin^2 x1 + sin^2 x2 + sin^2 x3) / 3, v*_1 = sin x3 cos x2 sin x2,
+    v*_2 = sin x1 cos x3 sin x3, v*_3 = sin x2 cos x1 sin x1 (the host arrays would take ~50 GB at 1024^3)."""
+    import torch
+
+    import claire_inputs as I
+    x = [torch.from_numpy(a).to(dev) for a in I.grid_coords(n)]
+    s = [torch.sin(a) for a in x]
+    c = [torch.cos(a) for a in x]
+    b1 = lambda a: a[:, None, None]
+    b2 = lambda a: a[None, :, None]
+    b3 = lambda a: a[None, None, :]
+    mT = ((b1(s[0]) ** 2 + b2(s[1]) ** 2 + b3(s[2]) ** 2) / 3.0).float()
+    v = torch.empty((3,) + tuple(n), dtype=torch.float32, device=dev)
+    v[0] = (b3(s[2]) * (b2(c[1]) * b2(s[1]))).expand(n).float()
+    v[1] = (b1(s[0]) * (b3(c[2]) * b3(s[2]))).expand(n).float()
+    v[2] = (b2(s[1]) * (b1(c[0]) * b1(s[0]))).expand(n).float()
+    return mT.contiguous(), v
+
+
+def large_study(args):
+    """Large single-GPU grids (Tab. 4, Sec. 4.7): the H1-div synthetic problem of Sec. 4.2 (beta_v 1e-3, beta_w
+    1e-4, H1, spectral preconditioner, FP32 fields, to ||g|| <= 1e-2 ||g(0)||) at --size (default 1024^3) with the
+    gradient history of the state stored in BF16 (bf16_mask = 1), which with the lean workspace layout lets the
+    1024^3 problem fit in HBM. Reports time, GN/matvec/PDE counts and the device memory in use; at --large-check
+    (default 256) the same problem is also solved with and without BF16 storage to state the error this adds."""
+    import torch
+
+    import paper_1808_04487_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+
+    def log(msg):
+        print(msg, file=sys.stderr, flush=True)
+
+    kw = dict(beta=1e-3, nt=4, regnorm=1, beta_w=1e-4, gtol_rel=1e-2)
+    keys = ("gn_iters", "matvecs", "pde_solves", "ls_trials", "converged")
+    out = {"study": "large", "solver": kw, "runs": []}
+    chk = int(args.large_check)
+    if chk > 0:
+        n = (chk,) * 3
+        mT, vs = paper_synthetic_on_device(n, dev)
+        res = {}
+        for mask in (0, 1):
+            c = pkg.Context(n, precision="f32", bf16_mask=mask, **kw)
+            mR = c.transport(mT, vs, +1)
+            v, r, st = c.register(mT, mR)
+            res[mask] = (v, r, st)
+            c.close()
+        out["bf16_check"] = {"n": list(n), "v_rel_diff": float((res[1][0] - res[0][0]).norm() / res[0][0].norm()),
+                             "gn_fp32": res[0][1]["gn_iters"], "gn_bf16": res[1][1]["gn_iters"],
+                             "matvecs_fp32": res[0][1]["matvecs"], "matvecs_bf16": res[1][1]["matvecs"],
+                             "rel_mismatch_fp32": res[0][1]["mismatch_rel"],
+                             "rel_mismatch_bf16": res[1][1]["mismatch_rel"]}
+        log("bf16 check %s: %s" % (n, out["bf16_check"]))
+        del mT, vs, mR, v, res
+        torch.cuda.empty_cache()
+    n = (args.size,) * 3
+    mT, v = paper_synthetic_on_device(n, dev)
+    torch.cuda.empty_cache()  # return the FP64 temporaries of the composition before the workspace is allocated
+    free0, total = torch.cuda.mem_get_info()
+    ctx = pkg.Context(n, precision="f32", bf16_mask=1, **kw)
+    mR = ctx.transport(mT, v, +1)
+    free1, _ = torch.cuda.mem_get_info()
+    runs = []
+    for it in range(max(1, args.steps) + 1):  # the first solve also runs the gather autotuner
+        v.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        _, rep, st = ctx.register(mT, mR, v)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - a
+        runs.append(dt)
+        log("%s solve %d: %.2f s, %d GN, %d matvecs, status %s" % (n, it, dt, rep["gn_iters"], rep["matvecs"], st))
+    out["runs"].append({"n": list(n), "seconds": min(runs[1:]) if len(runs) > 1 else runs[0], "status": st,
+                        **{k: rep[k] for k in keys}, "rel_mismatch": rep["mismatch_rel"],
+                        "rel_grad": rep["gnorm_rel"], "bf16_gradient_history": True,
+                        "workspace_gb": ctx.workspace_bytes() / 1e9,
+                        "device_used_gb": (total - free1) / 1e9, "device_total_gb": total / 1e9,
+                        "caller_arrays_gb": 5 * mT.numel() * 4 / 1e9,
+                        "note": "Tab. 4 (Sec. 4.7) context: the paper's 1024^3 run took 136.8 s on 256 and 15.5 s on "
+                                "4096 MPI tasks (two-level preconditioner, CPU cluster)"})
+    ctx.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.study == "precision":
@@ -666,6 +959,8 @@ def main():
         return warmstart_study(args)
     if args.study == "models":
         return models_study(args)
+    if args.study == "large":
+        return large_study(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -701,12 +996,12 @@ def main():
         solve()
     torch.cuda.synchronize()
 
-    # ---- timed region
+    # ---- timed region: the solves exactly as a user runs them (no per-kernel profiling; each PCG solve is one
+    # device-driven CUDA graph launch)
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ctx.launches()
-    ctx.profile(True)
-    ctx.profile_report()  # clear
+    graphs0 = ctx.pcg_graph_runs()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -722,35 +1017,59 @@ def main():
     if dist is not None:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    prof = ctx.profile_report()
-    ctx.profile(False)
     launches = ctx.launches() - launches0
+    pcg_graphs = ctx.pcg_graph_runs() - graphs0
     gather = ctx.gather_schedule()
     clk = clocks.stop()
     ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
     value = whole_job_seconds_per_registration(ms, args.steps, world)  # whole job: N replicas in parallel
 
-    # ---- Hessian matvecs/s at the converged linearisation (full matvec incl. beta A through its symbol)
+    # ---- per-kernel pass, timed separately: every launch bracketed by CUDA events on its stream (this forces the
+    # host-driven PCG loop; the kernels are the same)
+    prof_steps = max(1, min(args.steps, 2))
+    ctx.profile(True)
+    ctx.profile_report()  # clear
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(prof_steps):
+        solve()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1) / prof_steps
+    prof = ctx.profile_report()
+    ctx.profile(False)
+
+    # ---- Hessian matvecs/s at the converged linearisation. The solver's matvec is the data term H_data s (the
+    # incremental state and adjoint solves with K and the transforms, claire_hessvec_data) -- beta A s is a
+    # diagonal multiply on its Fourier-domain vectors; the stand-alone full matvec (beta A applied to a physical
+    # field through an FP64 transform) is timed beside it.
     ctx.linearize(mT, v)
     vt = torch.randn((3,) + n, dtype=torch.float32, device=dev, generator=torch.Generator(dev).manual_seed(0))
     vt = ctx.spectral("leray", vt)
     Hv = torch.empty_like(vt)
-    for _ in range(3):
-        ctx.hessvec_cached(vt, Hv)
-    times = []
-    for _ in range(20):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.hessvec_cached(vt, Hv)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    times.sort()
-    matvec_ms = times[len(times) // 2]
 
-    # ---- roofline of the dominant kernel (live CUDA-event durations over the timed region)
+    def median_ms(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    matvec_ms = median_ms(lambda: ctx.hessvec_data(vt, Hv))
+    matvec_full_ms = median_ms(lambda: ctx.hessvec_cached(vt, Hv))
+
+    # ---- roofline of the dominant kernel (live CUDA-event durations of the per-kernel pass)
     peak, peak_kind = read_peaks()
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     total_kernel_ms = sum(x[1] for x in prof.values()) if prof else 0.0
@@ -761,8 +1080,20 @@ def main():
         byt = algorithmic_bytes(name, n)
         achieved = byt / (avg_ms * 1e-3) / 1e9 if byt else None
         tr = traffic_from_profiles(name, n)
+        l1 = l1_from_profiles(name)
+        l1_line = None
+        if l1 is not None and clk.get("sm_mhz"):
+            # live: the captured wavefronts per node x this grid's nodes over the live launch time, against one
+            # wavefront per cycle per SM (the L1 data pipe) on 152 SMs at the sampled SM clock
+            nodes = n[0] * n[1] * n[2]
+            peak_wf = 152 * clk["sm_mhz"] * 1e6 * avg_ms * 1e-3
+            l1_line = {"bound": "L1 data pipe (LSU wavefronts)", "wavefronts_per_node": l1["wavefronts_per_node"],
+                       "shared_taps_per_node": l1["shared_taps_per_node"], "tap_minimum_per_node": 2.0,
+                       "frac": l1["wavefronts_per_node"] * nodes / peak_wf,
+                       "captured_at": l1["n"], "captured_l1_pct_of_peak": l1["l1_pct_of_peak"],
+                       "captured_fma_pipe_pct": l1["fma_pipe_pct"], "source": "profiles/l1_wavefronts.txt"}
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": tr,
+                "frac": (achieved / peak) if achieved else None, "traffic": tr, "l1": l1_line,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6800 GB/s",
                 "algorithmic_bytes_per_launch": byt, "avg_launch_ms": avg_ms, "launches": cnt,
@@ -822,7 +1153,7 @@ def main():
     rep, status = reps[-1]
     cb = None
     if not args.no_cpu_baseline and world == 1:
-        cb = cpu_baseline(n)
+        cb = cpu_baseline(n, {k: rep[k] for k in ("gn_iters", "matvecs", "ls_trials")})
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -831,7 +1162,12 @@ def main():
                   "pde_solves": rep["pde_solves"], "ls_trials": rep["ls_trials"], "gnorm_rel": rep["gnorm_rel"],
                   "mismatch_rel": rep["mismatch_rel"]},
         "hessian_matvecs_per_s": 1e3 / matvec_ms, "hessian_matvec_ms": matvec_ms,
-        "roofline": roof, "kernels": kernels, "gather_schedule": gather, "clocks": clk, "gpu_launches": launches,
+        "hessian_matvec_note": "claire_hessvec_data (H_data s: incremental state + adjoint solves, K, transforms; "
+                               "beta A s is diagonal on the solver's Fourier-domain vectors)",
+        "hessian_matvec_full_api_ms": matvec_full_ms,
+        "roofline": roof, "kernels": kernels, "kernel_pass": {"solves": prof_steps, "ms_per_solve": prof_ms,
+                                                              "note": "separate pass with per-launch CUDA events"},
+        "gather_schedule": gather, "clocks": clk, "gpu_launches": launches, "pcg_graph_launches": pcg_graphs,
         "e2e": e2e,
         "cpu_baseline": cb, "variants": variants,
     }

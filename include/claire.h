@@ -200,7 +200,9 @@ claire_status claire_register_f32(claire_ctx* ctx, const float* mT, const float*
 claire_status claire_register_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
                                   claire_report* rep, void* stream);
 /* Same solve with HOST arrays (pageable or pinned): mT, mR and v are copied to the context's device buffers on
- * stream, the solve runs, and v is copied back before the call returns. */
+ * stream, the solve runs, and v is copied back before the call returns. The first host-array call on a context
+ * allocates those device buffers (5 N values, kept until claire_destroy; CLAIRE_ENOMEM if that fails), so the
+ * workspace of a context that only takes device arrays stays smaller. */
 claire_status claire_register_host_f32(claire_ctx* ctx, const float* mT, const float* mR, float* v,
                                        claire_report* rep, void* stream);
 claire_status claire_register_host_f64(claire_ctx* ctx, const double* mT, const double* mR, double* v,
@@ -296,6 +298,11 @@ typedef struct {
     int halo_x, halo_y;
     int halo_x_heavy, halo_y_heavy;
     long long pcg_graph_runs; /* PCG solves (Alg. 2) run as one CUDA-graph launch, the loop driven on the device */
+    long long gn_graph_runs;  /* launches of the graph of the whole solve driven from the device (batched calls, or
+                                 CLAIRE_GN=device for single zero-start solves) */
+    long long tma_steps;      /* accumulating adjoint steps whose streamed operands (Y, grad m^j, b) were staged
+                                 in shared memory by TMA (FP32, brick-tiled schedule, n3 a multiple of 16; the
+                                 environment variable CLAIRE_TMA=0 turns this off) */
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 

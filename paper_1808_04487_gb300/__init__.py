@@ -58,7 +58,8 @@ class PairF32(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("halo_x", ctypes.c_int), ("halo_y", ctypes.c_int),
-                ("halo_x_heavy", ctypes.c_int), ("halo_y_heavy", ctypes.c_int), ("pcg_graph_runs", ctypes.c_longlong)]
+                ("halo_x_heavy", ctypes.c_int), ("halo_y_heavy", ctypes.c_int), ("pcg_graph_runs", ctypes.c_longlong),
+                ("gn_graph_runs", ctypes.c_longlong), ("tma_steps", ctypes.c_longlong)]
 
 
 _VP = ctypes.c_void_p
@@ -458,6 +459,18 @@ class Context:
         c = Counters()
         lib().claire_get_counters(self._h, ctypes.byref(c))
         return int(c.pcg_graph_runs)
+
+    def gn_graph_runs(self):
+        """Launches of the graph of the whole solve driven from the device on this context."""
+        c = Counters()
+        lib().claire_get_counters(self._h, ctypes.byref(c))
+        return int(c.gn_graph_runs)
+
+    def tma_steps(self):
+        """Adjoint steps run with TMA-staged operands on this context."""
+        c = Counters()
+        lib().claire_get_counters(self._h, ctypes.byref(c))
+        return int(c.tma_steps)
 
     def gather_schedule(self):
         """{"halo_x", "halo_y", "halo_x_heavy", "halo_y_heavy"}: brick halos of the tiled gathers of the cached

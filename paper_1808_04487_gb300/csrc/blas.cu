@@ -127,6 +127,11 @@ __global__ void k_scale_copy(long long n, T a, const T* __restrict__ x, T* __res
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i];
 }
+// y = 0 over n words of 4 or 8 bytes (T = float or double; complex arrays pass twice their length)
+template <class T> __global__ void k_zero(long long n, T* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = T(0);
+}
 static inline unsigned stream_blocks(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   return (unsigned)(b < 8 * 152 * 4 ? b : 8 * 152 * 4);
@@ -224,6 +229,12 @@ claire_status waxpy(claire_ctx* c, long long n, const T* x, double a, const T* y
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
+template <class T> claire_status zero_fill(claire_ctx* c, long long n, T* y, cudaStream_t st) {
+  c->prof_begin("zero", st);
+  k_zero<T><<<stream_blocks(n), kThreads, 0, st>>>(n, y);
+  CL_LAUNCHED(c);
+  return CLAIRE_OK;
+}
 template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st) {
   c->prof_begin("scale_copy", st);
   k_scale_copy<T><<<stream_blocks(n), kThreads, 0, st>>>(n, T(a), x, y);
@@ -272,7 +283,8 @@ static double* noalloc_scratch_on_current_device(claire_status* st) {
   template claire_status axpy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);                     \
   template claire_status xpay<T>(claire_ctx*, long long, const T*, double, T*, cudaStream_t);                     \
   template claire_status waxpy<T>(claire_ctx*, long long, const T*, double, const T*, T*, cudaStream_t);          \
-  template claire_status scale_copy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);
+  template claire_status scale_copy<T>(claire_ctx*, long long, double, const T*, T*, cudaStream_t);              \
+  template claire_status zero_fill<T>(claire_ctx*, long long, T*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

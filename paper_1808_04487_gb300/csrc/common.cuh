@@ -142,7 +142,7 @@ inline bool fault_injected(const char* name) {
     (ctxp)->counters.launches++;                                                                         \
     cudaError_t e_ = cudaGetLastError();                                                                 \
     if (e_ != cudaSuccess) {                                                                             \
-      (ctxp)->set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));                        \
+      (ctxp)->set_error(std::string("kernel launch (") + (ctxp)->last_launch + "): " + cudaGetErrorString(e_)); \
       return CLAIRE_ECUDA;                                                                               \
     }                                                                                                    \
   } while (0)

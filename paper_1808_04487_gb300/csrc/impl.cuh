@@ -1,12 +1,23 @@
 // Internal interfaces between the translation units of the library (not part of the C-ABI).
 #pragma once
 
+#include <cuda.h>
+
 #include <string>
 #include <vector>
 
 #include "common.cuh"
 
 namespace claire {
+
+// TMA tensor maps of the operands the staged adjoint steps load (sl_tma.cu): boxes of 16 x 16 x 4 nodes x 3
+// components of Y, the gradient history (FP32 or BF16, with the time index as a fifth dimension) and b; built
+// once per context for the workspace arrays they describe
+struct TmaMaps {
+  CUtensorMap dY, gm, gm16, b;
+  const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool tried = false, ok = false;
+};
 
 // Twiddle tables and radix schedules of the three 1D passes of a 3D real FFT (Sec. 2.3.1 spectral operators).
 template <class T> struct FFTPlan {
@@ -28,15 +39,16 @@ template <class T> struct Work {
   T* rho = nullptr;     // [N] div v (only without the div v = 0 constraint)
   T* la = nullptr;      // [N] adjoint ping
   T* lb = nullptr;      // [N] adjoint pong
-  T* ra = nullptr;      // [N] rho * adjoint ping
-  T* rb = nullptr;      // [N] rho * adjoint pong
+  T* ra = nullptr;      // [N] rho * adjoint ping (only without the div v = 0 constraint)
+  T* rb = nullptr;      // [N] rho * adjoint pong (only without the div v = 0 constraint)
   T* b = nullptr;       // [3][N] time integral accumulator
   cplx<T>* spec = nullptr;  // 6 half spectra of Ns values
   T* s = nullptr;       // [3][N] PCG search direction in physical space (input of the matvec's SL solves)
   T* vtrial = nullptr;  // [3][N] line-search trial velocity
-  T* vdev = nullptr;    // [3][N] device copy of v for the host-array API
-  T* mTdev = nullptr;   // [N]
-  T* mRdev = nullptr;   // [N]
+  T* vdev = nullptr;    // [3][N] device copy of v for the host-array API (allocated on first use; in the arena of
+                        // a two-level coarse context, which keeps its restricted v here)
+  T* mTdev = nullptr;   // [N] (the same; the coarse context's restricted m_T)
+  T* mRdev = nullptr;   // [N] (host-array API only)
   // Fourier-domain solver vectors, 3 half spectra (component stride Ns) each
   cplx<T>* Vh = nullptr;   // v (master copy)
   cplx<T>* Vtrh = nullptr; // line-search trial v
@@ -44,13 +56,15 @@ template <class T> struct Work {
   cplx<T>* Rh = nullptr;   // PCG residual
   cplx<T>* Sh = nullptr;   // PCG direction
   cplx<T>* VTh = nullptr;  // Newton step vt
-  cplx<T>* Bh = nullptr;   // transform of the time integral b
-  cplx<T>* Sc = nullptr;   // work array of inverse transforms
+  cplx<T>* Bh = nullptr;   // transform of the time integral b (= spec, the lower three spectra)
+  cplx<T>* Sc = nullptr;   // work array of inverse transforms (= spec + 3 Ns, the upper three)
   double* bigpart = nullptr;   // one FP64 partial per block of the gather launch shape
   long long nbig = 0;
   double* partials = nullptr;  // reduction partials, [4][kReduceBlocks]
-  double* scal = nullptr;      // device scalars
+  double* scal = nullptr;      // device scalars (kScalSlots doubles)
 };
+
+constexpr int kScalSlots = 64;
 
 constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs: the FP32 kernels on this grid are compiled for 8 resident
                                      // CTAs (32 registers), so the grid is one wave (two waves cost up to 1.5x)
@@ -72,6 +86,37 @@ enum PcgSlot {
   kPcgSlots
 };
 constexpr int kPcgBase = 16;
+
+// Device-side state of Alg. 1 driven from the device (FP64 slots of Work::scal from kGnBase): the iterate's
+// objective and gradient norm, the Armijo search, the counts of the report and the outcome.
+enum GnSlot {
+  kGnJ = 0,        // objective at the current iterate
+  kGnJt,           // objective at the last trial
+  kGnGnorm,        // ||g_k||
+  kGnGnorm0,       // ||g(v = 0)||
+  kGnGvt,          // <g, vt> (the Armijo slope)
+  kGnAlpha,        // step length of the current trial
+  kGnTrial,        // trials of the current search
+  kGnAccepted,     // the current search accepted a step
+  kGnIters,        // Gauss-Newton iterations
+  kGnMatvecs,      // Hessian matvecs
+  kGnPde,          // PDE solves
+  kGnLsTrials,     // objective evaluations of the Armijo searches
+  kGnBreakdowns,   // PCG iterations stopped by <s, H s> <= 0
+  kGnStatus,       // 0 running, 1 converged, 2 max_gn, 3 line search failed, 4 non-finite
+  kGnMaxGn,        // the options the loop reads
+  kGnMaxLs,
+  kGnC1,
+  kGnGtolRel,
+  kGnGtolAbs,
+  kGnPcgRtol,
+  kGnMaxKrylov,
+  kGnMismatch,     // 1/2 ||m_1 - m_R||^2 at the returned v
+  kGnJ0,           // objective (= mismatch) at v = 0
+  kGnSlots
+};
+constexpr int kGnBase = 32;
+static_assert(kGnBase + kGnSlots <= kScalSlots, "device state block");
 constexpr int kThreads = 256;
 
 }  // namespace claire
@@ -84,6 +129,8 @@ struct claire_ctx {
   std::string err;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  void* hostbuf = nullptr;     // device copies for the host-array calls, allocated on first use
+  bool is_coarse = false;      // the half-resolution context of a two-level preconditioner
   size_t arena_used = 0;
   claire::FFTPlan<float> pf{};
   claire::FFTPlan<double> pd{};
@@ -96,7 +143,24 @@ struct claire_ctx {
   bool gm_ready = false;       // the gradient history holds finite values (used as autotuning input)
   int haloX = -1, haloY = -1;    // brick halo of the cached departure points (-1: plain gathers), light kernels
   int haloXh = -1, haloYh = -1;  // the same for the heavy kernels (last incremental step, fused-product/div steps)
+  bool halo_fixed = false;       // keep the halos above (a solve driven from the device cannot read max |Y|)
+  // CUDA graph of a whole zero-start solve driven from the device (Alg. 1 and Alg. 2 as conditional nodes), kept
+  // for the pointers, halos and beta_v it was captured with
+  cudaGraph_t gn_graph = nullptr;
+  cudaGraphExec_t gn_exec = nullptr;
+  const void* gn_key_ptr[3] = {nullptr, nullptr, nullptr};
+  int gn_key_halo[4] = {0, 0, 0, 0};
+  double gn_beta = 0.0;
+  // launches per part of the captured solve (for the launch counter): per pair outside the loops, per GN
+  // iteration outside its inner loops, per PCG iteration, per Armijo trial, per accepted step
+  long long gn_l_pair = 0, gn_l_iter = 0, gn_l_pcg = 0, gn_l_trial = 0, gn_l_accept = 0;
+  // device block of the graph: current pair index, pair count, pair table, per-pair reports, state template
+  void* gn_dev = nullptr;
+  int gn_cap = 0;
+  cudaStream_t gn_cap_streams[3] = {nullptr, nullptr, nullptr};  // capture streams of the nested loop bodies
   long long dot_blocks = 0;    // partials written by the last dot-fused adjoint step
+  claire::TmaMaps tma;         // tensor maps of the TMA-staged adjoint steps (FP32 contexts)
+  long long tma_steps = 0;     // adjoint steps run with TMA-staged operands
   // CUDA graph of the device-driven PCG loop (one conditional WHILE node around one iteration), kept for the
   // gather schedule it was captured with
   cudaGraph_t pcg_graph = nullptr;
@@ -105,6 +169,7 @@ struct claire_ctx {
   double pcg_beta = 0.0;  // beta_v baked into the captured kernels' arguments (continuation changes it)
   long long pcg_body_launches = 0;
   long long pcg_graph_runs = 0;  // PCG solves run as one graph launch
+  long long gn_graph_runs = 0;   // launches of the device-driven solve graph
   bool pcg_graph_failed = false;
   cudaStream_t pcg_cap_stream = nullptr;  // capture needs a stream other than the legacy default stream
   double* hscal = nullptr;  // pinned host mirror of Work::scal
@@ -127,7 +192,9 @@ struct claire_ctx {
     }
     return e;
   }
+  const char* last_launch = "";  // name of the last kernel launched (for error messages)
   void prof_begin(const char* name, cudaStream_t st) {
+    last_launch = name;
     if (!prof_on) return;
     prof_pending.name = name;
     prof_pending.a = prof_event();
@@ -210,8 +277,10 @@ template <class T> claire_status sp_pcg_dir(claire_ctx* c, const cplx<T>* R, cpl
                                             cudaStream_t st, const double* ps = nullptr);
 template <class T> claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G, cplx<T>* Vt, double* partials,
                                                 cudaStream_t st);
+// alpha_dev (optional): the step length read from device memory instead of alpha
 template <class T> claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr,
-                                          cplx<T>* Sc, double alpha, double* partials, cudaStream_t st);
+                                          cplx<T>* Sc, double alpha, double* partials, cudaStream_t st,
+                                          const double* alpha_dev = nullptr);
 // two-level preconditioner (Sec. 2.3.3): c the fine context, cc its half-resolution context
 template <class T>
 claire_status tl_restrict(claire_ctx* c, claire_ctx* cc, const cplx<T>* R, cplx<T>* F, cplx<T>* P, cplx<T>* X,
@@ -250,6 +319,14 @@ template <class T> claire_status sl_adjoint_step(claire_ctx* c, const T* lam_nex
                                                  const T* dY, T* lam, T* rl, T* b, const void* gmj, bool g16, T w,
                                                  cudaStream_t st, const T* sdot = nullptr, double* part = nullptr,
                                                  int H = -1);
+// ---- sl_tma.cu: the accumulating adjoint step with TMA-staged operands (FP32, brick halo 2..5, no div source;
+// its operands must be the context's own Y, gradient history, b and s) ----
+bool sl_tma_prepare(claire_ctx* c);
+// sv (optional): also part[block] = partial <sv, b_final> (the fused product of PCG's <s, H s>)
+claire_status sl_adjoint_step_tma(claire_ctx* c, const float* lam_next, float* lam, int j, float w,
+                                  const float* sv, double* part, int H, cudaStream_t st);
+// CLAIRE_ETIMEOUT (and clears the flag) if a staged step's bounded wait ran out since the last call
+claire_status sl_tma_take_error(claire_ctx* c);
 // launch shape of the gather kernels: 256 threads, x along i3 (up to 64 wide), y along i2, z = i1
 struct Launch3 {
   dim3 grid, block;
@@ -290,6 +367,8 @@ template <class T> claire_status xpay(claire_ctx* c, long long n, const T* x, do
 template <class T> claire_status waxpy(claire_ctx* c, long long n, const T* x, double a, const T* y, T* z,
                                        cudaStream_t st);
 template <class T> claire_status scale_copy(claire_ctx* c, long long n, double a, const T* x, T* y, cudaStream_t st);
+// y = 0 (n values of T)
+template <class T> claire_status zero_fill(claire_ctx* c, long long n, T* y, cudaStream_t st);
 // out[v] = scale * sum(partials[v * np .. v * np + np)) for v < nv
 claire_status reduce_final_v(claire_ctx* c, const double* partials, int nv, int np, double scale, double* out,
                              cudaStream_t st);

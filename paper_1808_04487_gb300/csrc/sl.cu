@@ -127,6 +127,21 @@ claire_status sl_adjoint_step(claire_ctx* c, const T* lam_next, const T* rl_next
 #undef ADJ_PLAIN
   } else {
     const int h = tile_halo<T>(H);
+    if constexpr (sizeof(T) == 4) {
+      // the accumulating step on the context's own arrays with bricks: its streamed operands staged by TMA
+      Work<float>& W = c->work<float>();
+      const void* gbase = g16 ? W.gm16 : (const void*)W.gm;
+      const char* tma_env = std::getenv("CLAIRE_TMA");
+      const bool own = b == W.b && dY == W.dY && rho == nullptr && gbase;
+      if (h >= 2 && own && !(tma_env && std::strcmp(tma_env, "0") == 0) && sl_tma_prepare(c)) {
+        const long long off = (static_cast<const char*>(gmj) - static_cast<const char*>(gbase)) / (g16 ? 2 : 4);
+        const int j = (int)(off / (3 * c->d.N));
+        CL_TRY(sl_adjoint_step_tma(c, lam_next, lam, j, w, dot ? sdot : nullptr, part, h, st));
+        c->tma_steps++;
+        CL_LAUNCHED(c);
+        return CLAIRE_OK;
+      }
+    }
     with_halo<T>(h, [&](auto hc) {
       with_gm<T>(gmj, g16, [&](auto g) {
         using G = std::remove_const_t<std::remove_pointer_t<decltype(g)>>;

@@ -3,7 +3,10 @@
 
 #include <cuda_bf16.h>
 
+#include <mutex>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "impl.cuh"
 
@@ -560,6 +563,20 @@ template <class T, int H> static size_t tiled_smem(int nf) {
 }
 
 
+// The dynamic shared-memory limit of a kernel, raised where the kernel is launched (once per kernel): the tiled
+// launchers live in several translation units, and each sets the attribute on the instance it launches.
+inline cudaError_t smem_limit_once(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : done)
+    if (e.first == fn && e.second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.emplace_back(fn, bytes);
+  return e;
+}
+
 // ---------------------------------------------------------------------------------------------------------------
 // Host-side launchers, one instantiation per (precision, halo). The tiled FP32 ones (halo 2..kMaxHalo) are compiled
 // in sl_h<H>.cu so that the build compiles them in parallel; sl.cu instantiates the plain (-1) ones.
@@ -567,6 +584,7 @@ template <class T, int HC>
 void sl_launch_interp(const T* f, const T* disp, T* out, const Dims& d, cudaStream_t st) {
   dim3 grid, block;
   tiled_shape<HC>(d, grid, block);
+  smem_limit_once((const void*)k_interp<T, HC>, tiled_smem<T, HC>(1));
   k_interp<T, HC><<<grid, block, tiled_smem<T, HC>(1), st>>>(f, disp, out, d);
 }
 
@@ -577,12 +595,16 @@ void sl_launch_inc(int variant, const T* q, const T* dX, const T* vt, const G* g
   dim3 grid, block;
   tiled_shape<HC>(d, grid, block);
   const size_t sm = tiled_smem<T, HC>(1);
-  if (variant == 0)
+  if (variant == 0) {
+    smem_limit_once((const void*)k_inc_step<T, false, false, HC, G>, sm);
     k_inc_step<T, false, false, HC, G><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
-  else if (variant == 2)
+  } else if (variant == 2) {
+    smem_limit_once((const void*)k_inc_step<T, true, true, HC, G>, sm);
     k_inc_step<T, true, true, HC, G><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
-  else
+  } else {
+    smem_limit_once((const void*)k_inc_step<T, true, false, HC, G>, sm);
     k_inc_step<T, true, false, HC, G><<<grid, block, sm, st>>>(q, dX, vt, gm, qout, rho, rl, b, hdt, w, d);
+  }
 }
 
 // accumulating adjoint steps (rho: div source; store: keep lambda; dot: fused <sv, b>); returns the block count
@@ -593,8 +615,12 @@ long long sl_launch_adj(bool rho_on, bool store, bool dot, const T* lam_next, co
   dim3 grid, block;
   tiled_shape<HC>(d, grid, block);
   const size_t sm = tiled_smem<T, HC>(rho_on ? 2 : 1);
-#define ADJ(R, S, D) \
-  k_adj_step<T, R, S, true, D, HC, G><<<grid, block, sm, st>>>(lam_next, rl_next, rho, dY, lam, rl, b, gm, w, dt, d, sv, part)
+#define ADJ(R, S, D)                                                                                           \
+  do {                                                                                                         \
+    smem_limit_once((const void*)k_adj_step<T, R, S, true, D, HC, G>, sm);                                     \
+    k_adj_step<T, R, S, true, D, HC, G><<<grid, block, sm, st>>>(lam_next, rl_next, rho, dY, lam, rl, b, gm, w, \
+                                                                 dt, d, sv, part);                             \
+  } while (0)
   if (dot) {
     if (rho_on)
       ADJ(true, false, true);

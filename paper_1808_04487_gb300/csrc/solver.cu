@@ -55,19 +55,28 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
   if (!c->o.divfree) ok &= takeT(W.rho, N);
   ok &= takeT(W.la, N);
   ok &= takeT(W.lb, N);
-  ok &= takeT(W.ra, N);
-  ok &= takeT(W.rb, N);
+  if (!c->o.divfree) {
+    ok &= takeT(W.ra, N);
+    ok &= takeT(W.rb, N);
+  }
   ok &= takeT(W.b, 3 * N);
   ok &= takeC(W.spec, 6 * Ns);
-  for (T** p : {&W.s, &W.vtrial, &W.vdev}) ok &= takeT(*p, 3 * N);
-  ok &= takeT(W.mTdev, N);
-  ok &= takeT(W.mRdev, N);
-  for (cplx<T>** p : {&W.Vh, &W.Vtrh, &W.Gh, &W.Rh, &W.Sh, &W.VTh, &W.Bh, &W.Sc}) ok &= takeC(*p, 3 * Ns);
+  for (T** p : {&W.s, &W.vtrial}) ok &= takeT(*p, 3 * N);
+  if (c->is_coarse) {
+    // the two-level preconditioner's coarse problem keeps its restricted m_T and v here
+    ok &= takeT(W.vdev, 3 * N);
+    ok &= takeT(W.mTdev, N);
+  }
+  for (cplx<T>** p : {&W.Vh, &W.Vtrh, &W.Gh, &W.Rh, &W.Sh, &W.VTh}) ok &= takeC(*p, 3 * Ns);
+  // the transform of the time integral and the inverse-transform work array share the six spectra of W.spec:
+  // neither is live while a spectral operator works in W.spec
+  W.Bh = W.spec;
+  W.Sc = W.spec + 3 * Ns;
   const Launch3 L = launch3(c->d);
   W.nbig = (long long)L.grid.x * L.grid.y * L.grid.z;
   W.bigpart = static_cast<double*>(c->take(sizeof(double) * size_t(W.nbig)));
   W.partials = static_cast<double*>(c->take(sizeof(double) * 4 * kReduceBlocks));
-  W.scal = static_cast<double*>(c->take(sizeof(double) * 32));
+  W.scal = static_cast<double*>(c->take(sizeof(double) * kScalSlots));
   ok &= W.partials != nullptr && W.scal != nullptr && W.bigpart != nullptr;
   if (!ok) {
     c->set_error("workspace arena too small");
@@ -76,18 +85,21 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
   return CLAIRE_OK;
 }
 
-template <class T> size_t work_bytes(const claire_opts& o, const Dims& d) {
+template <class T> size_t work_bytes(const claire_opts& o, const Dims& d, bool coarse) {
   const long long N = d.N, Ns = d.Ns;
   const int nt = o.nt;
-  const long long elems = 3 * N * 2 + (nt + 1) * N + 3 * (nt + 1) * N + (o.divfree ? 0 : N) + 4 * N + 3 * N +
-                          3 * 3 * N + 2 * N;
-  const long long celems = 6 * Ns + 8 * 3 * Ns;
+  // dX, dY; m history; (rho, rho lambda ping/pong); lambda ping/pong; b; s, vtrial; (coarse: v, m_T)
+  const long long elems = 3 * N * 2 + (nt + 1) * N + (o.divfree ? 0 : 3 * N) + 2 * N + 3 * N + 2 * 3 * N +
+                          (coarse ? 4 * N : 0);
+  // gradient history, FP32/FP64 or BF16
+  const size_t gm_bytes = (o.bf16_mask & 1) ? 2 * size_t(3 * (nt + 1) * N) : sizeof(T) * size_t(3 * (nt + 1) * N);
+  const long long celems = 6 * Ns + 6 * 3 * Ns;
   const Launch3 L = launch3(d);
   const long long nbig = (long long)L.grid.x * L.grid.y * L.grid.z;
   // FP32 contexts also hold FP64 twiddle tables (stand-alone operators transform some inputs in FP64)
   const size_t tables = fft_table_bytes<T>(d) + (sizeof(T) == 4 ? fft_table_bytes<double>(d) : 0);
-  return sizeof(T) * size_t(elems) + sizeof(cplx<T>) * size_t(celems) +
-         sizeof(double) * size_t(nbig + 4 * kReduceBlocks + 32) + tables + 64 * 256;
+  return sizeof(T) * size_t(elems) + gm_bytes + sizeof(cplx<T>) * size_t(celems) +
+         sizeof(double) * size_t(nbig + 4 * kReduceBlocks + kScalSlots) + tables + 64 * 256;
 }
 
 // Read scal[slot] to the host (synchronises the stream).
@@ -162,7 +174,8 @@ template <class T> claire_status precond_apply(claire_ctx* c, const T* r, T* z, 
 // mode 0, or -|k|^2, mode 2). A symbol that grows with |k| multiplies the rounding error of an FP32 transform --
 // spread over all modes -- by up to its largest value (beta |k|^4 reaches 1e4 on a 40^3 grid at beta = 1e-2),
 // while the field itself may hold little at high k; the FP64 transform keeps that product at FP32 rounding. Uses
-// the trial-velocity array (N doubles) and the inverse-transform work array (Ns complex doubles) as scratch.
+// the trial-velocity array (N doubles) and the inverse-transform work array (Ns complex doubles, the upper half of
+// W.spec) as scratch, so S must lie in the lower half of W.spec.
 claire_status symbol_vec_f64(claire_ctx* c, const float* x, cplx<float>* S, int ncomp, int mode, double scale,
                              cudaStream_t st) {
   Work<float>& W = c->work<float>();
@@ -188,14 +201,16 @@ template <class T> claire_status spectral_tail(claire_ctx* c, const T* v, const 
     CL_TRY(spec_reg_partial<T>(c, V, W.partials, st));
     CL_TRY(reduce_final(c, W.partials, 0.5 * c->o.beta * cellvol(c->d) / double(c->d.N), W.scal + 1, st));
   }
-  CL_TRY(vec_r2c<T>(c, b, B, st));
   if constexpr (sizeof(T) == 4) {
     if (precise) {
+      // (its FP64 scratch lies in the upper half of W.spec: before b is transformed there)
       CL_TRY(symbol_vec_f64(c, v, V, 3, 0, c->o.beta, st));
+      CL_TRY(vec_r2c<T>(c, b, B, st));
       CL_TRY(spec_addk<T>(c, V, B, st));
       return vec_c2r<T>(c, B, out, st);
     }
   }
+  CL_TRY(vec_r2c<T>(c, b, B, st));
   CL_TRY(spec_combine<T>(c, V, B, st));
   return vec_c2r<T>(c, B, out, st);
 }
@@ -265,6 +280,7 @@ template <class T> claire_status tune_tiling(claire_ctx* c, int H, Schedule* out
 // CLAIRE_GATHER=plain; CLAIRE_GATHER=tiled forces the bricks wherever a halo exists)
 template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* halo, int* halo_heavy,
                                              cudaStream_t st) {
+  if (c->halo_fixed) return CLAIRE_OK;
   Work<T>& W = c->work<T>();
   CL_TRY(absmax_partial<T>(c, disp, 3 * c->d.N, W.partials, st));
   CL_TRY(max_final(c, W.partials, kReduceBlocks, W.scal + 12, st));
@@ -292,7 +308,7 @@ template <class T> claire_status update_halo(claire_ctx* c, const T* disp, int* 
 template <class T> claire_status state_history(claire_ctx* c, const T* mT, cudaStream_t st) {
   Work<T>& W = c->work<T>();
   const long long N = c->d.N;
-  if (W.m != mT) CL_CUDA(c, cudaMemcpyAsync(W.m, mT, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  if (W.m != mT) CL_TRY(scale_copy<T>(c, N, 1.0, mT, W.m, st));  // (a kernel: also capturable in a loop body)
   for (int j = 0; j < c->o.nt; ++j) CL_TRY(sl_interp<T>(c, W.m + j * N, W.dX, W.m + (j + 1) * N, st, c->haloX));
   return CLAIRE_OK;
 }
@@ -571,6 +587,33 @@ __global__ void k_pcg_next(double* __restrict__ ps, const double* __restrict__ s
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// One PCG iteration (Alg. 2 lines 6-12) with its scalars on the device, for capture into the body of a
+// conditional WHILE node whose handle h k_pcg_next sets: Gauss-Newton matvec with the fused <s, b~>, kappa,
+// the fused residual/step update with ||r||^2 and <r, z>, the stopping test, the new direction and s in physical
+// space. The FP64 operations and their order are those of the host loop.
+template <class T> claire_status pcg_body(claire_ctx* c, cudaStream_t st, cudaGraphConditionalHandle h) {
+  Work<T>& W = c->work<T>();
+  const double sc = cellvol(c->d) / double(c->d.N);
+  double* ps = W.scal + kPcgBase;
+  CL_TRY(hess_data<T>(c, W.s, st, true));
+  CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)c->dot_blocks, cellvol(c->d), W.scal + 4, st));
+  CL_TRY(vec_r2c<T>(c, W.b, W.Bh, st));
+  c->prof_begin("pcg_kappa", st);
+  k_pcg_kappa<<<1, 1, 0, st>>>(ps, W.scal + 4);
+  CL_LAUNCHED(c);
+  CL_TRY(sp_pcg_step<T>(c, W.Sh, W.Bh, W.Rh, W.VTh, 0.0, W.partials, st, ps));
+  CL_TRY(reduce_final_v(c, W.partials, 2, kReduceBlocks, sc, W.scal, st));
+  c->prof_begin("pcg_check", st);
+  k_pcg_check<<<1, 1, 0, st>>>(ps, W.scal);
+  CL_LAUNCHED(c);
+  CL_TRY(sp_pcg_dir<T>(c, W.Rh, W.Sh, 0.0, W.partials, st, ps));
+  CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 2, st));
+  c->prof_begin("pcg_next", st);
+  k_pcg_next<<<1, 1, 0, st>>>(ps, W.scal + 2, h);
+  CL_LAUNCHED(c);
+  return spec_to_phys<T>(c, W.Sh, W.s, st);
+}
+
 void pcg_graph_release(claire_ctx* c) {
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
@@ -629,23 +672,7 @@ template <class T> claire_status pcg_graph_get(claire_ctx* c, bool* ok) {
     return fail("begin capture", e);
   }
   const long long launches0 = c->counters.launches;
-  auto capture = [&]() -> claire_status {
-    CL_TRY(hess_data<T>(c, W.s, st, true));
-    CL_TRY(reduce_final_v(c, W.bigpart, 1, (int)c->dot_blocks, cellvol(c->d), W.scal + 4, st));
-    CL_TRY(vec_r2c<T>(c, W.b, W.Bh, st));
-    k_pcg_kappa<<<1, 1, 0, st>>>(ps, W.scal + 4);
-    CL_LAUNCHED(c);
-    CL_TRY(sp_pcg_step<T>(c, W.Sh, W.Bh, W.Rh, W.VTh, 0.0, W.partials, st, ps));
-    CL_TRY(reduce_final_v(c, W.partials, 2, kReduceBlocks, sc, W.scal, st));
-    k_pcg_check<<<1, 1, 0, st>>>(ps, W.scal);
-    CL_LAUNCHED(c);
-    CL_TRY(sp_pcg_dir<T>(c, W.Rh, W.Sh, 0.0, W.partials, st, ps));
-    CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 2, st));
-    k_pcg_next<<<1, 1, 0, st>>>(ps, W.scal + 2, h);
-    CL_LAUNCHED(c);
-    return spec_to_phys<T>(c, W.Sh, W.s, st);
-  };
-  const claire_status cs = capture();
+  const claire_status cs = pcg_body<T>(c, st, h);
   const std::string cap_err = c->err;
   cudaGraph_t captured = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(st, &captured);
@@ -778,6 +805,561 @@ template <class T> claire_status pcg(claire_ctx* c, double eps_H, claire_report*
   return CLAIRE_OK;
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// Alg. 1 driven from the device. A whole zero-start solve -- the reference gradient at v = 0, the Gauss-Newton
+// loop, PCG (Alg. 2), the Armijo search and the stopping tests of Sec. 2.3.2 -- is captured once into a CUDA graph
+// of conditional nodes: an outer WHILE over a table of pairs (m_T, m_R, v) copied through the context's own
+// buffers, a WHILE over Gauss-Newton iterations, and inside it the PCG WHILE, the Armijo WHILE and an IF for the
+// accepted step. Every decision is taken by one-thread kernels on an FP64 state block (GnSlot) in the same FP64
+// operations and order as the host-driven loop, so the iterates are bit-identical to it. Every loop is bounded by
+// the options (max_gn, max_krylov, max_ls), and the pair loop by the table's length. The gathers keep the halos
+// fixed at capture time: the brick-tiled and the global-tap gathers produce the same values, so the halo choice
+// changes only speed.
+struct PairRef {
+  const void* mT;
+  const void* mR;
+  void* v;
+};
+
+__device__ __forceinline__ void gn_decide(double* gs, cudaGraphConditionalHandle h) {
+  bool more = false;
+  if (gs[kGnStatus] == 0.0) {
+    const double g = gs[kGnGnorm];
+    if (g <= gs[kGnGtolRel] * gs[kGnGnorm0] || g <= gs[kGnGtolAbs])
+      gs[kGnStatus] = 1.0;
+    else if (gs[kGnIters] >= gs[kGnMaxGn])
+      gs[kGnStatus] = 2.0;
+    else
+      more = true;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+__global__ void k_pairs_first(int* __restrict__ k, const int* __restrict__ n, cudaGraphConditionalHandle h) {
+  *k = 0;
+  cudaGraphSetConditional(h, *n > 0 ? 1u : 0u);
+}
+__global__ void k_pairs_next(int* __restrict__ k, const int* __restrict__ n, cudaGraphConditionalHandle h) {
+  const int j = *k + 1;
+  *k = j;
+  cudaGraphSetConditional(h, j < *n ? 1u : 0u);
+}
+// pair k's images into the context's buffers, v = 0, and the state block reset from its template
+template <class T>
+__global__ void k_pair_in(const PairRef* __restrict__ tab, const int* __restrict__ k, T* __restrict__ mT,
+                          T* __restrict__ mR, T* __restrict__ v, long long N, double* __restrict__ gs,
+                          const double* __restrict__ tmpl) {
+  const PairRef p = tab[*k];
+  const T* a = static_cast<const T*>(p.mT);
+  const T* b = static_cast<const T*>(p.mR);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    mT[i] = a[i];
+    mR[i] = b[i];
+    v[i] = T(0);
+    v[N + i] = T(0);
+    v[2 * N + i] = T(0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < kGnSlots) gs[threadIdx.x] = tmpl[threadIdx.x];
+}
+// v to pair k's array and the state block to its report row
+template <class T>
+__global__ void k_pair_out(const PairRef* __restrict__ tab, const int* __restrict__ k, const T* __restrict__ v,
+                           long long N, const double* __restrict__ gs, double* __restrict__ reports) {
+  const PairRef p = tab[*k];
+  T* out = static_cast<T*>(p.v);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * N;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = v[i];
+  if (blockIdx.x == 0 && threadIdx.x < kGnSlots) reports[(long long)(*k) * kGnSlots + threadIdx.x] = gs[threadIdx.x];
+}
+// after the reference gradient at v = 0: non-finite inputs, mismatch0 = J0, g_0, then the first stopping test
+__global__ void k_gn_start(double* __restrict__ gs, const double* __restrict__ in2, double half_cell,
+                           const double* __restrict__ gg, cudaGraphConditionalHandle h) {
+  if (in2[0] != 0.0) gs[kGnStatus] = 4.0;
+  const double J = half_cell * in2[1];
+  gs[kGnJ0] = J;
+  gs[kGnJ] = J;
+  const double gn = sqrt(gg[0]);
+  gs[kGnGnorm0] = gn;
+  gs[kGnGnorm] = gn;
+  gs[kGnPde] = 2.0;
+  if (!isfinite(J) || !isfinite(gn)) gs[kGnStatus] = 4.0;
+  gn_decide(gs, h);
+}
+// forcing term and the PCG state from <r, z>, ||r||^2, <s, beta A s> (Alg. 2 lines 1-4)
+__global__ void k_gn_pcg_init(double* __restrict__ gs, double* __restrict__ ps, const double* __restrict__ s3,
+                              cudaGraphConditionalHandle h) {
+  for (int i = 0; i < kPcgSlots; ++i) ps[i] = 0.0;
+  ps[kPcgDone] = 1.0;
+  if (gs[kGnStatus] != 0.0) {
+    cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  const double rz = s3[0], r0 = sqrt(s3[1]);
+  if (!isfinite(rz) || !isfinite(r0)) {
+    gs[kGnStatus] = 4.0;
+    cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  ps[kPcgRz] = rz;
+  ps[kPcgR0] = r0;
+  ps[kPcgSAs] = s3[2];
+  ps[kPcgEps] = gs[kGnPcgRtol] > 0 ? gs[kGnPcgRtol] : fmin(0.5, sqrt(gs[kGnGnorm] / gs[kGnGnorm0]));
+  ps[kPcgMaxIt] = gs[kGnMaxKrylov];
+  ps[kPcgDone] = 0.0;
+  cudaGraphSetConditional(h, 1u);
+}
+// after the PCG loop: counts, breakdown, non-finite <s, H s>
+__global__ void k_gn_pcg_end(double* __restrict__ gs, const double* __restrict__ ps) {
+  if (gs[kGnStatus] != 0.0) return;
+  const double n = ps[kPcgCount];
+  gs[kGnMatvecs] += n;
+  gs[kGnPde] += 2.0 * n;
+  if (ps[kPcgNan] != 0.0) gs[kGnStatus] = 4.0;
+  if (ps[kPcgBreakdown] != 0.0) gs[kGnBreakdowns] += 1.0;
+}
+// breakdown in the first PCG iteration: the step is the first direction
+template <class T>
+__global__ void k_copy_if_first_breakdown(const double* __restrict__ ps, const T* __restrict__ src, T* __restrict__ dst,
+                                          long long n) {
+  if (ps[kPcgBreakdown] == 0.0 || ps[kPcgCopyS] == 0.0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+__global__ void k_ls_init(double* __restrict__ gs, const double* __restrict__ gvt, cudaGraphConditionalHandle h) {
+  gs[kGnGvt] = gvt[0];
+  gs[kGnAlpha] = 1.0;
+  gs[kGnTrial] = 0.0;
+  gs[kGnAccepted] = 0.0;
+  cudaGraphSetConditional(h, gs[kGnStatus] == 0.0 ? 1u : 0u);
+}
+// one Armijo test (Alg. 1 line 9): J(v + alpha vt) <= J + c1 alpha <g, vt>, else alpha /= 2
+__global__ void k_ls_check(double* __restrict__ gs, const double* __restrict__ r2, cudaGraphConditionalHandle h) {
+  const double Jt = r2[0] + r2[1];
+  gs[kGnJt] = Jt;
+  gs[kGnLsTrials] += 1.0;
+  gs[kGnPde] += 1.0;
+  gs[kGnTrial] += 1.0;
+  if (!isfinite(Jt)) {
+    gs[kGnStatus] = 4.0;
+    cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  const double alpha = gs[kGnAlpha];
+  if (Jt <= gs[kGnJ] + gs[kGnC1] * alpha * gs[kGnGvt]) {
+    gs[kGnAccepted] = 1.0;
+    cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  gs[kGnAlpha] = alpha * 0.5;
+  cudaGraphSetConditional(h, gs[kGnTrial] < gs[kGnMaxLs] ? 1u : 0u);
+}
+__global__ void k_ls_end(double* __restrict__ gs, cudaGraphConditionalHandle h) {
+  const bool ok = gs[kGnStatus] == 0.0;
+  if (ok && gs[kGnAccepted] == 0.0) gs[kGnStatus] = 3.0;
+  cudaGraphSetConditional(h, (ok && gs[kGnAccepted] != 0.0) ? 1u : 0u);
+}
+// the accepted step's gradient norm, then the stopping tests for the next iteration
+__global__ void k_gn_update(double* __restrict__ gs, const double* __restrict__ gg) {
+  gs[kGnJ] = gs[kGnJt];
+  gs[kGnPde] += 1.0;
+  const double gn = sqrt(gg[0]);
+  gs[kGnGnorm] = gn;
+  gs[kGnIters] += 1.0;
+  if (!isfinite(gn)) gs[kGnStatus] = 4.0;
+}
+__global__ void k_gn_next(double* __restrict__ gs, cudaGraphConditionalHandle h) { gn_decide(gs, h); }
+__global__ void k_gn_after(const double* __restrict__ gs, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, gs[kGnStatus] == 3.0 ? 1u : 0u);
+}
+
+// a handle for a conditional node that will be added to the graph stream st is capturing into
+cudaError_t cond_handle(cudaStream_t st, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault);
+}
+// appends a conditional node (WHILE or IF, one body) after the capture position of st; *body is its body graph
+cudaError_t cond_node(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                      cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np)) != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+#define GN_CE(call)                                                                                  \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      c->set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+      return CLAIRE_ECUDA;                                                                           \
+    }                                                                                                \
+  } while (0)
+
+// layout of the graph's device block
+struct GnBlock {
+  int* k;
+  int* n;
+  PairRef* tab;
+  double* tmpl;
+  double* reports;
+};
+inline GnBlock gn_block(claire_ctx* c) {
+  char* p = static_cast<char*>(c->gn_dev);
+  GnBlock b;
+  b.k = reinterpret_cast<int*>(p);
+  b.n = b.k + 1;
+  b.tmpl = reinterpret_cast<double*>(p + 256);
+  b.tab = reinterpret_cast<PairRef*>(p + 256 + 8 * kGnSlots);
+  b.reports = reinterpret_cast<double*>(p + 256 + 8 * kGnSlots + sizeof(PairRef) * size_t(c->gn_cap));
+  return b;
+}
+inline size_t gn_block_bytes(int cap) { return 256 + 8 * kGnSlots + (sizeof(PairRef) + 8 * kGnSlots) * size_t(cap); }
+
+inline unsigned copy_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  return (unsigned)(b < 4864 ? b : 4864);
+}
+
+// capture the whole solve into a new graph (the context's halos are held fixed while it runs)
+template <class T> claire_status gn_capture(claire_ctx* c, cudaGraph_t* out) {
+  Work<T>& W = c->work<T>();
+  const Dims& d = c->d;
+  const long long N = d.N, n3 = 3 * N, Ns = d.Ns;
+  const double sc = cellvol(d) / double(N);
+  double* gs = W.scal + kGnBase;
+  double* ps = W.scal + kPcgBase;
+  const GnBlock B = gn_block(c);
+  cudaStream_t s0 = c->pcg_cap_stream, s1 = c->gn_cap_streams[0], s2 = c->gn_cap_streams[1],
+               s3 = c->gn_cap_streams[2];
+  cudaGraph_t g = nullptr;
+  GN_CE(cudaGraphCreate(&g, 0));
+  *out = g;
+  GN_CE(cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  auto body = [&](cudaStream_t st, cudaGraph_t bg, long long* count, auto&& fn) -> claire_status {
+    GN_CE(cudaStreamBeginCaptureToGraph(st, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = c->counters.launches;
+    const claire_status r = fn();
+    cudaGraph_t tmp = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &tmp);
+    if (count) *count = c->counters.launches - l0;
+    if (r != CLAIRE_OK) return r;
+    GN_CE(e);
+    return CLAIRE_OK;
+  };
+  long long l_pcg = 0, l_trial = 0, l_acc = 0, l_fail = 0, l_iter_all = 0, l_pair_all = 0;
+  auto top = [&]() -> claire_status {
+    cudaGraphConditionalHandle hp;
+    GN_CE(cond_handle(s0, &hp));
+    k_pairs_first<<<1, 1, 0, s0>>>(B.k, B.n, hp);
+    GN_CE(cudaGetLastError());
+    cudaGraph_t bp;
+    GN_CE(cond_node(s0, hp, cudaGraphCondTypeWhile, &bp));
+    // ---- one pair: its images in, the reference gradient at v = 0, the Gauss-Newton loop, v and report out
+    return body(s1, bp, &l_pair_all, [&]() -> claire_status {
+      cudaStream_t st = s1;
+      c->prof_begin("pair_in", st);
+      k_pair_in<T><<<copy_blocks(N), 256, 0, st>>>(B.tab, B.k, W.mTdev, W.mRdev, W.vdev, N, gs, B.tmpl);
+      CL_LAUNCHED(c);
+      CL_TRY(nonfinite_partial<T>(c, W.mTdev, N, W.mRdev, N, W.partials, st));
+      CL_TRY(diffsq_partial<T>(c, W.mTdev, W.mRdev, N, W.partials + kReduceBlocks, st));
+      CL_TRY(reduce_final_v(c, W.partials, 2, kReduceBlocks, 1.0, W.scal + 13, st));
+      CL_TRY(zero_fill<T>(c, n3, W.vtrial, st));
+      CL_TRY(linearize<T>(c, W.mTdev, W.vtrial, st));
+      CL_TRY(gradient_spec<T>(c, W.mRdev, (const cplx<T>*)nullptr, 0, st));
+      CL_TRY(zero_fill<T>(c, 2 * 3 * Ns, reinterpret_cast<T*>(W.Vh), st));
+      cudaGraphConditionalHandle hg;
+      GN_CE(cond_handle(st, &hg));
+      c->prof_begin("gn_start", st);
+      k_gn_start<<<1, 1, 0, st>>>(gs, W.scal + 13, 0.5 * cellvol(d), W.scal, hg);
+      CL_LAUNCHED(c);
+      cudaGraph_t bg;
+      GN_CE(cond_node(st, hg, cudaGraphCondTypeWhile, &bg));
+      // ---- one Gauss-Newton iteration (Alg. 1 lines 4-12)
+      CL_TRY(body(s2, bg, &l_iter_all, [&]() -> claire_status {
+        cudaStream_t st = s2;
+        CL_TRY(sp_pcg0<T>(c, W.Gh, W.Rh, W.Sh, W.VTh, W.partials, st));
+        CL_TRY(reduce_final_v(c, W.partials, 3, kReduceBlocks, sc, W.scal, st));
+        cudaGraphConditionalHandle hpcg;
+        GN_CE(cond_handle(st, &hpcg));
+        c->prof_begin("gn_pcg_init", st);
+        k_gn_pcg_init<<<1, 1, 0, st>>>(gs, ps, W.scal, hpcg);
+        CL_LAUNCHED(c);
+        CL_TRY(spec_to_phys<T>(c, W.Sh, W.s, st));
+        cudaGraph_t bpcg;
+        GN_CE(cond_node(st, hpcg, cudaGraphCondTypeWhile, &bpcg));
+        CL_TRY(body(s3, bpcg, &l_pcg, [&]() { return pcg_body<T>(c, s3, hpcg); }));
+        c->prof_begin("gn_pcg_end", st);
+        k_gn_pcg_end<<<1, 1, 0, st>>>(gs, ps);
+        CL_LAUNCHED(c);
+        c->prof_begin("copy_if_breakdown", st);
+        k_copy_if_first_breakdown<T><<<copy_blocks(2 * 3 * Ns), 256, 0, st>>>(
+            ps, reinterpret_cast<const T*>(W.Sh), reinterpret_cast<T*>(W.VTh), 2 * 3 * Ns);
+        CL_LAUNCHED(c);
+        CL_TRY(sp_project_dot<T>(c, W.Gh, W.VTh, W.partials, st));
+        CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, sc, W.scal + 7, st));
+        cudaGraphConditionalHandle hls;
+        GN_CE(cond_handle(st, &hls));
+        c->prof_begin("ls_init", st);
+        k_ls_init<<<1, 1, 0, st>>>(gs, W.scal + 7, hls);
+        CL_LAUNCHED(c);
+        cudaGraph_t bls;
+        GN_CE(cond_node(st, hls, cudaGraphCondTypeWhile, &bls));
+        // ---- one Armijo trial
+        CL_TRY(body(s3, bls, &l_trial, [&]() -> claire_status {
+          cudaStream_t st = s3;
+          CL_TRY(sp_trial<T>(c, W.Vh, W.VTh, W.Vtrh, W.Sc, 0.0, W.partials, st, gs + kGnAlpha));
+          CL_TRY(reduce_final_v(c, W.partials, 1, kReduceBlocks, 0.5 * c->o.beta * sc, W.scal + 5, st));
+          CL_TRY(vec_c2r<T>(c, W.Sc, W.vtrial, st));
+          CL_TRY(state_mismatch<T>(c, W.mTdev, W.mRdev, W.vtrial, 6, st));
+          c->prof_begin("ls_check", st);
+          k_ls_check<<<1, 1, 0, st>>>(gs, W.scal + 5, hls);
+          CL_LAUNCHED(c);
+          return CLAIRE_OK;
+        }));
+        cudaGraphConditionalHandle hacc;
+        GN_CE(cond_handle(st, &hacc));
+        c->prof_begin("ls_end", st);
+        k_ls_end<<<1, 1, 0, st>>>(gs, hacc);
+        CL_LAUNCHED(c);
+        cudaGraph_t bacc;
+        GN_CE(cond_node(st, hacc, cudaGraphCondTypeIf, &bacc));
+        // ---- the accepted step: new iterate, its linearisation and gradient
+        CL_TRY(body(s3, bacc, &l_acc, [&]() -> claire_status {
+          cudaStream_t st = s3;
+          CL_TRY(scale_copy<T>(c, 2 * 3 * Ns, 1.0, reinterpret_cast<const T*>(W.Vtrh), reinterpret_cast<T*>(W.Vh),
+                               st));
+          CL_TRY(scale_copy<T>(c, n3, 1.0, W.vtrial, W.vdev, st));
+          CL_TRY(finish_linearization<T>(c, W.vdev, st));
+          CL_TRY(gradient_spec<T>(c, W.mRdev, W.Vh, 0, st));
+          c->prof_begin("gn_update", st);
+          k_gn_update<<<1, 1, 0, st>>>(gs, W.scal);
+          CL_LAUNCHED(c);
+          return CLAIRE_OK;
+        }));
+        c->prof_begin("gn_next", st);
+        k_gn_next<<<1, 1, 0, st>>>(gs, hg);
+        CL_LAUNCHED(c);
+        return CLAIRE_OK;
+      }));
+      // ---- after a failed line search the state is recomputed at the last accepted v
+      cudaGraphConditionalHandle hf;
+      GN_CE(cond_handle(st, &hf));
+      c->prof_begin("gn_after", st);
+      k_gn_after<<<1, 1, 0, st>>>(gs, hf);
+      CL_LAUNCHED(c);
+      cudaGraph_t bf;
+      GN_CE(cond_node(st, hf, cudaGraphCondTypeIf, &bf));
+      CL_TRY(body(s2, bf, &l_fail, [&]() -> claire_status {
+        CL_TRY(sl_departure<T>(c, W.vdev, +1, W.dX, s2));
+        return state_history<T>(c, W.mTdev, s2);
+      }));
+      CL_TRY(diffsq_partial<T>(c, W.m + c->o.nt * N, W.mRdev, N, W.partials, st));
+      CL_TRY(reduce_final(c, W.partials, 0.5 * cellvol(d), gs + kGnMismatch, st));
+      c->prof_begin("pair_out", st);
+      k_pair_out<T><<<copy_blocks(n3), 256, 0, st>>>(B.tab, B.k, W.vdev, N, gs, B.reports);
+      CL_LAUNCHED(c);
+      c->prof_begin("pairs_next", st);
+      k_pairs_next<<<1, 1, 0, st>>>(B.k, B.n, hp);
+      CL_LAUNCHED(c);
+      return CLAIRE_OK;
+    });
+  };
+  const long long launches0 = c->counters.launches;
+  const claire_status r = top();
+  cudaGraph_t tmp = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s0, &tmp);
+  c->counters.launches = launches0;
+  if (r != CLAIRE_OK) return r;
+  GN_CE(e);
+  // launches per part, each body counted without the bodies nested in it
+  c->gn_l_pcg = l_pcg;
+  c->gn_l_trial = l_trial;
+  c->gn_l_accept = l_acc;
+  c->gn_l_iter = l_iter_all - l_pcg - l_trial - l_acc;
+  c->gn_l_pair = l_pair_all - l_iter_all - l_fail + 2;
+  return CLAIRE_OK;
+}
+
+// the device copies of m_T, m_R and v that the host-array calls and the device-driven solve work on
+template <class T> claire_status ensure_hostbuf(claire_ctx* c) {
+  Work<T>& W = c->work<T>();
+  if (W.mRdev) return CLAIRE_OK;
+  const long long N = c->d.N;
+  if (cudaMalloc(&c->hostbuf, sizeof(T) * 5 * size_t(N)) != cudaSuccess) {
+    cudaGetLastError();
+    c->hostbuf = nullptr;
+    c->set_error("cudaMalloc of the context's copies of m_T, m_R and v failed");
+    return CLAIRE_ENOMEM;
+  }
+  W.vdev = static_cast<T*>(c->hostbuf);
+  W.mTdev = W.vdev + 3 * N;
+  W.mRdev = W.mTdev + N;
+  return CLAIRE_OK;
+}
+
+// Halos of a solve driven from the device, fixed before capture: 3 (departure points up to 2 voxels per time step
+// stay inside the bricks; farther ones fall back to global taps node by node), or global taps for a kernel class
+// where the autotuner has preferred them on this grid; CLAIRE_GATHER=plain|tiled overrides as elsewhere.
+template <class T> claire_status gn_fix_halos(claire_ctx* c, cudaStream_t st) {
+  const int H = sizeof(T) == 4 ? 3 : -1;
+  c->haloX = c->haloXh = c->haloY = c->haloYh = H;
+  const char* force = std::getenv("CLAIRE_GATHER");
+  if (force && std::strcmp(force, "plain") == 0) {
+    c->haloX = c->haloXh = c->haloY = c->haloYh = -1;
+  } else if (!(force && std::strcmp(force, "tiled") == 0) && sizeof(T) == 4 && c->gm_ready) {
+    Schedule sch;
+    CL_TRY(tune_tiling<T>(c, H, &sch, st));
+    if (!sch.light) c->haloX = c->haloY = -1;
+    if (!sch.heavy) c->haloXh = c->haloYh = -1;
+  }
+  return CLAIRE_OK;
+}
+
+void gn_graph_release(claire_ctx* c) {
+  if (c->gn_exec) cudaGraphExecDestroy(c->gn_exec);
+  if (c->gn_graph) cudaGraphDestroy(c->gn_graph);
+  c->gn_exec = nullptr;
+  c->gn_graph = nullptr;
+}
+
+// Enqueues the solves of pairs[0..n) (device arrays of this context's grid; every v is overwritten, the solves
+// start from v = 0) as one graph launch on st; the per-pair state blocks land in reports (pinned host memory,
+// n x kGnSlots doubles) once st has been synchronised.
+template <class T> claire_status gn_run(claire_ctx* c, const PairRef* pairs, int n, double* reports, cudaStream_t st) {
+  CL_TRY(ensure_hostbuf<T>(c));
+  if (!c->gn_dev || c->gn_cap < n) {
+    gn_graph_release(c);
+    if (c->gn_dev) cudaFree(c->gn_dev);
+    c->gn_dev = nullptr;
+    const int cap = n < 8 ? 8 : n;
+    if (cudaMalloc(&c->gn_dev, gn_block_bytes(cap)) != cudaSuccess) {
+      cudaGetLastError();
+      c->set_error("cudaMalloc of the device-driven solve's pair table failed");
+      return CLAIRE_ENOMEM;
+    }
+    c->gn_cap = cap;
+  }
+  if (!c->pcg_cap_stream) CL_CUDA(c, cudaStreamCreateWithFlags(&c->pcg_cap_stream, cudaStreamNonBlocking));
+  for (cudaStream_t& s : c->gn_cap_streams)
+    if (!s) CL_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  CL_TRY(gn_fix_halos<T>(c, st));
+  if constexpr (sizeof(T) == 4) sl_tma_prepare(c);  // host-side set-up of the staged gathers, before any capture
+  const int key[4] = {c->haloX, c->haloXh, c->haloY, c->haloYh};
+  if (!c->gn_exec || !std::equal(key, key + 4, c->gn_key_halo) || c->gn_beta != c->o.beta) {
+    gn_graph_release(c);
+    c->halo_fixed = true;
+    cudaGraph_t g = nullptr;
+    const claire_status cs = gn_capture<T>(c, &g);
+    c->halo_fixed = false;
+    if (cs != CLAIRE_OK) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return cs;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      c->set_error(std::string("cudaGraphInstantiate (device-driven solve): ") + cudaGetErrorString(e));
+      return CLAIRE_ECUDA;
+    }
+    c->gn_graph = g;
+    c->gn_exec = ex;
+    std::copy(key, key + 4, c->gn_key_halo);
+    c->gn_beta = c->o.beta;
+  }
+  const GnBlock B = gn_block(c);
+  double tmpl[kGnSlots] = {};
+  const claire_opts& o = c->o;
+  tmpl[kGnMaxGn] = o.max_gn;
+  tmpl[kGnMaxLs] = o.max_ls;
+  tmpl[kGnC1] = o.armijo_c1;
+  tmpl[kGnGtolRel] = o.gtol_rel;
+  tmpl[kGnGtolAbs] = o.gtol_abs;
+  tmpl[kGnPcgRtol] = o.pcg_rtol;
+  tmpl[kGnMaxKrylov] = o.max_krylov;
+  // (pageable sources: each copy is staged before the call returns)
+  CL_CUDA(c, cudaMemcpyAsync(B.tmpl, tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaMemcpyAsync(B.tab, pairs, sizeof(PairRef) * size_t(n), cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaMemcpyAsync(B.n, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaGraphLaunch(c->gn_exec, st));
+  c->gn_graph_runs++;
+  CL_CUDA(c, cudaMemcpyAsync(reports, B.reports, sizeof(double) * kGnSlots * size_t(n), cudaMemcpyDeviceToHost, st));
+  return CLAIRE_OK;
+}
+
+// a pair's report and status from its device state block (after the stream has been synchronised)
+claire_status gn_report(claire_ctx* c, const double* gs, claire_report* rep) {
+  std::memset(rep, 0, sizeof(*rep));
+  rep->gn_iters = (int)gs[kGnIters];
+  rep->matvecs = (int)gs[kGnMatvecs];
+  rep->pde_solves = (int)gs[kGnPde];
+  rep->ls_trials = (int)gs[kGnLsTrials];
+  rep->pcg_breakdowns = (int)gs[kGnBreakdowns];
+  rep->J0 = gs[kGnJ0];
+  rep->mismatch0 = gs[kGnJ0];
+  rep->J = gs[kGnJ];
+  rep->mismatch = gs[kGnMismatch];
+  rep->gnorm0 = gs[kGnGnorm0];
+  rep->gnorm = gs[kGnGnorm];
+  const int status = (int)gs[kGnStatus];
+  rep->converged = status == 1;
+  const long long entered = rep->gn_iters + ((status == 3 || status == 4) ? 1 : 0);
+  c->counters.launches += c->gn_l_pair + entered * c->gn_l_iter + rep->matvecs * c->gn_l_pcg +
+                          rep->ls_trials * c->gn_l_trial + rep->gn_iters * c->gn_l_accept;
+  switch (status) {
+    case 1: return CLAIRE_OK;
+    case 2: return CLAIRE_ENOTCONV;
+    case 3: return CLAIRE_ELINESEARCH;
+    case 4: c->set_error("non-finite input, objective or gradient"); return CLAIRE_ENAN;
+    default: c->set_error("device-driven solve ended without a status"); return CLAIRE_ECUDA;
+  }
+}
+
+// the device-driven form of register_dev for a zero initial guess (one pair)
+template <class T> claire_status register_graph(claire_ctx* c, const T* mT, const T* mR, T* v, claire_report* rep,
+                                                cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  CL_CUDA(c, cudaEventCreate(&e0));
+  CL_CUDA(c, cudaEventCreate(&e1));
+  CL_CUDA(c, cudaEventRecord(e0, st));
+  const PairRef p{mT, mR, v};
+  double* hs = c->hscal + 64;
+  claire_status s = gn_run<T>(c, &p, 1, hs, st);
+  if (s == CLAIRE_OK) {
+    CL_CUDA(c, cudaEventRecord(e1, st));
+    CL_CUDA(c, cudaEventSynchronize(e1));
+    s = gn_report(c, hs, rep);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    rep->ms_total = ms;
+    if (sizeof(T) == 4 && c->tma_steps > 0) {
+      const claire_status ts = sl_tma_take_error(c);
+      if (ts != CLAIRE_OK) s = ts;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
 // Alg. 1 with Armijo backtracking and the stopping rules of Sec. 2.3.2. The iterate is kept as its half spectrum
 // (master copy) next to its physical values (needed by the departure points); the gradient, the step and the
 // regularisation value live in the Fourier domain (see pcg).
@@ -788,6 +1370,15 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
   const claire_opts& o = c->o;
   const double sc = cellvol(c->d) / double(N);
   std::memset(rep, 0, sizeof(*rep));
+  {
+    // the whole zero-start solve as one graph launch (CLAIRE_GN=device; spectral preconditioner, no profiling)
+    const char* gm = std::getenv("CLAIRE_GN");
+    if (gm && std::strcmp(gm, "device") == 0 && !c->prof_on && !c->coarse) {
+      double vv = 0.0;
+      CL_TRY(inner<T>(c, v, v, n3, &vv, st));
+      if (vv == 0.0) return register_graph<T>(c, mT, mR, v, rep, st);
+    }
+  }
   cudaEvent_t e0, e1;
   CL_CUDA(c, cudaEventCreate(&e0));
   CL_CUDA(c, cudaEventCreate(&e1));
@@ -929,7 +1520,114 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
   rep->ms_total = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // a staged gather whose bounded wait ran out left its outputs incomplete
+  if (sizeof(T) == 4 && c->tma_steps > 0) {
+    const claire_status ts = sl_tma_take_error(c);
+    if (ts != CLAIRE_OK) return ts;
+  }
   return status;
+}
+
+// Batched registration with every solve driven from the device: the pairs are grouped by grid; each group gets up
+// to nworkers contexts with a stream each, and each context runs its share of the group as ONE graph launch (the
+// pair loop of the captured solve), all launches issued before the first synchronisation. Pairs with a nonzero
+// initial guess take the host-driven solve afterwards.
+claire_status register_batch_device(const claire_opts* base, claire_pair_f32* pairs, int npairs, int nworkers) {
+  std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+  for (int i = 0; i < npairs; ++i) groups[std::make_tuple(pairs[i].n[0], pairs[i].n[1], pairs[i].n[2])].push_back(i);
+  struct Lane {
+    claire_ctx* c = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<int> idx;
+    std::vector<PairRef> tab;
+    double* reports = nullptr;  // pinned
+  };
+  std::vector<Lane> lanes;
+  std::vector<std::pair<int, int>> host_pairs;  // (pair, lane of its group) with a nonzero initial guess
+  claire_status first = CLAIRE_OK;
+  auto note = [&](int i, claire_status s) {
+    pairs[i].status = s;
+    if (s != CLAIRE_OK && s != CLAIRE_ENOTCONV && s != CLAIRE_ELINESEARCH && first == CLAIRE_OK) first = s;
+  };
+  for (auto& kv : groups) {
+    const std::vector<int>& members = kv.second;
+    const int nl = nworkers < (int)members.size() ? nworkers : (int)members.size();
+    const size_t l0 = lanes.size();
+    for (int w = 0; w < nl; ++w) {
+      claire_opts o = *base;
+      o.n[0] = std::get<0>(kv.first);
+      o.n[1] = std::get<1>(kv.first);
+      o.n[2] = std::get<2>(kv.first);
+      Lane L;
+      const claire_status cs = claire_create(&o, &L.c);
+      if (cs != CLAIRE_OK) {
+        for (int i : members) note(i, cs);
+        break;
+      }
+      if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess) {
+        claire_destroy(L.c);
+        for (int i : members) note(i, CLAIRE_ECUDA);
+        break;
+      }
+      lanes.push_back(L);
+    }
+    if (lanes.size() == l0) continue;
+    const int nlan = (int)(lanes.size() - l0);
+    int r = 0;
+    for (int i : members) {
+      Lane& L = lanes[l0 + (r++ % nlan)];
+      double vv = 0.0;
+      const claire_status s = inner<float>(L.c, pairs[i].v, pairs[i].v, 3LL * L.c->d.N, &vv, L.st);
+      if (s != CLAIRE_OK) {
+        note(i, s);
+      } else if (vv != 0.0) {
+        host_pairs.emplace_back(i, (int)(l0 + (r - 1) % nlan));
+      } else {
+        L.idx.push_back(i);
+        L.tab.push_back(PairRef{pairs[i].mT, pairs[i].mR, pairs[i].v});
+      }
+    }
+  }
+  // issue every lane's graph launch, then synchronise once
+  for (Lane& L : lanes) {
+    if (L.idx.empty()) continue;
+    if (cudaMallocHost(&L.reports, sizeof(double) * kGnSlots * L.idx.size()) != cudaSuccess) {
+      cudaGetLastError();
+      L.reports = nullptr;
+      for (int i : L.idx) note(i, CLAIRE_ENOMEM);
+      L.idx.clear();
+      continue;
+    }
+    const claire_status s = gn_run<float>(L.c, L.tab.data(), (int)L.idx.size(), L.reports, L.st);
+    if (s != CLAIRE_OK) {
+      for (int i : L.idx) note(i, s);
+      L.idx.clear();
+    }
+  }
+  for (Lane& L : lanes) {
+    if (cudaStreamSynchronize(L.st) != cudaSuccess) {
+      for (int i : L.idx) note(i, CLAIRE_ECUDA);
+      L.idx.clear();
+    }
+    for (size_t k = 0; k < L.idx.size(); ++k) {
+      const int i = L.idx[k];
+      note(i, gn_report(L.c, L.reports + k * kGnSlots, &pairs[i].rep));
+    }
+    if (!L.idx.empty() && L.c->tma_steps > 0 && sl_tma_take_error(L.c) != CLAIRE_OK)
+      for (int i : L.idx) note(i, CLAIRE_ETIMEOUT);
+  }
+  for (auto& hp : host_pairs) {
+    Lane& L = lanes[hp.second];
+    claire_pair_f32& p = pairs[hp.first];
+    note(hp.first, register_dev<float>(L.c, p.mT, p.mR, p.v, &p.rep, L.st));
+  }
+  for (Lane& L : lanes) {
+    if (L.reports) cudaFreeHost(L.reports);
+    claire_destroy(L.c);
+    cudaStreamDestroy(L.st);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return CLAIRE_ECUDA;
+  return first;
 }
 
 template <class T> claire_status transport_dev(claire_ctx* c, const T* m0, const T* v, int dir, T* m1,
@@ -1209,6 +1907,7 @@ template <class T> claire_status api_register_host(claire_ctx* c, const T* mT, c
   Work<T>& W = c->work<T>();
   cudaStream_t st = (cudaStream_t)s;
   const long long N = c->d.N;
+  CL_TRY(ensure_hostbuf<T>(c));  // device copies of m_T, m_R and v, allocated on first use (kept until destroy)
   CL_CUDA(c, cudaMemcpyAsync(W.mTdev, mT, sizeof(T) * N, cudaMemcpyHostToDevice, st));
   CL_CUDA(c, cudaMemcpyAsync(W.mRdev, mR, sizeof(T) * N, cudaMemcpyHostToDevice, st));
   CL_CUDA(c, cudaMemcpyAsync(W.vdev, v, sizeof(T) * 3 * N, cudaMemcpyHostToDevice, st));
@@ -1304,7 +2003,14 @@ claire_status claire_default_opts(claire_opts* o, int n1, int n2, int n3, int pr
   return CLAIRE_OK;
 }
 
-claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
+namespace {
+claire_status create_ctx(const claire_opts* opts, bool coarse, claire_ctx** out);
+}
+
+claire_status claire_create(const claire_opts* opts, claire_ctx** out) { return create_ctx(opts, false, out); }
+
+namespace {
+claire_status create_ctx(const claire_opts* opts, bool coarse, claire_ctx** out) {
   if (!opts || !out) return CLAIRE_EINVAL;
   *out = nullptr;
   const claire_opts& o = *opts;
@@ -1327,6 +2033,7 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   claire_ctx* c = new (std::nothrow) claire_ctx();
   if (!c) return CLAIRE_ENOMEM;
   c->o = o;
+  c->is_coarse = coarse;
   c->gm16_on = (o.bf16_mask & 1) != 0;
   c->d.n1 = o.n[0];
   c->d.n2 = o.n[1];
@@ -1341,14 +2048,15 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
     delete c;
     return CLAIRE_EINVAL;
   }
-  const size_t bytes = o.precision == CLAIRE_F32 ? work_bytes<float>(o, c->d) : work_bytes<double>(o, c->d);
+  const size_t bytes =
+      o.precision == CLAIRE_F32 ? work_bytes<float>(o, c->d, coarse) : work_bytes<double>(o, c->d, coarse);
   if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return CLAIRE_ENOMEM;
   }
   c->arena_bytes = bytes;
-  if (cudaMallocHost(&c->hscal, 64 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost(&c->hscal, 128 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->arena);
     delete c;
@@ -1374,7 +2082,7 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
     claire_opts oc = o;
     for (int a = 0; a < 3; ++a) oc.n[a] = o.n[a] / 2;
     oc.precond = 0;
-    s = claire_create(&oc, &c->coarse);
+    s = create_ctx(&oc, true, &c->coarse);
     if (s != CLAIRE_OK) {
       c->coarse = nullptr;
       claire_destroy(c);
@@ -1384,6 +2092,7 @@ claire_status claire_create(const claire_opts* opts, claire_ctx** out) {
   *out = c;
   return CLAIRE_OK;
 }
+}  // namespace
 
 claire_status claire_profile_enable(claire_ctx* c, int on) {
   if (!c) return CLAIRE_EINVAL;
@@ -1431,12 +2140,17 @@ claire_status claire_destroy(claire_ctx* c) {
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
   if (c->pcg_cap_stream) cudaStreamDestroy(c->pcg_cap_stream);
+  gn_graph_release(c);
+  if (c->gn_dev) cudaFree(c->gn_dev);
+  for (cudaStream_t s : c->gn_cap_streams)
+    if (s) cudaStreamDestroy(s);
   for (auto& r : c->prof_recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
   if (c->arena) cudaFree(c->arena);
+  if (c->hostbuf) cudaFree(c->hostbuf);
   if (c->hscal) cudaFreeHost(c->hscal);
   delete c;
   return CLAIRE_OK;
@@ -1454,6 +2168,8 @@ claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   out->halo_x_heavy = c->haloXh;
   out->halo_y_heavy = c->haloYh;
   out->pcg_graph_runs = c->pcg_graph_runs;
+  out->tma_steps = c->tma_steps + (c->coarse ? c->coarse->tma_steps : 0);
+  out->gn_graph_runs = c->gn_graph_runs;
   return CLAIRE_OK;
 }
 
@@ -1556,6 +2272,10 @@ claire_status claire_register_batch_f32(const claire_opts* base, claire_pair_f32
   if (base->precision != CLAIRE_F32) return CLAIRE_EINVAL;
   for (int i = 0; i < npairs; ++i)
     if (!pairs[i].mT || !pairs[i].mR || !pairs[i].v) return CLAIRE_EINVAL;
+  {
+    const char* gm = std::getenv("CLAIRE_GN");
+    if (!(gm && std::strcmp(gm, "host") == 0) && base->precond == 0) return register_batch_device(base, pairs, npairs, nworkers);
+  }
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return CLAIRE_ECUDA;
   // largest grids first (longest-processing-time order over the workers)
@@ -1617,6 +2337,7 @@ claire_status claire_register_batch_f32(const claire_opts* base, claire_pair_f32
       }
       for (auto e : c->prof_pool) cudaEventDestroy(e);
       cudaFree(c->arena);
+      if (c->hostbuf) cudaFree(c->hostbuf);
       cudaFreeHost(c->hscal);
       delete c;
     }

@@ -470,10 +470,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_sp_project_dot(
 // partial sum_k w a(k) |Vtr|^2 (the regularisation value)
 template <class T>
 __global__ void __launch_bounds__(256) k_sp_trial(const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ Vt,
-                                                  cplx<T>* __restrict__ Vtr, cplx<T>* __restrict__ Sc, T alpha,
-                                                  int regnorm, int kmode, T rw, Dims d,
-                                                  double* __restrict__ partials) {
+                                                  cplx<T>* __restrict__ Vtr, cplx<T>* __restrict__ Sc, T alpha_h,
+                                                  const double* __restrict__ alpha_dev, int regnorm, int kmode, T rw,
+                                                  Dims d, double* __restrict__ partials) {
   const long long s = d.Ns;
+  const T alpha = alpha_dev ? T(*alpha_dev) : alpha_h;
   Acc<T> acc[1];
   HLOOP {
     const HWave h = hwave(j, d);
@@ -804,10 +805,10 @@ claire_status sp_project_dot(claire_ctx* c, const cplx<T>* G, cplx<T>* Vt, doubl
 }
 template <class T>
 claire_status sp_trial(claire_ctx* c, const cplx<T>* V, const cplx<T>* Vt, cplx<T>* Vtr, cplx<T>* Sc, double alpha,
-                       double* partials, cudaStream_t st) {
+                       double* partials, cudaStream_t st, const double* alpha_dev) {
   c->prof_begin("sp_trial", st);
-  k_sp_trial<T><<<kReduceBlocks, 256, 0, st>>>(V, Vt, Vtr, Sc, T(alpha), c->o.regnorm, kmode_of(c), T(rw_of(c)), c->d,
-                                               partials);
+  k_sp_trial<T><<<kReduceBlocks, 256, 0, st>>>(V, Vt, Vtr, Sc, T(alpha), alpha_dev, c->o.regnorm, kmode_of(c),
+                                               T(rw_of(c)), c->d, partials);
   CL_LAUNCHED(c);
   return CLAIRE_OK;
 }
@@ -886,7 +887,7 @@ claire_status tl_dir(claire_ctx* c, const cplx<T>* Z, cplx<T>* S, double mu, dou
                                        const double*);                                                           \
   template claire_status sp_project_dot<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double*, cudaStream_t);        \
   template claire_status sp_trial<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, double,      \
-                                     double*, cudaStream_t);                                                     \
+                                     double*, cudaStream_t, const double*);                                      \
   template claire_status sp_copy_reg<T>(claire_ctx*, const cplx<T>*, cplx<T>*, double*, cudaStream_t);          \
   template claire_status spec_grad<T>(claire_ctx*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, cudaStream_t);  \
   template claire_status spec_div<T>(claire_ctx*, const cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*,      \

@@ -296,6 +296,32 @@ def test_gather_schedules_match_the_oracle(schedule, n, monkeypatch):
         assert rel(m1, lin.m[-1]) < TOL["f32"]
 
 
+@pytest.mark.parametrize("case", [dict(regnorm=2, divfree=True), dict(regnorm=2, divfree=True, bf16_mask=1)])
+@pytest.mark.parametrize("n", [(48, 40, 64), (36, 20, 32)])
+def test_tma_staged_adjoint_steps_are_bit_identical(n, case, monkeypatch):
+    """The accumulating adjoint steps with their operands staged by TMA (the default wherever the bricks run and
+    n3 is a multiple of 16) against the same steps with per-thread loads (CLAIRE_TMA=0): the same solve, bit for
+    bit, with the bricks forced; on 36 x 20 x 32 the tiles along i2 and i1 are partial (TMA fills and clips)."""
+    monkeypatch.setenv("CLAIRE_GATHER", "tiled")
+    kw = dict(beta=1e-3, nt=4, gtol_rel=1e-2, max_gn=3, **case)
+    mT = I.brain_phantom(n, 0)
+    vs = I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=3.0, divfree=True)
+    runs = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("CLAIRE_TMA", mode)
+        with ctx(n, "f32", **kw) as c:
+            mR = c.transport(dev(mT, "f32"), dev(vs, "f32"), +1)
+            v, rep, st = c.register(dev(mT, "f32"), mR)
+            vt = dev(I.random_velocity(n, seed=5, kmax=4, amplitude=1.0, divfree=True), "f32")
+            hd = c.hessvec_data(vt)
+            g = c.gradient(dev(mT, "f32"), mR, v)
+            runs[mode] = (v.cpu(), rep, hd.cpu(), g.cpu())
+            assert (c.tma_steps() > 0) == (mode == "1")
+    (v0, r0, h0, g0), (v1, r1, h1, g1) = runs["0"], runs["1"]
+    assert r0["gn_iters"] == r1["gn_iters"] and r0["matvecs"] == r1["matvecs"]
+    assert torch.equal(v0, v1) and torch.equal(h0, h1) and torch.equal(g0, g1)
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_inner_product_fp64_accumulation(prec):
     n = (40, 36, 42)
@@ -381,6 +407,52 @@ def test_device_driven_pcg_graph_is_bit_identical_to_the_host_loop(prec, problem
     for k in ("gn_iters", "matvecs", "pde_solves", "ls_trials", "pcg_breakdowns", "converged"):
         assert rh[k] == rg[k], k
     assert torch.equal(vh, vg)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("problem", ["cfg0", "h2_divfree", "h1div", "max_gn", "armijo_fails"])
+def test_device_driven_solve_is_bit_identical_to_the_host_loop(prec, problem, monkeypatch):
+    """The whole zero-start solve as one CUDA graph launch (Alg. 1 and Alg. 2 as conditional nodes, every scalar
+    decision on the device; CLAIRE_GN=device) against the host-driven loop: same iterates bit for bit, same counts
+    and the same status, also when the solve stops at max_gn (ENOTCONV) or in a failed Armijo search
+    (ELINESEARCH, v = the last accepted iterate, here 0)."""
+    if problem in ("cfg0", "max_gn", "armijo_fails"):
+        p, kw, mT, mR = cfg0(n=(24, 20, 16))
+        if problem == "max_gn":
+            kw = dict(kw, max_gn=1, pcg_rtol=0.0, gtol_rel=1e-3)
+        elif problem == "armijo_fails":
+            kw = dict(kw, armijo_c1=0.9, max_ls=2)
+    elif problem == "h2_divfree":
+        n = (32, 32, 32)
+        kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, max_gn=4, gtol_rel=1e-2)
+        mT = I.brain_phantom(n, 0)
+        mR = O.transport(O.Problem(n, **kw), mT, I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=2.0,
+                                                                   divfree=True), +1)
+    else:
+        n = (32, 32, 32)
+        kw = dict(beta=1e-3, nt=4, regnorm=1, beta_w=1e-4, gtol_rel=1e-2)
+        mT, vs = I.paper_synthetic(n)
+        mR = O.transport(O.Problem(n, **kw), mT, vs, +1)
+    n = tuple(mT.shape)
+    runs = {}
+    for mode in ("host", "device"):
+        monkeypatch.setenv("CLAIRE_GN", mode)
+        with ctx(n, prec, **kw) as c:
+            v, rep, status = c.register(dev(mT, prec), dev(mR, prec))
+            runs[mode] = (v.cpu(), rep, status, c.gn_graph_runs())
+    (vh, rh, sh, gh), (vd, rd, sd, gd) = runs["host"], runs["device"]
+    print(problem, prec, sh, {k: rh[k] for k in ("gn_iters", "matvecs", "ls_trials")})
+    assert gh == 0 and gd == 1
+    assert sh == sd
+    for k in ("gn_iters", "matvecs", "pde_solves", "ls_trials", "pcg_breakdowns", "converged"):
+        assert rh[k] == rd[k], k
+    for k in ("J", "J0", "gnorm", "gnorm0", "mismatch", "mismatch0"):
+        assert rh[k] == rd[k], k
+    assert torch.equal(vh, vd)
+    if problem == "max_gn":
+        assert sh == "ENOTCONV"
+    if problem == "armijo_fails":
+        assert sh == "ELINESEARCH" and float(vd.abs().max()) == 0.0
 
 
 def test_degenerate_identical_images_converge_immediately():

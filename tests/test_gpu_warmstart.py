@@ -305,6 +305,52 @@ def test_training_set_and_short_training(ws_mod):
     ws.close()
 
 
+def test_trained_network_saves_gauss_newton_work_on_held_out_pairs(ws_mod):
+    """What the learned warm start gains over the method without it. The network is trained on (m_T, m_R, v)
+    triples that the plain solver makes (384 seeded phantom pairs on 64^3, H2, beta 1e-3, div v = 0, to
+    ||g|| <= 1e-2 ||g(v = 0)||; network grid 32^3, 2000 Adam steps with cube-symmetry augmentation). On 16
+    held-out pairs (unseen phantoms and velocities) the unchanged solver then runs from v = 0 and from the
+    prediction (low-passed to |k_i| <= 4). Both stop by the same rule of Sec. 2.3.2 with the same reference
+    ||g(v = 0)||; the warm start must need fewer Gauss-Newton matvecs on average, no more GN steps, and reach the
+    same final mismatch (mean relative difference within 0.5%)."""
+    import claire_inputs as I
+    from paper_1808_04487_gb300 import Context
+    n, n_net = (64, 64, 64), (32, 32, 32)
+    images, targets, stats = ws_mod.make_training_set(384, n_solve=n, n_net=n_net, seed=0, phantoms=32, chunk=64)
+    assert stats["converged"] == 384
+    rms = float(targets.pow(2).mean().sqrt())
+    ws = ws_mod.WarmStart(n=n_net, batch=8, vscale=1.0 / rms, seed=0)
+    ws_mod.train(ws, images, targets, 2000, lr=2e-3, lr_final=1e-4, seed=0, augment=True)
+    del images, targets
+    ctx = Context(n, "f32", beta=1e-3, regnorm=2, divfree=True, nt=4, gtol_rel=1e-2)
+    ctx_n = Context(n_net, "f32")
+    disp_net = 8.0 * max(n) / 256.0 * max(n_net) / max(n)
+    zero, warm = [], []
+    for j in range(16):
+        mT = torch.from_numpy(I.brain_phantom(n, seed=500009 + 7 * j)).float().cuda()
+        vs = I.random_velocity(n_net, seed=900001 + 13 * j, kmax=6, max_disp_voxels=disp_net, divfree=True)
+        vs = ctx_n.resample_to(ctx, torch.from_numpy(vs).float().cuda().contiguous())
+        mR = ctx.transport(mT, vs, +1)
+        _, rz, sz = ctx.register(mT, mR)
+        v0 = ws.predict(ctx, mT, mR, kmax=4)
+        _, rw, sw = ctx.register(mT, mR, v0.clone())
+        assert sz == "OK" and sw == "OK"
+        assert abs(rw["gnorm0"] - rz["gnorm0"]) <= 1e-6 * rz["gnorm0"]  # the same reference gradient
+        assert rw["gnorm"] <= 1e-2 * rw["gnorm0"] and rz["gnorm"] <= 1e-2 * rz["gnorm0"]
+        zero.append(rz)
+        warm.append(rw)
+    mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
+    dmis = float(np.mean([w["mismatch"] / z["mismatch"] - 1.0 for w, z in zip(warm, zero)]))
+    print("held-out 64^3: zero start %.2f GN / %.2f matvecs, warm start %.2f GN / %.2f matvecs, mismatch %+.4f"
+          % (mean(zero, "gn_iters"), mean(zero, "matvecs"), mean(warm, "gn_iters"), mean(warm, "matvecs"), dmis))
+    assert mean(warm, "matvecs") < mean(zero, "matvecs")
+    assert mean(warm, "gn_iters") <= mean(zero, "gn_iters")
+    assert abs(dmis) <= 5e-3
+    ws.close()
+    ctx.close()
+    ctx_n.close()
+
+
 def test_restart_from_truncated_solution_256():
     """At 256^3 with H2 and div v = 0, a restart from the zero-start solution truncated to 32^3 converges in a
     few Gauss-Newton steps (it needs the projection of the guess: its rounding error has a curl-free part that
