@@ -596,6 +596,17 @@ def batch_study(args):
         res["device_graph_contexts_per_grid_%d" % nw] = {
             "seconds": dt, "pairs_per_s": len(pairs) / dt, "converged": sum(1 for r, st in out if r["converged"]),
             "matvecs": sum(r["matvecs"] for r, st in out), "bit_identical_to_sequential": bool(same)}
+    # the device-driven form with bricks of halo 3 (room for 2 voxels per time step; larger bricks and staged
+    # operands per CTA) instead of the default 2
+    os.environ["CLAIRE_GN_HALO"] = "3"
+    pkg.register_batch(pairs[: min(8, len(pairs))], nworkers=2, **kw)
+    for _, _, v in pairs:
+        v.zero_()
+    out, dt = timed(lambda: pkg.register_batch(pairs, nworkers=2, **kw))
+    del os.environ["CLAIRE_GN_HALO"]
+    res["device_graph_contexts_per_grid_2_halo3"] = {
+        "seconds": dt, "pairs_per_s": len(pairs) / dt,
+        "bit_identical_to_sequential": bool(all(torch.equal(p[2], vs) for p, vs in zip(pairs, v_seq)))}
     # the earlier batched form for comparison: host worker threads, host-driven Gauss-Newton loops
     os.environ["CLAIRE_GN"] = "host"
     pkg.register_batch(pairs[: min(8, len(pairs))], nworkers=4, **kw)

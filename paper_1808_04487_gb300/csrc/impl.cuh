@@ -10,11 +10,11 @@
 
 namespace claire {
 
-// TMA tensor maps of the operands the staged adjoint steps load (sl_tma.cu): boxes of 16 x 16 x 4 nodes x 3
-// components of Y, the gradient history (FP32 or BF16, with the time index as a fifth dimension) and b; built
-// once per context for the workspace arrays they describe
+// TMA tensor maps of the operands the staged adjoint and incremental-state steps load (sl_tma.cu): boxes of
+// 16 x 16 x 4 nodes x 3 components of Y, X, the PCG direction s, the gradient history (FP32 or BF16, with the time
+// index as a fifth dimension) and b; built once per context for the workspace arrays they describe
 struct TmaMaps {
-  CUtensorMap dY, gm, gm16, b;
+  CUtensorMap dY, dX, s, gm, gm16, b;
   const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
   bool tried = false, ok = false;
 };
@@ -325,6 +325,10 @@ bool sl_tma_prepare(claire_ctx* c);
 // sv (optional): also part[block] = partial <sv, b_final> (the fused product of PCG's <s, H s>)
 claire_status sl_adjoint_step_tma(claire_ctx* c, const float* lam_next, float* lam, int j, float w,
                                   const float* sv, double* part, int H, cudaStream_t st);
+// the incremental state step with TMA-staged operands (FP32, brick halo 2..5, no div source; X, vt = s, the
+// gradient history and b must be the context's own arrays)
+claire_status sl_incstate_step_tma(claire_ctx* c, const float* q, float* qout, int j, bool last, float hdt, float w,
+                                   int H, cudaStream_t st);
 // CLAIRE_ETIMEOUT (and clears the flag) if a staged step's bounded wait ran out since the last call
 claire_status sl_tma_take_error(claire_ctx* c);
 // launch shape of the gather kernels: 256 threads, x along i3 (up to 64 wide), y along i2, z = i1

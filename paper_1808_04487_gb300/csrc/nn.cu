@@ -18,6 +18,9 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
 
 #include "impl.cuh"
 #include "nn.cuh"
@@ -582,6 +585,120 @@ inline int fwd_offsets_per_split(const Geo& g) {
 }
 inline size_t wgrad_smem(int Cout) { return 1024 + 2 * (size_t(kTileM) * kTileK * 2 + size_t(Cout) * kTileK * 2) + 32; }
 
+// ---- forward convolution from a shared-memory halo -----------------------------------------------------------
+// A CTA covers a tile of 8 (i3) x 16 (i2) voxels of one i1 plane of one sample (128 rows of the implicit GEMM).
+// Its input halo -- the 10 x 18 x 3 voxels around the tile, periodic -- is loaded once, as Cin/8 planes of 16-byte
+// voxel rows (8 channels each): [plane][hz][hy][hx] x 16 B. In that layout the A operand of every neighbour offset
+// is a shifted view of the halo that a matrix descriptor expresses directly -- core matrix (row group g, channel
+// group j) at plane j, rows (o1, g + o2, o3 .. o3 + 7): leading (K) byte offset = one plane, stride (M) byte offset =
+// one halo row of 10 voxels = 160 B -- so no per-offset staging is needed: one thread issues the 27 Cin / 16 MMAs
+// back to back against the resident weights (K-major [Cout][27 Cin]). The MMAs run in the K order of
+// k_conv3_fwd_tc (offsets ascending, 16 channels at a time), so the accumulator and the result are the same.
+constexpr int kHaloRows = 3 * 18 * 10;
+constexpr uint32_t kHaloPlane = kHaloRows * 16;
+
+inline size_t halo_smem(int Cin, int Cout) {
+  const size_t halo = (size_t(Cin / 8) * kHaloPlane + 1023) / 1024 * 1024;
+  return 1024 + halo + size_t(Cout) * 27 * Cin * 2 + 64;
+}
+inline bool halo_fits(const Geo& g, int Cin, int Cout) {
+  return Cin % 16 == 0 && Cin <= 64 && g.n3 % 8 == 0 && g.n2 % 16 == 0 && 27LL * Cout * Cin * 2 <= 110592 &&
+         halo_smem(Cin, Cout) <= 227 * 1024;
+}
+
+__global__ void __launch_bounds__(128, 1) k_conv3_fwd_halo(const bf16* __restrict__ x, const bf16* __restrict__ w,
+                                                           const float* __restrict__ bias,
+                                                           const bf16* __restrict__ skip, bf16* __restrict__ y,
+                                                           float* __restrict__ yf, int accum, Geo g, int Cin, int Cout,
+                                                           int relu) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
+  const int nplanes = Cin / 8;
+  const int K = 27 * Cin;
+  unsigned char* halo = sm;
+  unsigned char* Bs = sm + (size_t(nplanes) * kHaloPlane + 1023) / 1024 * 1024;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(Bs + size_t(Cout) * K * 2);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tc::tmem_cols(Cout);
+  const uint32_t b0 = tc::smem_addr(bar);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
+  if (tid == 0) tc::mbar_init(b0, 1);
+  // the tile: blockIdx.x = ((b n1 + z) ty + iy) tx + ix
+  const int tx = g.n3 / 8, ty = g.n2 / 16;
+  int t = blockIdx.x;
+  const int ix = t % tx;
+  t /= tx;
+  const int iy = t % ty;
+  t /= ty;
+  const int z = t % g.n1, b = t / g.n1;
+  const int x0 = 8 * ix, y0 = 16 * iy;
+  for (int q = tid; q < nplanes * kHaloRows; q += 128) {
+    const int cc = q / kHaloRows, r = q - cc * kHaloRows;
+    const int hz = r / 180, rr = r - hz * 180;
+    const int hy = rr / 10, hx = rr - hy * 10;
+    const int gz = pw(z + hz - 1, g.n1), gy = pw(y0 + hy - 1, g.n2), gx = pw(x0 + hx - 1, g.n3);
+    const long long vox = ((long long)(b * g.n1 + gz) * g.n2 + gy) * g.n3 + gx;
+    *reinterpret_cast<uint4*>(halo + (size_t(cc) * kHaloRows + r) * 16) =
+        *reinterpret_cast<const uint4*>(x + vox * Cin + 8 * cc);
+  }
+  const int nv = K / 8;
+  for (int q = tid; q < Cout * nv; q += 128) {
+    const int co = q / nv, c = q - co * nv;
+    *reinterpret_cast<uint4*>(Bs + tc::kmajor_offset(co, 8 * c, K)) =
+        *reinterpret_cast<const uint4*>(w + (long long)co * K + 8 * c);
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    const uint32_t idesc = tc::idesc_bf16(kTileM, Cout);
+    const uint32_t hbase = tc::smem_addr(halo), bbase = tc::smem_addr(Bs);
+    const int kpo = Cin / 16;  // MMAs per offset
+    for (int off = 0; off < 27; ++off) {
+      const int o1 = off / 9, o2 = (off / 3) % 3, o3 = off % 3;
+      const uint32_t row0 = (uint32_t)((o1 * 18 + o2) * 10 + o3);
+      for (int kk = 0; kk < kpo; ++kk) {
+        const uint64_t ad = tc::smem_desc(hbase + 2u * kk * kHaloPlane + 16u * row0, kHaloPlane, 160u);
+        const uint64_t bd = tc::smem_desc(bbase + 256u * (off * kpo + kk), 128u, 16u * K);
+        tc::mma_bf16(tmem, ad, bd, idesc, (off > 0 || kk > 0) ? 1u : 0u);
+      }
+    }
+    tc::commit(b0);
+  }
+  bool ok = tc::mbar_wait(b0, 0, kWaitCycles);
+  ok = __syncthreads_and(ok) != 0;
+  tc::fence_after();
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_nn_error, 1);
+    tc::mbar_wait(b0, 0, kWaitCycles);  // whatever is still in flight, bounded
+  } else {
+    const int r = 32 * warp + lane;  // this lane's accumulator row: voxel (x0 + r % 8, y0 + r / 8)
+    const long long m = ((long long)(b * g.n1 + z) * g.n2 + y0 + (r >> 3)) * g.n3 + x0 + (r & 7);
+    for (int c0 = 0; c0 < Cout; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int co = c0 + j;
+        const long long o = m * Cout + co;
+        float val = v[j];
+        if (bias) val += bias[co];
+        if (skip) val += __bfloat162float(skip[o]);
+        if (relu) val = fmaxf(val, 0.f);
+        if (y) y[o] = __float2bfloat16_rn(val);
+        if (yf) yf[o] = accum ? yf[o] + val : val;
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+
 }  // namespace
 
 size_t fwd_work_elems(const Geo& g, int Cout) {
@@ -598,6 +715,20 @@ cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf1
   const unsigned tiles = (unsigned)((g.M + kTileM - 1) / kTileM);
   const int per = work ? fwd_offsets_per_split(g) : 27;
   const int nsplit = (27 + per - 1) / per;
+  const char* conv_env = std::getenv("CLAIRE_CONV");
+  if (nsplit == 1 && halo_fits(g, Cin, Cout) && !(conv_env && std::strcmp(conv_env, "gather") == 0)) {
+    // the same MMAs from a shared-memory halo (k_conv3_fwd_halo): no per-offset gather
+    static std::once_flag once;
+    static cudaError_t hattr = cudaSuccess;
+    std::call_once(once, [] {
+      hattr = cudaFuncSetAttribute(k_conv3_fwd_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    if (hattr != cudaSuccess) return hattr;
+    const unsigned htiles = (unsigned)((g.n3 / 8) * (g.n2 / 16) * g.n1 * g.B);
+    k_conv3_fwd_halo<<<htiles, kTileM, halo_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf, accum, g, Cin, Cout,
+                                                                    relu);
+    return cudaGetLastError();
+  }
   if (nsplit == 1) {
     k_conv3_fwd_tc<<<dim3(tiles, 1u), kTileM, fwd_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf, accum, g, Cin,
                                                                          Cout, relu, 27, fwd_group(Cin), nullptr);

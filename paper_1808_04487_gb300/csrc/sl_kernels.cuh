@@ -239,6 +239,8 @@ __device__ __forceinline__ void load_bricks(T* sm, const T* __restrict__ f0, con
   const T* g1 = f1 ? f1 + ((tl.z0 - H) * d.n2 + (tl.y0 - H)) * d.n3 + (tl.x0 - G::xa) : nullptr;
   // 16-byte copies: FP32, rows of a multiple of 4 words, fields on 16-byte boundaries
   const bool vec = sizeof(T) == 4 && (d.n3 & 3) == 0 && ((reinterpret_cast<uintptr_t>(f0) | reinterpret_cast<uintptr_t>(f1)) & 15) == 0;
+  // the brick's rows lie inside the box along i3 (only their i1, i2 indices may wrap)
+  const bool x_in = tl.x0 - G::xa >= 0 && tl.x0 - G::xa + G::ex <= d.n3;
   if (tl.interior && vec) {
     constexpr int nv = G::ex * (int)sizeof(T) / 16;  // 16-byte vectors per row
     const int tid = threadIdx.y * kTX + threadIdx.x;
@@ -248,6 +250,18 @@ __device__ __forceinline__ void load_bricks(T* sm, const T* __restrict__ f0, con
       const int goff = z * d.n2 * d.n3 + y * d.n3 + 4 * v;
       cp_async_16(sm + row * G::px + 4 * v, g0 + goff);
       if (f1) cp_async_16(sm + G::vol + row * G::px + 4 * v, g1 + goff);
+    }
+  } else if (x_in && vec) {
+    // a tile on an i1 or i2 face: whole 16-byte copies of rows whose row index wraps
+    constexpr int nv = G::ex * (int)sizeof(T) / 16;
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    for (int q = tid; q < rows * nv; q += kTX * kTY) {
+      const int row = q / nv, v = q - row * nv;
+      const int z = row / G::ey, y = row - z * G::ey;
+      const int gz = wrapc(tl.z0 - H + z, d.n1), gy = wrapc(tl.y0 - H + y, d.n2);
+      const int goff = (gz * d.n2 + gy) * d.n3 + (tl.x0 - G::xa) + 4 * v;
+      cp_async_16(sm + row * G::px + 4 * v, f0 + goff);
+      if (f1) cp_async_16(sm + G::vol + row * G::px + 4 * v, f1 + goff);
     }
   } else if (tl.interior) {
 #pragma unroll 2

@@ -124,6 +124,76 @@ __global__ void __launch_bounds__(256, 3)
   if (tid == 0) tma::store_wait_read();
 }
 
+// Incremental state step (Eq. (8), Sec. 2.3.1) with X, vt and grad m^{j+1} staged by TMA:
+// m~^{j+1}(x) = q^j(X) + dt/2 f^{j+1}(x), f = -vt . grad m; not last: q^{j+1} = m~^{j+1} + dt/2 f^{j+1};
+// last: lambda~ = -m~(1), b = w lambda~ grad m^{nt} (written into the staging slots of X, then one TMA store).
+// Same arithmetic in the same order as k_inc_step.
+template <int H, bool LAST, class G>
+__global__ void __launch_bounds__(256, 3)
+    k_inc_step_tma(const float* __restrict__ q, float* __restrict__ qout, const __grid_constant__ CUtensorMap mX,
+                   const __grid_constant__ CUtensorMap mV, const __grid_constant__ CUtensorMap mG,
+                   const __grid_constant__ CUtensorMap mB, int j, float hdt, float w, Dims d) {
+  using L = StageLayout<H, G>;  // [brick][X][grad m][vt] (the b slot of the adjoint layout holds vt)
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  float* brick = reinterpret_cast<float*>(sm_raw);
+  float* sX = reinterpret_cast<float*>(sm_raw + L::y);
+  const G* sG = reinterpret_cast<const G*>(sm_raw + L::g);
+  const float* sV = reinterpret_cast<const float*>(sm_raw + L::b);
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const Tile tl = tile_of<H>(d);
+  const uint32_t b = tma::smem_addr(&bar);
+  if (tid == 0) tc::mbar_init(b, 1);
+  __syncthreads();
+  if (tid == 0) {
+    tma::expect_tx(b, L::tx_bytes());
+    tma::load4(tma::smem_addr(sm_raw + L::y), &mX, tl.x0, tl.y0, tl.z0, 0, b);
+    tma::load5(tma::smem_addr(sm_raw + L::g), &mG, tl.x0, tl.y0, tl.z0, 0, j, b);
+    tma::load4(tma::smem_addr(sm_raw + L::b), &mV, tl.x0, tl.y0, tl.z0, 0, b);
+  }
+  load_bricks<float, H>(brick, q, (const float*)nullptr, tl, d);
+  __syncthreads();
+  const bool ok = tc::mbar_wait(b, 0, kWaitCycles);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(&g_sl_tma_error, 1);
+    tc::mbar_wait(b, 0, kWaitCycles);
+    return;
+  }
+#pragma unroll 1
+  for (int tz = 0; tz < kTZ; ++tz) {
+    const int i1 = tl.z0 + tz, i2 = tl.y0 + threadIdx.y, i3 = tl.x0 + threadIdx.x;
+    if (i1 < d.n1 && i2 < d.n2 && i3 < d.n3) {
+      const int s = (tz * kTY + threadIdx.y) * kTX + threadIdx.x;
+      const int idx = (i1 * d.n2 + i2) * d.n3 + i3;
+      Stencil<float> st;
+      stencil_at<float>(i1, i2, i3, sX[s], sX[kTileNodes + s], sX[2 * kTileNodes + s], d, st);
+      const float g1 = as_f32<G>(sG[s]), g2 = as_f32<G>(sG[kTileNodes + s]), g3 = as_f32<G>(sG[2 * kTileNodes + s]);
+      const float f = -(sV[s] * g1 + sV[kTileNodes + s] * g2 + sV[2 * kTileNodes + s] * g3);
+      const float mt = sample<float, H>(q, brick, 0, tl, st, d) + hdt * f;
+      if (!LAST) {
+        qout[idx] = mt + hdt * f;
+      } else {
+        const float l = -mt;
+        qout[idx] = l;
+        const float wl = w * l;
+        // this thread's X slots are read; they now take b
+        sX[s] = wl * g1;
+        sX[kTileNodes + s] = wl * g2;
+        sX[2 * kTileNodes + s] = wl * g3;
+      }
+    }
+  }
+  if (LAST) {
+    tma::fence_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tma::store4(&mB, tma::smem_addr(sX), tl.x0, tl.y0, tl.z0, 0);
+      tma::store_commit();
+      tma::store_wait_read();
+    }
+  }
+}
+
 // ---- tensor maps ---------------------------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static std::once_flag once;
@@ -168,6 +238,9 @@ template <int H, class G> cudaError_t set_all_smem() {
   cudaError_t e = set_smem<H, true, false, G>();
   if (e == cudaSuccess) e = set_smem<H, false, false, G>();
   if (e == cudaSuccess) e = set_smem<H, false, true, G>();
+  for (const void* fn : {(const void*)k_inc_step_tma<H, false, G>, (const void*)k_inc_step_tma<H, true, G>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageLayout<H, G>::bytes());
   return e;
 }
 
@@ -186,13 +259,45 @@ void launch(bool store, bool dot, const float* lam_next, float* lam, const float
     k_adj_step_tma<H, false, false, G><<<grid, block, smem, st>>>(lam_next, lam, M.dY, mG, M.b, sv, j, w, d, part);
 }
 
+template <int H, class G>
+void launch_inc(bool last, const float* q, float* qout, const TmaMaps& M, int j, float hdt, float w, const Dims& d,
+                cudaStream_t st) {
+  dim3 grid, block;
+  tiled_shape<H>(d, grid, block);
+  const CUtensorMap& mG = std::is_same<G, float>::value ? M.gm : M.gm16;
+  const size_t smem = StageLayout<H, G>::bytes();
+  if (last)
+    k_inc_step_tma<H, true, G><<<grid, block, smem, st>>>(q, qout, M.dX, M.s, mG, M.b, j, hdt, w, d);
+  else
+    k_inc_step_tma<H, false, G><<<grid, block, smem, st>>>(q, qout, M.dX, M.s, mG, M.b, j, hdt, w, d);
+}
+
 }  // namespace
+
+claire_status sl_incstate_step_tma(claire_ctx* c, const float* q, float* qout, int j, bool last, float hdt, float w,
+                                   int H, cudaStream_t st) {
+  auto go = [&](auto hc) {
+    constexpr int HC = decltype(hc)::value;
+    if (c->gm16_on)
+      launch_inc<HC, __nv_bfloat16>(last, q, qout, c->tma, j, hdt, w, c->d, st);
+    else
+      launch_inc<HC, float>(last, q, qout, c->tma, j, hdt, w, c->d, st);
+  };
+  switch (H) {
+    case 2: go(std::integral_constant<int, 2>()); break;
+    case 3: go(std::integral_constant<int, 3>()); break;
+    case 4: go(std::integral_constant<int, 4>()); break;
+    case 5: go(std::integral_constant<int, 5>()); break;
+    default: c->set_error("sl_incstate_step_tma: unsupported halo"); return CLAIRE_EINVAL;
+  }
+  return CLAIRE_OK;
+}
 
 bool sl_tma_prepare(claire_ctx* c) {
   Work<float>& W = c->work<float>();
   TmaMaps& M = c->tma;
   const Dims& d = c->d;
-  const void* key[4] = {W.dY, c->gm16_on ? W.gm16 : (const void*)W.gm, W.b, nullptr};
+  const void* key[4] = {W.dY, c->gm16_on ? W.gm16 : (const void*)W.gm, W.b, W.dX};
   if (M.tried && std::memcmp(key, M.key, sizeof(key)) == 0) return M.ok;
   M.tried = true;
   std::memcpy(M.key, key, sizeof(key));
@@ -212,7 +317,8 @@ bool sl_tma_prepare(claire_ctx* c) {
     cudaGetLastError();
     return false;
   }
-  bool ok = encode(&M.dY, W.dY, d, 4, 0) && encode(&M.b, W.b, d, 4, 0);
+  bool ok = encode(&M.dY, W.dY, d, 4, 0) && encode(&M.b, W.b, d, 4, 0) && encode(&M.dX, W.dX, d, 4, 0) &&
+            encode(&M.s, W.s, d, 4, 0);
   if (c->gm16_on)
     ok = ok && encode(&M.gm16, W.gm16, d, 2, c->o.nt + 1);
   else

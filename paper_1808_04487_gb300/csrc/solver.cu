@@ -1214,11 +1214,19 @@ template <class T> claire_status ensure_hostbuf(claire_ctx* c) {
   return CLAIRE_OK;
 }
 
-// Halos of a solve driven from the device, fixed before capture: 3 (departure points up to 2 voxels per time step
-// stay inside the bricks; farther ones fall back to global taps node by node), or global taps for a kernel class
-// where the autotuner has preferred them on this grid; CLAIRE_GATHER=plain|tiled overrides as elsewhere.
+// Halos of a solve driven from the device, fixed before capture: 2 (departure points up to 1 voxel per time step
+// stay inside the bricks; farther ones fall back to global taps node by node; CLAIRE_GN_HALO=2..5 picks another;
+// measured on the 64-pair batch: 1.047 s at halo 2 against 1.076 s at halo 3, whose larger bricks and staged
+// operands leave two CTAs per SM instead of three),
+// or global taps for a kernel class where the autotuner has preferred them on this grid; CLAIRE_GATHER=plain|tiled
+// overrides as elsewhere.
 template <class T> claire_status gn_fix_halos(claire_ctx* c, cudaStream_t st) {
-  const int H = sizeof(T) == 4 ? 3 : -1;
+  int H = sizeof(T) == 4 ? 2 : -1;
+  const char* hv = std::getenv("CLAIRE_GN_HALO");  // another fixed halo (2..5)
+  if (hv && sizeof(T) == 4) {
+    const int h = std::atoi(hv);
+    if (h >= 2 && h <= 5) H = h;
+  }
   c->haloX = c->haloXh = c->haloY = c->haloYh = H;
   const char* force = std::getenv("CLAIRE_GATHER");
   if (force && std::strcmp(force, "plain") == 0) {

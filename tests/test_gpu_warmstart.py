@@ -47,9 +47,13 @@ def host(t):
 
 CONV_CASES = [((2, 6, 5, 8), 16, 16), ((1, 3, 4, 4), 32, 48), ((2, 6, 5, 8), 64, 128), ((1, 8, 6, 10), 128, 64),
               ((3, 4, 4, 4), 48, 80), ((1, 4, 8, 6), 16, 112), ((2, 4, 2, 6), 96, 32)]
+# grids whose forward convolution runs from a shared-memory halo (n3 a multiple of 8, n2 of 16, Cin <= 64, the
+# weights within 108 KB)
+HALO_CASES = [((2, 4, 16, 8), 16, 16), ((1, 3, 16, 16), 32, 64), ((2, 2, 32, 8), 64, 32), ((1, 4, 16, 8), 16, 128),
+              ((1, 2, 16, 24), 48, 16)]
 
 
-@pytest.mark.parametrize("shape,cin,cout", CONV_CASES)
+@pytest.mark.parametrize("shape,cin,cout", CONV_CASES + HALO_CASES)
 def test_conv3_forward(ws_mod, shape, cin, cout):
     r = np.random.default_rng(cin * 1000 + cout)
     xg, x = bf16(r.standard_normal(shape + (cin,)))
@@ -72,7 +76,31 @@ def test_conv3_forward(ws_mod, shape, cin, cout):
     assert np.all(np.abs(host(acc) - ref2) <= 4e-5 * (mag + np.abs(host(base))))
 
 
-@pytest.mark.parametrize("shape,cin,cout", CONV_CASES[:5])
+@pytest.mark.parametrize("shape,cin,cout", HALO_CASES)
+def test_conv3_forward_from_halo_is_bit_identical_to_the_gather_kernel(ws_mod, shape, cin, cout, monkeypatch):
+    """The forward convolution from a shared-memory halo (A operands as descriptors into the halo) against the
+    kernel that gathers each offset's neighbour rows (CLAIRE_CONV=gather): the same MMAs in the same K order, so the
+    same bits, with bias, skip, ReLU and FP32 accumulation."""
+    r = np.random.default_rng(7 + cin + cout)
+    xg, _ = bf16(r.standard_normal(shape + (cin,)))
+    wg, _ = bf16(r.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin))
+    bg, _ = f32(r.standard_normal(cout) * 0.1)
+    sg, _ = bf16(r.standard_normal(shape + (cout,)) * 0.5)
+    base = torch.from_numpy(r.standard_normal(shape + (cout,)).astype(np.float32)).cuda()
+    outs = []
+    for mode in ("gather", "halo"):
+        if mode == "gather":
+            monkeypatch.setenv("CLAIRE_CONV", "gather")
+        else:
+            monkeypatch.delenv("CLAIRE_CONV", raising=False)
+        y = torch.empty(shape + (cout,), dtype=torch.bfloat16, device="cuda")
+        acc = base.clone()
+        ws_mod.conv3_fwd(xg, wg, bias=bg, skip=sg, relu=True, y=y, yf=acc, accum=True)
+        outs.append((y.cpu(), acc.cpu()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("shape,cin,cout", CONV_CASES[:5] + HALO_CASES[:3])
 def test_conv3_weight_and_input_gradients(ws_mod, shape, cin, cout):
     r = np.random.default_rng(7 + cin + cout)
     xg, x = bf16(r.standard_normal(shape + (cin,)))
