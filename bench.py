@@ -1178,7 +1178,7 @@ def main():
         "hessian_matvec_full_api_ms": matvec_full_ms,
         "roofline": roof, "kernels": kernels, "kernel_pass": {"solves": prof_steps, "ms_per_solve": prof_ms,
                                                               "note": "separate pass with per-launch CUDA events"},
-        "gather_schedule": gather, "clocks": clk, "gpu_launches": launches, "pcg_graph_launches": pcg_graphs,
+        "gather_schedule": gather, "fft_tiles": ctx.fft_tiles(), "clocks": clk, "gpu_launches": launches, "pcg_graph_launches": pcg_graphs,
         "e2e": e2e,
         "cpu_baseline": cb, "variants": variants,
     }

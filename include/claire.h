@@ -124,6 +124,8 @@ claire_status claire_default_opts(claire_opts* opts, int n1, int n2, int n3, int
  * device workspace for grid opts->n. The context keeps a copy of *opts. Returns CLAIRE_EINVAL for bad options,
  * CLAIRE_ENOMEM / CLAIRE_ECUDA on allocation failure (then *out is NULL). Uses the current CUDA device. */
 claire_status claire_create(const claire_opts* opts, claire_ctx** out);
+/* (FP32 contexts also time the tile variants of the FFT passes on their grid once per process; see
+ * claire_counters.fft_tile.) */
 
 /* Free the context and its workspace (synchronises the device first). NULL is accepted. */
 claire_status claire_destroy(claire_ctx* ctx);
@@ -303,6 +305,11 @@ typedef struct {
     long long tma_steps;      /* accumulating adjoint steps whose streamed operands (Y, grad m^j, b) were staged
                                  in shared memory by TMA (FP32, brick-tiled schedule, n3 a multiple of 16; the
                                  environment variable CLAIRE_TMA=0 turns this off) */
+    int fft_tile[3];          /* tile variant of the length-specialised FFT passes chosen by the autotuner at
+                                 claire_create (FP32) for the contiguous (z), y and x passes: 0 the default lines or
+                                 columns per CTA, 1 half as many, 2 twice as many (CLAIRE_FFT_TILES=default keeps 0; CLAIRE_FFT_TILES=z,y,x forces
+                                 the three; a variant that does not fit a length runs as 0); a variant changes
+                                 no result bit */
 } claire_counters;
 claire_status claire_get_counters(const claire_ctx* ctx, claire_counters* out);
 

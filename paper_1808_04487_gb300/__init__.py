@@ -59,7 +59,8 @@ class PairF32(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("halo_x", ctypes.c_int), ("halo_y", ctypes.c_int),
                 ("halo_x_heavy", ctypes.c_int), ("halo_y_heavy", ctypes.c_int), ("pcg_graph_runs", ctypes.c_longlong),
-                ("gn_graph_runs", ctypes.c_longlong), ("tma_steps", ctypes.c_longlong)]
+                ("gn_graph_runs", ctypes.c_longlong), ("tma_steps", ctypes.c_longlong),
+                ("fft_tile", ctypes.c_int * 3)]
 
 
 _VP = ctypes.c_void_p
@@ -471,6 +472,12 @@ class Context:
         c = Counters()
         lib().claire_get_counters(self._h, ctypes.byref(c))
         return int(c.tma_steps)
+
+    def fft_tiles(self):
+        """{"z", "y", "x"}: tile variant of each length-specialised FFT pass (0 default, 1 half, 2 double)."""
+        c = Counters()
+        lib().claire_get_counters(self._h, ctypes.byref(c))
+        return {"z": int(c.fft_tile[0]), "y": int(c.fft_tile[1]), "x": int(c.fft_tile[2])}
 
     def gather_schedule(self):
         """{"halo_x", "halo_y", "halo_x_heavy", "halo_y_heavy"}: brick halos of the tiled gathers of the cached

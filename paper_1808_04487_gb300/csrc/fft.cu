@@ -13,6 +13,11 @@
 #include <cmath>
 #include <vector>
 
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "impl.cuh"
 
 namespace claire {
@@ -308,19 +313,19 @@ template <class T> claire_status fft_r2c(claire_ctx* c, const T* in, cplx<T>* ou
   const long long nlines = (long long)d.n1 * d.n2;
   const long long inner1 = (long long)d.n2 * d.n3h;
   c->prof_begin("fft_z_r2c", st);
-  if (!fft2_z<T>(d.n3 / 2, -1, in, out, nlines, p.tw3, T(1), st)) {
+  if (!fft2_z<T>(d.n3 / 2, -1, in, out, nlines, p.tw3, T(1), st, p.var_z)) {
     const unsigned grid = (unsigned)((nlines + p.lpc3 - 1) / p.lpc3);
     k_fft_z_r2c<T><<<grid, 256, smem_z<T>(d.n3, p.lpc3), st>>>(in, out, nlines, d.n3, p.ax3, p.tw3, p.lpc3);
   }
   CL_LAUNCHED(c);
   c->prof_begin("fft_y_fwd", st);
-  if (!fft2_strided<T>(d.n2, -1, out, out, d.n3h, d.n1, p.tw2, st)) {
+  if (!fft2_strided<T>(d.n2, -1, out, out, d.n3h, d.n1, p.tw2, st, p.var_y)) {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
     k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(out, out, d.n3h, p.ax2, p.tw2, p.ti12);
   }
   CL_LAUNCHED(c);
   c->prof_begin("fft_x_fwd", st);
-  if (!fft2_strided<T>(d.n1, -1, out, out, inner1, 1, p.tw1, st)) {
+  if (!fft2_strided<T>(d.n1, -1, out, out, inner1, 1, p.tw1, st, p.var_x)) {
     dim3 grid((unsigned)((inner1 + p.ti12 - 1) / p.ti12), 1u);
     k_fft_strided<T, -1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(out, out, inner1, p.ax1, p.tw1, p.ti12);
   }
@@ -336,19 +341,19 @@ claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_
   const long long inner1 = (long long)d.n2 * d.n3h;
   const cplx<T>* first = src ? src : spec;
   c->prof_begin("fft_x_inv", st);
-  if (!fft2_strided<T>(d.n1, +1, first, spec, inner1, 1, p.tw1, st)) {
+  if (!fft2_strided<T>(d.n1, +1, first, spec, inner1, 1, p.tw1, st, p.var_x)) {
     dim3 grid((unsigned)((inner1 + p.ti12 - 1) / p.ti12), 1u);
     k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n1, p.ti12), st>>>(first, spec, inner1, p.ax1, p.tw1, p.ti12);
   }
   CL_LAUNCHED(c);
   c->prof_begin("fft_y_inv", st);
-  if (!fft2_strided<T>(d.n2, +1, spec, spec, d.n3h, d.n1, p.tw2, st)) {
+  if (!fft2_strided<T>(d.n2, +1, spec, spec, d.n3h, d.n1, p.tw2, st, p.var_y)) {
     dim3 grid((unsigned)((d.n3h + p.ti12 - 1) / p.ti12), (unsigned)d.n1);
     k_fft_strided<T, +1><<<grid, 256, smem_s<T>(d.n2, p.ti12), st>>>(spec, spec, d.n3h, p.ax2, p.tw2, p.ti12);
   }
   CL_LAUNCHED(c);
   c->prof_begin("fft_z_c2r", st);
-  if (!fft2_z<T>(d.n3 / 2, +1, spec, out, nlines, p.tw3, scale, st)) {
+  if (!fft2_z<T>(d.n3 / 2, +1, spec, out, nlines, p.tw3, scale, st, p.var_z)) {
     const unsigned grid = (unsigned)((nlines + p.lpc3 - 1) / p.lpc3);
     k_fft_z_c2r<T><<<grid, 256, smem_z<T>(d.n3, p.lpc3), st>>>(spec, out, nlines, d.n3, p.ax3, p.tw3, p.lpc3,
                                                                 scale);
@@ -357,7 +362,96 @@ claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T scale, cudaStream_
   return CLAIRE_OK;
 }
 
+// Autotuner of the FFT tile shapes: for each axis whose length has a specialised pass, time a forward and an
+// inverse pass of each tile variant (columns per CTA of the strided y and x passes, lines per CTA of the contiguous
+// z passes) on this context's work arrays, three times after a warm-up, and keep the fastest; the choice is cached
+// per grid for the process. Only FP32 passes have variants. CLAIRE_FFT_TILES=default keeps the defaults;
+// CLAIRE_FFT_TILES=z,y,x (three variants 0..2) forces a choice. A variant changes only how many lines one CTA
+// transforms: every line takes the same arithmetic in the same order, so the results are bit-identical.
+template <class T> claire_status fft_tune(claire_ctx* c) {
+  if (sizeof(T) != 4) return CLAIRE_OK;
+  FFTPlan<T>& p = c->plan<T>();
+  const char* env = std::getenv("CLAIRE_FFT_TILES");
+  if (env && std::strcmp(env, "default") == 0) return CLAIRE_OK;
+  int fz = 0, fy = 0, fx = 0;
+  if (env && std::sscanf(env, "%d,%d,%d", &fz, &fy, &fx) == 3) {  // forced variants (z, y, x), each 0..2
+    if (fz < 0 || fz > 2 || fy < 0 || fy > 2 || fx < 0 || fx > 2) return CLAIRE_EINVAL;
+    p.var_z = fz;
+    p.var_y = fy;
+    p.var_x = fx;
+    return CLAIRE_OK;
+  }
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> cache;
+  const Dims& d = c->d;
+  const auto key = std::make_tuple(d.n1, d.n2, d.n3);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      std::tie(p.var_y, p.var_x, p.var_z) = it->second;
+      return CLAIRE_OK;
+    }
+  }
+  Work<T>& W = c->work<T>();
+  cplx<T>* S = W.spec;
+  T* f = W.b;  // 3N values, at least N
+  cudaStream_t st;
+  CL_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e[2];
+  CL_CUDA(c, cudaEventCreate(&e[0]));
+  CL_CUDA(c, cudaEventCreate(&e[1]));
+  claire_status status = CLAIRE_OK;
+  auto best_of = [&](auto&& run, int* out) -> claire_status {
+    float best = 0.f;
+    int bv = 0;
+    for (int v = 0; v < 3; ++v) {
+      if (!run(v)) return CLAIRE_OK;  // no specialised pass for this length
+      CL_CUDA(c, cudaEventRecord(e[0], st));
+      for (int r = 0; r < 3; ++r) run(v);
+      CL_CUDA(c, cudaEventRecord(e[1], st));
+      CL_CUDA(c, cudaEventSynchronize(e[1]));
+      float ms = 0.f;
+      CL_CUDA(c, cudaEventElapsedTime(&ms, e[0], e[1]));
+      CL_CUDA(c, cudaGetLastError());
+      if (v == 0 || ms < best) {
+        best = ms;
+        bv = v;
+      }
+    }
+    *out = bv;
+    return CLAIRE_OK;
+  };
+  const long long nlines = (long long)d.n1 * d.n2;
+  const long long inner1 = (long long)d.n2 * d.n3h;
+  status = zero_fill<T>(c, d.N, f, st);
+  if (status == CLAIRE_OK) status = zero_fill<T>(c, 2 * d.Ns, reinterpret_cast<T*>(S), st);
+  int vy = 0, vx = 0, vz = 0;
+  if (status == CLAIRE_OK)
+    status = best_of([&](int v) { return fft2_strided<T>(d.n2, -1, S, S, d.n3h, d.n1, p.tw2, st, v) &&
+                                         fft2_strided<T>(d.n2, +1, S, S, d.n3h, d.n1, p.tw2, st, v); }, &vy);
+  if (status == CLAIRE_OK)
+    status = best_of([&](int v) { return fft2_strided<T>(d.n1, -1, S, S, inner1, 1, p.tw1, st, v) &&
+                                         fft2_strided<T>(d.n1, +1, S, S, inner1, 1, p.tw1, st, v); }, &vx);
+  if (status == CLAIRE_OK)
+    status = best_of([&](int v) { return fft2_z<T>(d.n3 / 2, -1, f, S, nlines, p.tw3, T(1), st, v) &&
+                                         fft2_z<T>(d.n3 / 2, +1, S, f, nlines, p.tw3, T(1), st, v); }, &vz);
+  cudaEventDestroy(e[0]);
+  cudaEventDestroy(e[1]);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (status != CLAIRE_OK) return status;
+  p.var_y = vy;
+  p.var_x = vx;
+  p.var_z = vz;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = std::make_tuple(vy, vx, vz);
+  return CLAIRE_OK;
+}
+
 template size_t fft_table_bytes<float>(const Dims&);
+template claire_status fft_tune<float>(claire_ctx*);
+template claire_status fft_tune<double>(claire_ctx*);
 template size_t fft_table_bytes<double>(const Dims&);
 template claire_status fft_init<float>(claire_ctx*);
 template claire_status fft_init<double>(claire_ctx*);

@@ -308,10 +308,19 @@ __global__ void __launch_bounds__(LPC * cmax<R1, R2>(), 4) k_fft2_z_c2r(const cp
 template <class T> __host__ __device__ constexpr int strided_ti() { return sizeof(T) == 4 ? 16 : 8; }
 template <class T, int TT> __host__ __device__ constexpr int z_lpc() { return (256 / TT) / (sizeof(T) == 4 ? 1 : 2) > 0 ? (256 / TT) / (sizeof(T) == 4 ? 1 : 2) : 1; }
 
-template <class T, int R1, int R2>
-void launch_strided(int sign, const cplx<T>* src, cplx<T>* dst, long long inner, int outer, const cplx<T>* W,
-                    cudaStream_t st) {
-  constexpr int TI = strided_ti<T>();
+// Tile variants of the specialised FP32 passes, chosen per grid by the autotuner in fft.cu: 0 the default
+// columns (strided) or lines (contiguous) per CTA, 1 half as many, 2 twice as many -- where the static shared
+// memory (48 KB) and the block size allow, else the default. FP64 passes keep the default.
+template <class T, int V> __host__ __device__ constexpr int ti_of() {
+  return V == 0 ? strided_ti<T>() : (V == 1 ? strided_ti<T>() / 2 : strided_ti<T>() * 2);
+}
+template <class T, int R1, int R2, int TI> __host__ __device__ constexpr bool strided_fits() {
+  return TI >= 1 && (size_t(R1 * R2) * TI + R1 * R2) * sizeof(cplx<T>) <= 48 * 1024 && TI * cmax<R1, R2>() <= 1024;
+}
+
+template <class T, int R1, int R2, int TI>
+void launch_strided_ti(int sign, const cplx<T>* src, cplx<T>* dst, long long inner, int outer, const cplx<T>* W,
+                       cudaStream_t st) {
   constexpr int TT = cmax<R1, R2>();
   dim3 grid((unsigned)((inner + TI - 1) / TI), (unsigned)outer);
   dim3 block(TI, TT);
@@ -321,21 +330,64 @@ void launch_strided(int sign, const cplx<T>* src, cplx<T>* dst, long long inner,
     k_fft2_strided<T, +1, R1, R2, TI><<<grid, block, 0, st>>>(src, dst, inner, W);
 }
 
-// (R1, R2) of the forward pass; the inverse pass may use another split (C1, C2) of the same length
-template <class T, int R1, int R2, int C1 = R1, int C2 = R2>
-void launch_z(int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3, T scale, cudaStream_t st) {
-  static_assert(R1 * R2 == C1 * C2, "one line length");
+template <class T, int R1, int R2>
+void launch_strided(int sign, const cplx<T>* src, cplx<T>* dst, long long inner, int outer, const cplx<T>* W,
+                    cudaStream_t st, int var) {
+  if constexpr (sizeof(T) == 4) {
+    if (var == 1 && strided_fits<T, R1, R2, ti_of<T, 1>()>()) {
+      if constexpr (strided_fits<T, R1, R2, ti_of<T, 1>()>())
+        launch_strided_ti<T, R1, R2, ti_of<T, 1>()>(sign, src, dst, inner, outer, W, st);
+      return;
+    }
+    if (var == 2 && strided_fits<T, R1, R2, ti_of<T, 2>()>()) {
+      if constexpr (strided_fits<T, R1, R2, ti_of<T, 2>()>())
+        launch_strided_ti<T, R1, R2, ti_of<T, 2>()>(sign, src, dst, inner, outer, W, st);
+      return;
+    }
+  }
+  launch_strided_ti<T, R1, R2, strided_ti<T>()>(sign, src, dst, inner, outer, W, st);
+}
+
+template <class T, int R1, int R2, int LPC> __host__ __device__ constexpr bool z_fits() {
+  return LPC >= 1 && (size_t(LPC) * (R1 * R2 + R1 * R2 / R1 + 1) + 2 * R1 * R2 + 1) * sizeof(cplx<T>) <= 48 * 1024 &&
+         LPC * cmax<R1, R2>() <= 1024;
+}
+template <class T, int R1, int R2, int V> __host__ __device__ constexpr int lpc_of() {
+  return V == 0 ? z_lpc<T, cmax<R1, R2>()>() : (V == 1 ? z_lpc<T, cmax<R1, R2>()>() / 2 : z_lpc<T, cmax<R1, R2>()>() * 2);
+}
+
+template <class T, int R1, int R2, int C1, int C2, int V>
+bool launch_z_v(int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3, T scale, cudaStream_t st) {
   if (sign < 0) {
     constexpr int TT = cmax<R1, R2>();
-    constexpr int LPC = z_lpc<T, TT>();
-    k_fft2_z_r2c<T, R1, R2, LPC><<<dim3((unsigned)((nlines + LPC - 1) / LPC)), dim3(TT, LPC), 0, st>>>(
-        static_cast<const T*>(in), static_cast<cplx<T>*>(out), nlines, Wn3);
+    constexpr int LPC = lpc_of<T, R1, R2, V>();
+    if constexpr (z_fits<T, R1, R2, LPC>()) {
+      k_fft2_z_r2c<T, R1, R2, LPC><<<dim3((unsigned)((nlines + LPC - 1) / LPC)), dim3(TT, LPC), 0, st>>>(
+          static_cast<const T*>(in), static_cast<cplx<T>*>(out), nlines, Wn3);
+      return true;
+    }
   } else {
     constexpr int TT = cmax<C1, C2>();
-    constexpr int LPC = z_lpc<T, TT>();
-    k_fft2_z_c2r<T, C1, C2, LPC><<<dim3((unsigned)((nlines + LPC - 1) / LPC)), dim3(TT, LPC), 0, st>>>(
-        static_cast<const cplx<T>*>(in), static_cast<T*>(out), nlines, Wn3, scale);
+    constexpr int LPC = lpc_of<T, C1, C2, V>();
+    if constexpr (z_fits<T, C1, C2, LPC>()) {
+      k_fft2_z_c2r<T, C1, C2, LPC><<<dim3((unsigned)((nlines + LPC - 1) / LPC)), dim3(TT, LPC), 0, st>>>(
+          static_cast<const cplx<T>*>(in), static_cast<T*>(out), nlines, Wn3, scale);
+      return true;
+    }
   }
+  return false;
+}
+
+// (R1, R2) of the forward pass; the inverse pass may use another split (C1, C2) of the same length
+template <class T, int R1, int R2, int C1 = R1, int C2 = R2>
+void launch_z(int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3, T scale, cudaStream_t st,
+              int var) {
+  static_assert(R1 * R2 == C1 * C2, "one line length");
+  if constexpr (sizeof(T) == 4) {
+    if (var == 1 && launch_z_v<T, R1, R2, C1, C2, 1>(sign, in, out, nlines, Wn3, scale, st)) return;
+    if (var == 2 && launch_z_v<T, R1, R2, C1, C2, 2>(sign, in, out, nlines, Wn3, scale, st)) return;
+  }
+  launch_z_v<T, R1, R2, C1, C2, 0>(sign, in, out, nlines, Wn3, scale, st);
 }
 
 }  // namespace
@@ -343,19 +395,19 @@ void launch_z(int sign, const void* in, void* out, long long nlines, const cplx<
 // Specialised strided pass for line length L; returns false when L has no specialisation.
 template <class T>
 bool fft2_strided(int L, int sign, const cplx<T>* src, cplx<T>* dst, long long inner, int outer, const cplx<T>* W,
-                  cudaStream_t st) {
+                  cudaStream_t st, int var) {
   switch (L) {
-    case 16: launch_strided<T, 4, 4>(sign, src, dst, inner, outer, W, st); return true;
-    case 32: launch_strided<T, 8, 4>(sign, src, dst, inner, outer, W, st); return true;
-    case 48: launch_strided<T, 8, 6>(sign, src, dst, inner, outer, W, st); return true;
-    case 64: launch_strided<T, 8, 8>(sign, src, dst, inner, outer, W, st); return true;
-    case 96: launch_strided<T, 8, 12>(sign, src, dst, inner, outer, W, st); return true;
-    case 112: launch_strided<T, 16, 7>(sign, src, dst, inner, outer, W, st); return true;
-    case 128: launch_strided<T, 16, 8>(sign, src, dst, inner, outer, W, st); return true;
-    case 144: launch_strided<T, 12, 12>(sign, src, dst, inner, outer, W, st); return true;
-    case 160: launch_strided<T, 16, 10>(sign, src, dst, inner, outer, W, st); return true;
-    case 192: launch_strided<T, 16, 12>(sign, src, dst, inner, outer, W, st); return true;
-    case 256: launch_strided<T, 16, 16>(sign, src, dst, inner, outer, W, st); return true;
+    case 16: launch_strided<T, 4, 4>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 32: launch_strided<T, 8, 4>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 48: launch_strided<T, 8, 6>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 64: launch_strided<T, 8, 8>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 96: launch_strided<T, 8, 12>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 112: launch_strided<T, 16, 7>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 128: launch_strided<T, 16, 8>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 144: launch_strided<T, 12, 12>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 160: launch_strided<T, 16, 10>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 192: launch_strided<T, 16, 12>(sign, src, dst, inner, outer, W, st, var); return true;
+    case 256: launch_strided<T, 16, 16>(sign, src, dst, inner, outer, W, st, var); return true;
     default: return false;
   }
 }
@@ -363,28 +415,28 @@ bool fft2_strided(int L, int sign, const cplx<T>* src, cplx<T>* dst, long long i
 // Specialised contiguous-axis pass for complex length L = n3/2 (sign -1: R2C from real `in`; +1: C2R to `out`).
 template <class T>
 bool fft2_z(int L, int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3, T scale,
-            cudaStream_t st) {
+            cudaStream_t st, int var) {
   switch (L) {
-    case 16: launch_z<T, 4, 4>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 24: launch_z<T, 8, 3>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 32: launch_z<T, 8, 4>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 48: launch_z<T, 8, 6>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 56: launch_z<T, 8, 7>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 64: launch_z<T, 8, 8>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 72: launch_z<T, 8, 9>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 80: launch_z<T, 8, 10>(sign, in, out, nlines, Wn3, scale, st); return true;
-    case 96: launch_z<T, 8, 12>(sign, in, out, nlines, Wn3, scale, st); return true;
+    case 16: launch_z<T, 4, 4>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 24: launch_z<T, 8, 3>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 32: launch_z<T, 8, 4>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 48: launch_z<T, 8, 6>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 56: launch_z<T, 8, 7>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 64: launch_z<T, 8, 8>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 72: launch_z<T, 8, 9>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 80: launch_z<T, 8, 10>(sign, in, out, nlines, Wn3, scale, st, var); return true;
+    case 96: launch_z<T, 8, 12>(sign, in, out, nlines, Wn3, scale, st, var); return true;
     // inverse 8 x 16: its first stage, which also applies the Hermitian split, runs on all 16 threads of a line
-    case 128: launch_z<T, 16, 8, 8, 16>(sign, in, out, nlines, Wn3, scale, st); return true;
+    case 128: launch_z<T, 16, 8, 8, 16>(sign, in, out, nlines, Wn3, scale, st, var); return true;
     default: return false;
   }
 }
 
 template bool fft2_strided<float>(int, int, const cplx<float>*, cplx<float>*, long long, int, const cplx<float>*,
-                                  cudaStream_t);
+                                  cudaStream_t, int);
 template bool fft2_strided<double>(int, int, const cplx<double>*, cplx<double>*, long long, int,
-                                   const cplx<double>*, cudaStream_t);
-template bool fft2_z<float>(int, int, const void*, void*, long long, const cplx<float>*, float, cudaStream_t);
-template bool fft2_z<double>(int, int, const void*, void*, long long, const cplx<double>*, double, cudaStream_t);
+                                   const cplx<double>*, cudaStream_t, int);
+template bool fft2_z<float>(int, int, const void*, void*, long long, const cplx<float>*, float, cudaStream_t, int);
+template bool fft2_z<double>(int, int, const void*, void*, long long, const cplx<double>*, double, cudaStream_t, int);
 
 }  // namespace claire

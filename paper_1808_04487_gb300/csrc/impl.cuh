@@ -27,6 +27,7 @@ template <class T> struct FFTPlan {
   cplx<T>* tw3 = nullptr;          // exp(-2 pi i t / n3), t < n3 (the z pass uses every other entry)
   int ti12 = 16;                   // columns per CTA of the strided passes
   int lpc3 = 16;                   // lines per CTA of the contiguous pass
+  int var_y = 0, var_x = 0, var_z = 0;  // tile variants of the specialised passes (chosen by fft_tune)
 };
 
 // Device workspace of one context (all owned by the context arena).
@@ -236,10 +237,13 @@ template <class T> claire_status fft_c2r(claire_ctx* c, cplx<T>* spec, T* out, T
                                          const cplx<T>* src = nullptr);
 
 // ---- fft2.cu: length-specialised passes (false: no specialisation for L) ----
+// var: tile variant of the FP32 passes (0 default, 1 half, 2 double the columns or lines per CTA; see fft2.cu)
 template <class T> bool fft2_strided(int L, int sign, const cplx<T>* src, cplx<T>* dst, long long inner, int outer,
-                                     const cplx<T>* W, cudaStream_t st);
+                                     const cplx<T>* W, cudaStream_t st, int var = 0);
 template <class T> bool fft2_z(int L, int sign, const void* in, void* out, long long nlines, const cplx<T>* Wn3,
-                               T scale, cudaStream_t st);
+                               T scale, cudaStream_t st, int var = 0);
+// time the tile variants of the specialised passes on this grid once (FP32; cached per grid) and keep the fastest
+template <class T> claire_status fft_tune(claire_ctx* c);
 
 // ---- spectral.cu ----------------------------------------------------------------------------------------------
 template <class T> claire_status spec_grad(claire_ctx* c, const cplx<T>* F, cplx<T>* G0, cplx<T>* G1, cplx<T>* G2,

@@ -2079,6 +2079,7 @@ claire_status create_ctx(const claire_opts* opts, bool coarse, claire_ctx** out)
   }
   if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? sl_init<float>(c) : sl_init<double>(c);
   if (s == CLAIRE_OK) s = o.precision == CLAIRE_F32 ? alloc_work<float>(c) : alloc_work<double>(c);
+  if (s == CLAIRE_OK && o.precision == CLAIRE_F32) s = fft_tune<float>(c);
   if (s != CLAIRE_OK) {
     cudaFreeHost(c->hscal);
     cudaFree(c->arena);
@@ -2178,6 +2179,10 @@ claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   out->pcg_graph_runs = c->pcg_graph_runs;
   out->tma_steps = c->tma_steps + (c->coarse ? c->coarse->tma_steps : 0);
   out->gn_graph_runs = c->gn_graph_runs;
+  const auto& fp = c->pf;  // (FP64 passes have no tile variants)
+  out->fft_tile[0] = fp.var_z;
+  out->fft_tile[1] = fp.var_y;
+  out->fft_tile[2] = fp.var_x;
   return CLAIRE_OK;
 }
 

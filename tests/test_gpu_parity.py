@@ -117,6 +117,33 @@ def test_fft_length_specialised_passes(n, prec):
         assert rel(c.ifft(spec), f) < TOL[prec]
 
 
+@pytest.mark.parametrize("n", [(64, 96, 128), (112, 48, 160), (192, 256, 144), (256, 32, 256), (96, 112, 96)])
+def test_fft_tile_variants_are_bit_identical(n, monkeypatch):
+    """The FFT tile autotuner only changes how many lines one CTA transforms: every forced variant (z, y, x) and
+    the tuned choice give bit-identical transforms; a variant outside 0..2 is refused at context creation."""
+    f = dev(np.random.default_rng(12).normal(size=n), "f32")
+    g = np.random.default_rng(13).normal(size=(3,) + n)
+    runs = {}
+    for tiles in ("default", "1,1,1", "2,2,2", "1,2,0", "2,0,1", None):
+        if tiles is None:
+            monkeypatch.delenv("CLAIRE_FFT_TILES", raising=False)
+        else:
+            monkeypatch.setenv("CLAIRE_FFT_TILES", tiles)
+        with ctx(n, "f32", regnorm=2) as c:
+            spec = c.fft(f)
+            runs[tiles] = (spec.clone(), c.ifft(spec.clone()), c.spectral("A", dev(g, "f32")), c.fft_tiles())
+    base = runs["default"]
+    assert base[3] == {"z": 0, "y": 0, "x": 0}
+    assert runs["2,0,1"][3] == {"z": 2, "y": 0, "x": 1}
+    assert all(v in (0, 1, 2) for v in runs[None][3].values())
+    for tiles, r in runs.items():
+        for a, b in zip(r[:3], base[:3]):
+            assert torch.equal(a, b), tiles
+    monkeypatch.setenv("CLAIRE_FFT_TILES", "3,0,0")
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        ctx(n, "f32")
+
+
 # ------------------------------------------------------------------------------------------------------ spectral ops
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("n", [(16, 16, 16), (12, 16, 20), (40, 36, 42)])
