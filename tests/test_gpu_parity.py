@@ -482,6 +482,38 @@ def test_device_driven_solve_is_bit_identical_to_the_host_loop(prec, problem, mo
         assert sh == "ELINESEARCH" and float(vd.abs().max()) == 0.0
 
 
+def test_device_driven_solve_does_not_depend_on_the_fixed_halo(monkeypatch):
+    """The device-driven solve fixes its brick halo at capture (a fresh context has no measured displacement; halo
+    2 by default). With 1.5-voxel steps a halo-2 brick misses some stencils, which then take the global taps: the
+    solve is bit-identical for fixed halos 2, 3 and 5 and to the host-driven loop, whose halos follow the measured
+    displacement (bricks forced, operands TMA-staged: n3 = 64)."""
+    n = (48, 40, 64)
+    kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, max_gn=3, gtol_rel=1e-2)
+    mT = I.brain_phantom(n, 0)
+    vs = I.random_velocity(n, seed=1, kmax=6, max_disp_voxels=6.0, divfree=True)
+    monkeypatch.setenv("CLAIRE_GATHER", "tiled")
+    runs = {}
+    for mode, halo in (("host", None), ("device", "2"), ("device", "3"), ("device", "5")):
+        monkeypatch.setenv("CLAIRE_GN", mode)
+        if halo is None:
+            monkeypatch.delenv("CLAIRE_GN_HALO", raising=False)
+        else:
+            monkeypatch.setenv("CLAIRE_GN_HALO", halo)
+        with ctx(n, "f32", **kw) as c:
+            mR = c.transport(dev(mT, "f32"), dev(vs, "f32"), +1)
+            v, rep, status = c.register(dev(mT, "f32"), mR)
+            runs[(mode, halo)] = (v.cpu(), rep, status, c.gn_graph_runs(), c.tma_steps())
+    vh, rh, sh, gh, th = runs[("host", None)]
+    assert gh == 0 and th > 0
+    for key, (v, r, st, g, t) in runs.items():
+        if key[0] == "device":
+            assert g == 1 and t > 0, key
+        assert st == sh, key
+        for k in ("gn_iters", "matvecs", "pde_solves", "ls_trials", "J", "gnorm"):
+            assert r[k] == rh[k], (key, k)
+        assert torch.equal(v, vh), key
+
+
 def test_degenerate_identical_images_converge_immediately():
     n = (16, 16, 16)
     mT = I.trig_image(n, 0)
