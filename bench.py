@@ -353,10 +353,11 @@ def oracle_solve_estimate(per_op, counts):
 
 def scale_linear(per_op, n_from, n_target):
     """Per-operator seconds at n_target from one measured grid, linear in the node count. On the GB300 host's
-    Neoverse-V2 cores the oracle's operators grow 8.0x from 128^3 to 256^3 (measured: transport 16.8 -> 130.9 s,
-    gradient 33.7 -> 268.1 s, matvec 19.4 -> 155.3 s, preconditioner 0.26 -> 2.48 s; `--study oracle`), while
-    from 64^3 to 128^3 they grow 29-33x (the 64^3 fields still sit in the caches): grids below 128^3 do not
-    extrapolate, 128^3 does."""
+    Neoverse-V2 cores the oracle's operators grow 8.1-8.8x from 128^3 to 256^3 (`--study oracle`: transport
+    3.97 -> 32.4 s, gradient 8.68 -> 70.4 s, matvec 4.87 -> 42.7 s, preconditioner 0.09 -> 1.0 s), so the linear
+    scale from 128^3 gives a solve estimate about 11% below the 256^3 operators times the same counts: a
+    conservative (low) CPU time. Grids much below 128^3 extrapolate worse (on an x86 host the operators grew 30x
+    from 64^3 to 128^3, with the 64^3 fields in the caches)."""
     N = lambda n: float(n[0] * n[1] * n[2])
     return {k: t * N(n_target) / N(n_from) for k, t in per_op.items()}
 
@@ -391,8 +392,9 @@ def cpu_baseline(n_target, counts, base=(128, 128, 128), probe=(64, 64, 64)):
     tgt = "x".join(map(str, n_target))
     return {"value": one, "unit": "s", "cores": 1, "kind": "oracle",
             "sample": "oracle operators (transport, gradient, GN matvec, preconditioner) timed once each at %s on "
-                      "one pinned core, scaled to %s linearly in the node count (measured 8.0x from 128^3 to "
-                      "256^3 on this host), times the GPU solve's counts (%d GN, %d matvecs, %d Armijo trials)"
+                      "one pinned core, scaled to %s linearly in the node count (the operators grow 8.1-8.8x from "
+                      "128^3 to 256^3 on this host: about 11%% low), times the GPU solve's counts (%d GN, %d "
+                      "matvecs, %d Armijo trials)"
                       % ("x".join(map(str, base)), tgt, counts["gn_iters"], counts["matvecs"], counts["ls_trials"]),
             "all_cores_value": oracle_solve_estimate(est_all, counts),
             "all_cores_note": "per-operator ratio of unpinned to pinned time at %s applied to the one-core "
