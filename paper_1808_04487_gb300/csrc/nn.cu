@@ -358,14 +358,33 @@ __global__ void __launch_bounds__(128, 1) k_conv3_wgrad_tc(const bf16* __restric
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
-// dst[i] = sum_c part[c][i], c in order
-__global__ void k_sum_chunks(const float* __restrict__ part, int nchunks, long long count, float* __restrict__ dst) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x) {
+// dst[i] = sum_c part[c][i] in a fixed order: a CTA takes 32 consecutive i, each of its 8 warps sums one contiguous
+// eighth of the chunks in order (coalesced 128-byte rows), and the 8 range sums are added in order. (One thread per
+// i summing all chunks in order left a few dozen CTAs on the GPU, each thread a chain of ~190 strided loads.)
+__global__ void __launch_bounds__(256) k_sum_chunks(const float* __restrict__ part, int nchunks, long long count,
+                                                    float* __restrict__ dst) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int per = (nchunks + 7) / 8;
+  const int c0 = w * per, c1 = min(nchunks, c0 + per);
+  for (long long base = (long long)blockIdx.x * 32; base < count; base += (long long)gridDim.x * 32) {
+    const long long i = base + lane;
     float s = 0.f;
-    for (int c = 0; c < nchunks; ++c) s += part[(long long)c * count + i];
-    dst[i] = s;
+    if (i < count)
+      for (int c = c0; c < c1; ++c) s += part[(long long)c * count + i];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < count) {
+      float t = red[0][lane];
+      for (int k = 1; k < 8; ++k) t += red[k][lane];
+      dst[i] = t;
+    }
+    __syncthreads();
   }
+}
+inline unsigned sum_blocks(long long count) {
+  const long long b = (count + 31) / 32;
+  return (unsigned)(b < 4864 ? (b > 0 ? b : 1) : 4864);
 }
 
 __global__ void k_wt_flip(const bf16* __restrict__ w, bf16* __restrict__ wt, int Cin, int Cout) {
@@ -764,7 +783,7 @@ cudaError_t conv3_wgrad(const bf16* dz, const bf16* x, float* dw, float* work, c
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long count = 27LL * Cin * Cout;
-  k_sum_chunks<<<nblocks(count), 256, 0, st>>>(work, nchunks, count, dw);
+  k_sum_chunks<<<sum_blocks(count), 256, 0, st>>>(work, nchunks, count, dw);
   return cudaGetLastError();
 }
 
@@ -800,7 +819,7 @@ cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* wor
   k_chan_sum<<<kBiasBlocks, threads, 0, st>>>(dz, M, C, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sum_chunks<<<nblocks(C), 256, 0, st>>>(work, kBiasBlocks, C, db);
+  k_sum_chunks<<<sum_blocks(C), 256, 0, st>>>(work, kBiasBlocks, C, db);
   return cudaGetLastError();
 }
 
