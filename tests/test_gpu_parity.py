@@ -729,6 +729,56 @@ def test_fullsize_gradient_and_hessvec_closed_forms_at_zero(big_inputs):
     assert rel(hv, ref_h) < 1e-5
 
 
+def test_fullsize_departure_points_against_the_oracle():
+    """The bench's grid and displacement regime (div-free v*, |k| <= 6, 8 voxels over the unit time: 2 per step):
+    the RK2 departure points of both directions on the 256^3 grid against the FP64 oracle, every node."""
+    vs = I.random_velocity(BIG, seed=1, kmax=6, max_disp_voxels=8.0, divfree=True)
+    g = O.Grid(BIG)
+    with ctx(BIG, "f32", nt=4) as c:
+        v = dev(vs, "f32")
+        v64 = v.cpu().double().numpy()
+        for sign in (+1, -1):
+            got = c.departure(v, sign).cpu().double().numpy()
+            ref = O.departure(g, v64, 4, sign)
+            assert rel(got, ref) < 1e-5, sign
+            assert float(np.abs(ref).max()) > 1.5  # the regime of halo-3 bricks, not a trivial shift
+
+
+def test_fullsize_solve_is_bit_identical_across_gather_schedules(monkeypatch):
+    """The bench's workload at 256^3 (phantom, div-free v* of 8 voxels, H2, beta 1e-3, div v = 0, n_t 4; two GN
+    iterations) solved with the schedule the bench runs -- brick-tiled gathers with TMA-staged operands -- and with
+    per-thread operand loads (CLAIRE_TMA=0): the same iterates bit for bit; with global taps (CLAIRE_GATHER=plain,
+    float2 pair loads whose roundings are those of the scalar taps) the same counts and v within 1e-6. The brick
+    and TMA paths are held to the oracle on the small grids; at full size they are held to the global taps."""
+    mT = I.brain_phantom(BIG, 0)
+    vs = I.random_velocity(BIG, seed=1, kmax=6, max_disp_voxels=8.0, divfree=True)
+    kw = dict(beta=1e-3, nt=4, regnorm=2, divfree=True, gtol_rel=1e-2, max_gn=2)
+    runs = {}
+    for mode, env in (("tma", {"CLAIRE_GATHER": "tiled"}), ("bricks", {"CLAIRE_TMA": "0", "CLAIRE_GATHER": "tiled"}),
+                      ("plain", {"CLAIRE_GATHER": "plain"})):
+        for k in ("CLAIRE_TMA", "CLAIRE_GATHER"):
+            monkeypatch.delenv(k, raising=False)
+        for k, val in env.items():
+            monkeypatch.setenv(k, val)
+        with ctx(BIG, "f32", **kw) as c:
+            mR = c.transport(dev(mT, "f32"), dev(vs, "f32"), +1)
+            v, rep, status = c.register(dev(mT, "f32"), mR)
+            runs[mode] = (v.cpu(), rep, status, c.tma_steps(), c.gather_schedule())
+    vt, rt, st, tt, gt = runs["tma"]
+    vb, rb, sb, tb, gb = runs["bricks"]
+    vp, rp, sp, tp, gp = runs["plain"]
+    print(gt, gb, gp, {k: rt[k] for k in ("gn_iters", "matvecs")})
+    assert tt > 0 and tb == 0 and tp == 0
+    assert gp["halo_x"] == -1 and gb["halo_x"] >= 2
+    assert st == sb == sp
+    for k in ("gn_iters", "matvecs", "pde_solves", "ls_trials", "J", "gnorm"):
+        assert rt[k] == rb[k], k
+    assert torch.equal(vt, vb)
+    for k in ("gn_iters", "matvecs", "pde_solves", "ls_trials"):
+        assert rt[k] == rp[k], k
+    assert rel(vp.double(), vt.double()) < 1e-6
+
+
 # ------------------------------------------------------------------------------------------------------ precision form
 @pytest.fixture(scope="module")
 def h2_phantom48():
