@@ -609,7 +609,8 @@ def batch_study(args):
         c.close()
     res["sequential"] = {"seconds": t_seq, "pairs_per_s": len(pairs) / t_seq,
                          "matvecs": sum(r["matvecs"] for r, _ in seq_out)}
-    # batched: every pair's solve driven from the device, each context's share of a grid class in one graph launch
+    # batched: every pair's solve driven from the device; the whole batch one graph launch (each context's share of
+    # a grid class a branch of it), 1, 2 or 4 contexts per grid class
     for nw in (1, 2, 4):
         pkg.register_batch(pairs[: min(8, len(pairs))], nworkers=nw, **kw)  # warm-up (autotuner, module load)
         for _, _, v in pairs:
@@ -618,17 +619,17 @@ def batch_study(args):
         same = all(torch.equal(p[2], vs) for p, vs in zip(pairs, v_seq))
         res["device_graph_contexts_per_grid_%d" % nw] = {
             "seconds": dt, "pairs_per_s": len(pairs) / dt, "converged": sum(1 for r, st in out if r["converged"]),
-            "matvecs": sum(r["matvecs"] for r, st in out), "bit_identical_to_sequential": bool(same)}
-    # the device-driven form with bricks of halo 3 (room for 2 voxels per time step; larger bricks and staged
-    # operands per CTA) instead of the default 2
-    os.environ["CLAIRE_GN_HALO"] = "3"
+            "matvecs": sum(r["matvecs"] for r, st in out), "bit_identical_to_sequential": bool(same),
+            "graph_launches": pkg.last_batch_graph_launches()}
+    # the same with one graph launch per context (CLAIRE_BATCH_GRAPH=lanes)
+    os.environ["CLAIRE_BATCH_GRAPH"] = "lanes"
     pkg.register_batch(pairs[: min(8, len(pairs))], nworkers=2, **kw)
     for _, _, v in pairs:
         v.zero_()
     out, dt = timed(lambda: pkg.register_batch(pairs, nworkers=2, **kw))
-    del os.environ["CLAIRE_GN_HALO"]
-    res["device_graph_contexts_per_grid_2_halo3"] = {
-        "seconds": dt, "pairs_per_s": len(pairs) / dt,
+    del os.environ["CLAIRE_BATCH_GRAPH"]
+    res["device_graph_per_context_contexts_per_grid_2"] = {
+        "seconds": dt, "pairs_per_s": len(pairs) / dt, "graph_launches": pkg.last_batch_graph_launches(),
         "bit_identical_to_sequential": bool(all(torch.equal(p[2], vs) for p, vs in zip(pairs, v_seq)))}
     # the earlier batched form for comparison: host worker threads, host-driven Gauss-Newton loops
     os.environ["CLAIRE_GN"] = "host"

@@ -227,13 +227,19 @@ claire_status claire_register_continuation_f64(claire_ctx* ctx, const double* mT
 claire_status claire_set_beta(claire_ctx* ctx, double beta);
 
 /* ---- batched registration of many independent pairs (population-to-atlas) ------------------------------------
- * Solves every pair with claire_register_f32's algorithm. Pairs may have different grids. nworkers host threads
- * (>= 1) each own a CUDA stream and one context per grid shape they meet (created from *base with n replaced by the
- * pair's grid, freed before the call returns); pairs are taken largest grid first from a shared queue, so the
- * solves of different pairs overlap on the GPU (small grids alone leave most SMs idle, and every GN/PCG step waits
- * for a host round trip). mT, mR, v are DEVICE arrays of the pair's grid on the current device; v is in/out
- * (zeros = the plain method). Per-pair results land in rep and status; the call returns CLAIRE_OK when every pair
- * ran (statuses CLAIRE_OK / ENOTCONV / ELINESEARCH), else the first failing status. Synchronises the device. */
+ * Solves every pair with claire_register_f32's algorithm (Alg. 1 with Alg. 2); pairs may have different grids. mT,
+ * mR, v are DEVICE arrays of the pair's grid on the current device; v is in/out (zeros = the plain method). By
+ * default every zero-start solve is driven from the device: the pairs are grouped by grid, each group is split over
+ * up to nworkers (>= 1) contexts (created from *base with n replaced by the group's grid, freed before the call
+ * returns), each context's share becomes one branch of a single CUDA graph -- a WHILE over its pairs around the
+ * Gauss-Newton WHILE, the PCG WHILE and the Armijo WHILE as conditional nodes, every decision taken on the device --
+ * and the whole batch runs as ONE graph launch whose branches overlap on the GPU. Results are bit-identical to the
+ * single-pair solves. A pair with a nonzero v, and every pair when base->precond != 0 or CLAIRE_GN=host, is solved by
+ * the host-driven loop (CLAIRE_GN=host: nworkers host threads, one stream and one context per grid each, pairs taken
+ * largest grid first). CLAIRE_BATCH_GRAPH=lanes launches one graph per context instead of one for the batch; so does
+ * the call if the single graph cannot be built. Per-pair results land in rep and status; the call returns CLAIRE_OK
+ * when every pair ran (statuses CLAIRE_OK / ENOTCONV / ELINESEARCH), else the first failing status. Synchronises the
+ * device. */
 typedef struct {
     int n[3];
     const float* mT;
@@ -243,6 +249,9 @@ typedef struct {
     int status;
 } claire_pair_f32;
 claire_status claire_register_batch_f32(const claire_opts* base, claire_pair_f32* pairs, int npairs, int nworkers);
+/* Graph launches made by the most recent claire_register_batch_f32 call of this process: 1 when the batch ran as one
+ * graph, one per context on the per-context path, 0 when every pair took the host-driven loop. */
+long long claire_last_batch_graph_launches(void);
 
 /* ---- building blocks exposed for testing and for callers composing their own solver --------------------------
  * claire_departure_*: RK2 departure points of one time step (dt = 1/nt) in grid units, disp = (X - x) / h per

@@ -148,6 +148,8 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     L.claire_default_opts.argtypes = [ctypes.POINTER(Opts), _I, _I, _I, _I]
     L.claire_default_opts.restype = _I
+    L.claire_last_batch_graph_launches.argtypes = []
+    L.claire_last_batch_graph_launches.restype = ctypes.c_longlong
     L.claire_create.argtypes = [ctypes.POINTER(Opts), ctypes.POINTER(_VP)]
     L.claire_create.restype = _I
     L.claire_destroy.argtypes = [_VP]
@@ -203,6 +205,11 @@ def register_batch(pairs, nworkers=4, beta=5e-3, nt=4, regnorm=1, divfree=False,
     if st not in (OK, ENOTCONV, ELINESEARCH):
         raise ClaireError(st, "claire_register_batch_f32 failed")
     return [(arr[i].rep.as_dict(), STATUS.get(arr[i].status, arr[i].status)) for i in range(len(pairs))]
+
+
+def last_batch_graph_launches():
+    """Graph launches of the most recent register_batch call: 1 when the batch ran as one CUDA graph."""
+    return int(lib().claire_last_batch_graph_launches())
 
 
 def _torch():

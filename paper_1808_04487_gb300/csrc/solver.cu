@@ -1038,7 +1038,9 @@ inline unsigned copy_blocks(long long n) {
 }
 
 // capture the whole solve into a new graph (the context's halos are held fixed while it runs)
-template <class T> claire_status gn_capture(claire_ctx* c, cudaGraph_t* out) {
+// Captures the device-driven solve of this context's pair table into a new graph (*out), or, with `into`, appends it
+// to that graph as an independent branch (the batch's single graph: one branch per context).
+template <class T> claire_status gn_capture(claire_ctx* c, cudaGraph_t* out, cudaGraph_t into = nullptr) {
   Work<T>& W = c->work<T>();
   const Dims& d = c->d;
   const long long N = d.N, n3 = 3 * N, Ns = d.Ns;
@@ -1048,9 +1050,11 @@ template <class T> claire_status gn_capture(claire_ctx* c, cudaGraph_t* out) {
   const GnBlock B = gn_block(c);
   cudaStream_t s0 = c->pcg_cap_stream, s1 = c->gn_cap_streams[0], s2 = c->gn_cap_streams[1],
                s3 = c->gn_cap_streams[2];
-  cudaGraph_t g = nullptr;
-  GN_CE(cudaGraphCreate(&g, 0));
-  *out = g;
+  cudaGraph_t g = into;
+  if (!g) {
+    GN_CE(cudaGraphCreate(&g, 0));
+    *out = g;
+  }
   GN_CE(cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   auto body = [&](cudaStream_t st, cudaGraph_t bg, long long* count, auto&& fn) -> claire_status {
     GN_CE(cudaStreamBeginCaptureToGraph(st, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -1250,7 +1254,8 @@ void gn_graph_release(claire_ctx* c) {
 // Enqueues the solves of pairs[0..n) (device arrays of this context's grid; every v is overwritten, the solves
 // start from v = 0) as one graph launch on st; the per-pair state blocks land in reports (pinned host memory,
 // n x kGnSlots doubles) once st has been synchronised.
-template <class T> claire_status gn_run(claire_ctx* c, const PairRef* pairs, int n, double* reports, cudaStream_t st) {
+// Buffers, capture streams, halos and TMA maps of a device-driven solve of n pairs on this context.
+template <class T> claire_status gn_setup(claire_ctx* c, int n, cudaStream_t st) {
   CL_TRY(ensure_hostbuf<T>(c));
   if (!c->gn_dev || c->gn_cap < n) {
     gn_graph_release(c);
@@ -1269,6 +1274,30 @@ template <class T> claire_status gn_run(claire_ctx* c, const PairRef* pairs, int
     if (!s) CL_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   CL_TRY(gn_fix_halos<T>(c, st));
   if constexpr (sizeof(T) == 4) sl_tma_prepare(c);  // host-side set-up of the staged gathers, before any capture
+  return CLAIRE_OK;
+}
+
+// The pair table, the solver settings and the pair count of a device-driven solve, copied to the device on st.
+template <class T> claire_status gn_upload(claire_ctx* c, const PairRef* pairs, int n, cudaStream_t st) {
+  const GnBlock B = gn_block(c);
+  double tmpl[kGnSlots] = {};
+  const claire_opts& o = c->o;
+  tmpl[kGnMaxGn] = o.max_gn;
+  tmpl[kGnMaxLs] = o.max_ls;
+  tmpl[kGnC1] = o.armijo_c1;
+  tmpl[kGnGtolRel] = o.gtol_rel;
+  tmpl[kGnGtolAbs] = o.gtol_abs;
+  tmpl[kGnPcgRtol] = o.pcg_rtol;
+  tmpl[kGnMaxKrylov] = o.max_krylov;
+  // (pageable sources: each copy is staged before the call returns)
+  CL_CUDA(c, cudaMemcpyAsync(B.tmpl, tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaMemcpyAsync(B.tab, pairs, sizeof(PairRef) * size_t(n), cudaMemcpyHostToDevice, st));
+  CL_CUDA(c, cudaMemcpyAsync(B.n, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+  return CLAIRE_OK;
+}
+
+template <class T> claire_status gn_run(claire_ctx* c, const PairRef* pairs, int n, double* reports, cudaStream_t st) {
+  CL_TRY(gn_setup<T>(c, n, st));
   const int key[4] = {c->haloX, c->haloXh, c->haloY, c->haloYh};
   if (!c->gn_exec || !std::equal(key, key + 4, c->gn_key_halo) || c->gn_beta != c->o.beta) {
     gn_graph_release(c);
@@ -1294,19 +1323,7 @@ template <class T> claire_status gn_run(claire_ctx* c, const PairRef* pairs, int
     c->gn_beta = c->o.beta;
   }
   const GnBlock B = gn_block(c);
-  double tmpl[kGnSlots] = {};
-  const claire_opts& o = c->o;
-  tmpl[kGnMaxGn] = o.max_gn;
-  tmpl[kGnMaxLs] = o.max_ls;
-  tmpl[kGnC1] = o.armijo_c1;
-  tmpl[kGnGtolRel] = o.gtol_rel;
-  tmpl[kGnGtolAbs] = o.gtol_abs;
-  tmpl[kGnPcgRtol] = o.pcg_rtol;
-  tmpl[kGnMaxKrylov] = o.max_krylov;
-  // (pageable sources: each copy is staged before the call returns)
-  CL_CUDA(c, cudaMemcpyAsync(B.tmpl, tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, st));
-  CL_CUDA(c, cudaMemcpyAsync(B.tab, pairs, sizeof(PairRef) * size_t(n), cudaMemcpyHostToDevice, st));
-  CL_CUDA(c, cudaMemcpyAsync(B.n, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+  CL_TRY(gn_upload<T>(c, pairs, n, st));
   CL_CUDA(c, cudaGraphLaunch(c->gn_exec, st));
   c->gn_graph_runs++;
   CL_CUDA(c, cudaMemcpyAsync(reports, B.reports, sizeof(double) * kGnSlots * size_t(n), cudaMemcpyDeviceToHost, st));
@@ -1540,7 +1557,10 @@ template <class T> claire_status register_dev(claire_ctx* c, const T* mT, const 
 // to nworkers contexts with a stream each, and each context runs its share of the group as ONE graph launch (the
 // pair loop of the captured solve), all launches issued before the first synchronisation. Pairs with a nonzero
 // initial guess take the host-driven solve afterwards.
+std::atomic<long long> g_last_batch_launches(0);
+
 claire_status register_batch_device(const claire_opts* base, claire_pair_f32* pairs, int npairs, int nworkers) {
+  g_last_batch_launches.store(0);
   std::map<std::tuple<int, int, int>, std::vector<int>> groups;
   for (int i = 0; i < npairs; ++i) groups[std::make_tuple(pairs[i].n[0], pairs[i].n[1], pairs[i].n[2])].push_back(i);
   struct Lane {
@@ -1596,7 +1616,6 @@ claire_status register_batch_device(const claire_opts* base, claire_pair_f32* pa
       }
     }
   }
-  // issue every lane's graph launch, then synchronise once
   for (Lane& L : lanes) {
     if (L.idx.empty()) continue;
     if (cudaMallocHost(&L.reports, sizeof(double) * kGnSlots * L.idx.size()) != cudaSuccess) {
@@ -1604,16 +1623,69 @@ claire_status register_batch_device(const claire_opts* base, claire_pair_f32* pa
       L.reports = nullptr;
       for (int i : L.idx) note(i, CLAIRE_ENOMEM);
       L.idx.clear();
-      continue;
-    }
-    const claire_status s = gn_run<float>(L.c, L.tab.data(), (int)L.idx.size(), L.reports, L.st);
-    if (s != CLAIRE_OK) {
-      for (int i : L.idx) note(i, s);
-      L.idx.clear();
     }
   }
+  // The whole batch as one graph launch: every lane's device-driven solve captured as an independent branch of one
+  // graph (the lanes' branches run concurrently). CLAIRE_BATCH_GRAPH=lanes launches one graph per lane instead; so
+  // does any failure to build the single graph.
+  std::vector<Lane*> act;
+  for (Lane& L : lanes)
+    if (!L.idx.empty()) act.push_back(&L);
+  const char* bg_env = std::getenv("CLAIRE_BATCH_GRAPH");
+  bool one = !act.empty() && !(bg_env && std::strcmp(bg_env, "lanes") == 0);
+  cudaGraph_t whole = nullptr;
+  cudaGraphExec_t whole_exec = nullptr;
+  cudaStream_t st0 = act.empty() ? nullptr : act.front()->st;
+  if (one) {
+    claire_status s = cudaGraphCreate(&whole, 0) == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
+    for (Lane* L : act) {
+      if (s != CLAIRE_OK) break;
+      s = gn_setup<float>(L->c, (int)L->idx.size(), L->st);
+      if (s == CLAIRE_OK && cudaStreamSynchronize(L->st) != cudaSuccess) s = CLAIRE_ECUDA;
+      if (s == CLAIRE_OK) {
+        L->c->halo_fixed = true;
+        cudaGraph_t unused = nullptr;
+        s = gn_capture<float>(L->c, &unused, whole);
+        L->c->halo_fixed = false;
+      }
+    }
+    if (s == CLAIRE_OK && cudaGraphInstantiate(&whole_exec, whole, 0) != cudaSuccess) s = CLAIRE_ECUDA;
+    for (Lane* L : act)
+      if (s == CLAIRE_OK) s = gn_upload<float>(L->c, L->tab.data(), (int)L->idx.size(), st0);
+    if (s == CLAIRE_OK && cudaGraphLaunch(whole_exec, st0) != cudaSuccess) s = CLAIRE_ECUDA;
+    if (s == CLAIRE_OK) g_last_batch_launches.store(1);
+    if (s == CLAIRE_OK) {
+      for (Lane* L : act) {
+        L->c->gn_graph_runs++;
+        const GnBlock B = gn_block(L->c);
+        if (s == CLAIRE_OK && cudaMemcpyAsync(L->reports, B.reports, sizeof(double) * kGnSlots * L->idx.size(),
+                                               cudaMemcpyDeviceToHost, st0) != cudaSuccess)
+          s = CLAIRE_ECUDA;
+      }
+    }
+    if (s != CLAIRE_OK) {
+      // nothing of the single graph ran (or its launch failed): per-lane launches instead
+      cudaGetLastError();
+      if (whole_exec) cudaGraphExecDestroy(whole_exec);
+      whole_exec = nullptr;
+      if (cudaStreamSynchronize(st0) != cudaSuccess) cudaGetLastError();
+      one = false;
+    }
+  }
+  if (!one) {
+    g_last_batch_launches.store(0);
+    for (Lane* L : act) {
+      const claire_status s = gn_run<float>(L->c, L->tab.data(), (int)L->idx.size(), L->reports, L->st);
+      if (s == CLAIRE_OK) g_last_batch_launches.fetch_add(1);
+      if (s != CLAIRE_OK) {
+        for (int i : L->idx) note(i, s);
+        L->idx.clear();
+      }
+    }
+  }
+  const bool one_ok = !one || cudaStreamSynchronize(st0) == cudaSuccess;
   for (Lane& L : lanes) {
-    if (cudaStreamSynchronize(L.st) != cudaSuccess) {
+    if (!one_ok || cudaStreamSynchronize(L.st) != cudaSuccess) {
       for (int i : L.idx) note(i, CLAIRE_ECUDA);
       L.idx.clear();
     }
@@ -1629,6 +1701,8 @@ claire_status register_batch_device(const claire_opts* base, claire_pair_f32* pa
     claire_pair_f32& p = pairs[hp.first];
     note(hp.first, register_dev<float>(L.c, p.mT, p.mR, p.v, &p.rep, L.st));
   }
+  if (whole_exec) cudaGraphExecDestroy(whole_exec);
+  if (whole) cudaGraphDestroy(whole);
   for (Lane& L : lanes) {
     if (L.reports) cudaFreeHost(L.reports);
     claire_destroy(L.c);
@@ -2280,8 +2354,11 @@ claire_status claire_register_host_f64(claire_ctx* c, const double* mT, const do
                                        claire_report* rep, void* s) {
   return api_register_host<double>(c, mT, mR, v, rep, s);
 }
+long long claire_last_batch_graph_launches(void) { return g_last_batch_launches.load(); }
+
 claire_status claire_register_batch_f32(const claire_opts* base, claire_pair_f32* pairs, int npairs, int nworkers) {
   if (!base || (!pairs && npairs > 0) || npairs < 0 || nworkers < 1) return CLAIRE_EINVAL;
+  g_last_batch_launches.store(0);
   if (base->precision != CLAIRE_F32) return CLAIRE_EINVAL;
   for (int i = 0; i < npairs; ++i)
     if (!pairs[i].mT || !pairs[i].mR || !pairs[i].v) return CLAIRE_EINVAL;

@@ -824,10 +824,16 @@ def test_bf16_gradient_history_errors_against_the_oracle(h2_phantom48):
 
 
 # ------------------------------------------------------------------------------------------------------ batched form
-def test_register_batch_matches_single_solves_on_uneven_grids():
+@pytest.mark.parametrize("graph", ["one", "lanes"])
+def test_register_batch_matches_single_solves_on_uneven_grids(graph, monkeypatch):
     """claire_register_batch_f32 (several workers, pairs of different grids) reproduces the single-pair solves
-    exactly: same kernels and summation order on every stream."""
+    exactly -- same kernels and summation order on every branch -- whether the batch runs as one graph launch
+    (every context's device-driven solve a branch of it; the default) or as one graph launch per context."""
     import paper_1808_04487_gb300 as pkg
+    if graph == "lanes":
+        monkeypatch.setenv("CLAIRE_BATCH_GRAPH", "lanes")
+    else:
+        monkeypatch.delenv("CLAIRE_BATCH_GRAPH", raising=False)
     kw = dict(beta=5e-3, nt=4, regnorm=1, divfree=False, gtol_rel=5e-2)
     grids = [(32, 32, 32), (24, 28, 20), (32, 32, 32), (16, 24, 32), (24, 28, 20)]
     pairs, singles = [], []
@@ -840,6 +846,8 @@ def test_register_batch_matches_single_solves_on_uneven_grids():
         singles.append((v1.clone(), rep1, st1))
         pairs.append((mT, atlas, torch.zeros((3,) + n, dtype=torch.float32, device="cuda")))
     out = pkg.register_batch(pairs, nworkers=3, **kw)
+    # contexts: 3 grids, (32^3 x2, 24x28x20 x2, 16x24x32 x1) -> 2 + 2 + 1 lanes with nworkers = 3
+    assert pkg.last_batch_graph_launches() == (1 if graph == "one" else 5)
     for (mT, mR, v), (rep, st), (v1, rep1, st1) in zip(pairs, out, singles):
         assert st == st1 and rep["gn_iters"] == rep1["gn_iters"] and rep["matvecs"] == rep1["matvecs"]
         assert torch.equal(v, v1)
