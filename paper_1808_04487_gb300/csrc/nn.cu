@@ -82,12 +82,16 @@ __device__ __forceinline__ int nb_of(const Geo& g, const Nbr& n, int off) {
 // mbarrier each: the staging of step i + 1 overlaps the MMAs of step i, and a stage is rewritten only after the
 // MMAs that read it have completed. Epilogue: with part == nullptr the full result (bias, skip, ReLU) goes to
 // y / yf; otherwise the raw FP32 partial sums go to part[blockIdx.y][m][co] for k_conv3_reduce.
+// CIN > 0: the input channel count as a compile-time constant (see k_conv3_wgrad_tc), else Cin_rt.
+template <int CIN>
 __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict__ x, const bf16* __restrict__ w,
                                                          const float* __restrict__ bias,
                                                          const bf16* __restrict__ skip, bf16* __restrict__ y,
-                                                         float* __restrict__ yf, int accum, Geo g, int Cin, int Cout,
-                                                         int relu, int offs_per_split, int group,
+                                                         float* __restrict__ yf, int accum, Geo g, int Cin_rt,
+                                                         int Cout, int relu, int offs_per_split, int group_rt,
                                                          float* __restrict__ part) {
+  const int Cin = CIN > 0 ? CIN : Cin_rt;
+  const int group = CIN > 0 ? (CIN < 64 ? 64 / CIN : 1) : group_rt;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
   const int KS = group * Cin;  // K extent of a full step
@@ -143,11 +147,17 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict_
       }
     }
     const int nv = nk / 8;
-    for (int q = tid; q < Cout * nv; q += kTileM) {
-      const int co = q / nv, c = q - co * nv;
-      *reinterpret_cast<uint4*>(Bs + tc::kmajor_offset(co, 8 * c, KS)) =
-          *reinterpret_cast<const uint4*>(w + ((long long)co * 27 + oa) * Cin + 8 * c);
-    }
+    auto stage_w = [&](int nvc) {
+      for (int q = tid; q < Cout * nvc; q += kTileM) {
+        const int co = q / nvc, c = q - co * nvc;
+        *reinterpret_cast<uint4*>(Bs + tc::kmajor_offset(co, 8 * c, KS)) =
+            *reinterpret_cast<const uint4*>(w + ((long long)co * 27 + oa) * Cin + 8 * c);
+      }
+    };
+    if (CIN > 0 && nk == KS)
+      stage_w(CIN > 0 ? (CIN < 64 ? 64 / CIN : 1) * CIN / 8 : 1);  // a full step: a constant divisor
+    else
+      stage_w(nv);
     tc::fence_smem_to_async();
     __syncthreads();
     if (tid == 0) {
@@ -233,9 +243,13 @@ __global__ void k_conv3_reduce(const float* __restrict__ part, int nsplit, const
 // likewise with the Cout channels of dz; thread t copies the 16-byte channel groups of voxel t % 64 (half t / 64
 // of them). In the unswizzled MN-major layout the descriptor's leading offset steps along K (8-voxel groups) and
 // its stride offset along M / N. Two stages with one mbarrier each: the loads of step s + 1 overlap the MMAs of s.
-__global__ void __launch_bounds__(128, 1) k_conv3_wgrad_tc(const bf16* __restrict__ dz, const bf16* __restrict__ x,
-                                                           float* __restrict__ part, Geo g, int Cin, int Cout,
+// CIN > 0: the input channel count as a compile-time constant (the network's 16, 32, 64, 128: the staging index
+// arithmetic then divides by constants), else Cin_rt at run time.
+template <int CIN>
+__global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restrict__ dz, const bf16* __restrict__ x,
+                                                           float* __restrict__ part, Geo g, int Cin_rt, int Cout,
                                                            int group, int chunk) {
+  const int Cin = CIN > 0 ? CIN : Cin_rt;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
   constexpr uint32_t a_bytes = kTileM * kTileK * 2;  // 16 KB
@@ -625,11 +639,13 @@ inline bool halo_fits(const Geo& g, int Cin, int Cout) {
          halo_smem(Cin, Cout) <= 227 * 1024;
 }
 
+template <int CIN>  // CIN > 0: the input channel count at compile time (constant divisors), else Cin_rt
 __global__ void __launch_bounds__(128, 1) k_conv3_fwd_halo(const bf16* __restrict__ x, const bf16* __restrict__ w,
                                                            const float* __restrict__ bias,
                                                            const bf16* __restrict__ skip, bf16* __restrict__ y,
-                                                           float* __restrict__ yf, int accum, Geo g, int Cin, int Cout,
-                                                           int relu) {
+                                                           float* __restrict__ yf, int accum, Geo g, int Cin_rt,
+                                                           int Cout, int relu) {
+  const int Cin = CIN > 0 ? CIN : Cin_rt;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
   const int nplanes = Cin / 8;
@@ -718,6 +734,34 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_halo(const bf16* __restric
 }
 
 
+// f(std::integral_constant<int, C>) with C = Cin for the channel counts that have their own instantiation, else 0
+template <class F> void with_cin(int Cin, F&& f) {
+  switch (Cin) {
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 32: f(std::integral_constant<int, 32>()); break;
+    case 64: f(std::integral_constant<int, 64>()); break;
+    case 128: f(std::integral_constant<int, 128>()); break;
+    default: f(std::integral_constant<int, 0>()); break;
+  }
+}
+template <int C> cudaError_t conv_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_fwd_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fwd_smem(kMaxC, kMaxC));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv3_wgrad_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)wgrad_smem(kMaxC));
+  return e;
+}
+cudaError_t conv_attrs_once() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    for (cudaError_t r : {conv_attrs<0>(), conv_attrs<16>(), conv_attrs<32>(), conv_attrs<64>(), conv_attrs<128>()})
+      if (r != cudaSuccess) e = r;
+  });
+  return e;
+}
+
 }  // namespace
 
 size_t fwd_work_elems(const Geo& g, int Cout) {
@@ -728,8 +772,7 @@ size_t fwd_work_elems(const Geo& g, int Cout) {
 
 cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf16* skip, bf16* y, float* yf,
                       int accum, const Geo& g, int Cin, int Cout, int relu, float* work, cudaStream_t st) {
-  static const cudaError_t attr = cudaFuncSetAttribute(k_conv3_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)fwd_smem(kMaxC, kMaxC));
+  const cudaError_t attr = conv_attrs_once();
   if (attr != cudaSuccess) return attr;
   const unsigned tiles = (unsigned)((g.M + kTileM - 1) / kTileM);
   const int per = work ? fwd_offsets_per_split(g) : 27;
@@ -740,22 +783,36 @@ cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf1
     static std::once_flag once;
     static cudaError_t hattr = cudaSuccess;
     std::call_once(once, [] {
-      hattr = cudaFuncSetAttribute(k_conv3_fwd_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      for (const void* fn : {(const void*)k_conv3_fwd_halo<0>, (const void*)k_conv3_fwd_halo<16>,
+                             (const void*)k_conv3_fwd_halo<32>, (const void*)k_conv3_fwd_halo<64>})
+        if (hattr == cudaSuccess)
+          hattr = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     });
     if (hattr != cudaSuccess) return hattr;
     const unsigned htiles = (unsigned)((g.n3 / 8) * (g.n2 / 16) * g.n1 * g.B);
-    k_conv3_fwd_halo<<<htiles, kTileM, halo_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf, accum, g, Cin, Cout,
-                                                                    relu);
+    auto go = [&](auto cc) {
+      k_conv3_fwd_halo<decltype(cc)::value><<<htiles, kTileM, halo_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf,
+                                                                                          accum, g, Cin, Cout, relu);
+    };
+    switch (Cin) {
+      case 16: go(std::integral_constant<int, 16>()); break;
+      case 32: go(std::integral_constant<int, 32>()); break;
+      case 64: go(std::integral_constant<int, 64>()); break;
+      default: go(std::integral_constant<int, 0>()); break;
+    }
     return cudaGetLastError();
   }
   if (nsplit == 1) {
-    k_conv3_fwd_tc<<<dim3(tiles, 1u), kTileM, fwd_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf, accum, g, Cin,
-                                                                         Cout, relu, 27, fwd_group(Cin), nullptr);
+    with_cin(Cin, [&](auto cc) {
+      k_conv3_fwd_tc<decltype(cc)::value><<<dim3(tiles, 1u), kTileM, fwd_smem(Cin, Cout), st>>>(
+          x, w, bias, skip, y, yf, accum, g, Cin, Cout, relu, 27, fwd_group(Cin), nullptr);
+    });
     return cudaGetLastError();
   }
-  k_conv3_fwd_tc<<<dim3(tiles, (unsigned)nsplit), kTileM, fwd_smem(Cin, Cout), st>>>(x, w, nullptr, nullptr, nullptr,
-                                                                                      nullptr, 0, g, Cin, Cout, 0,
-                                                                                      per, fwd_group(Cin), work);
+  with_cin(Cin, [&](auto cc) {
+    k_conv3_fwd_tc<decltype(cc)::value><<<dim3(tiles, (unsigned)nsplit), kTileM, fwd_smem(Cin, Cout), st>>>(
+        x, w, nullptr, nullptr, nullptr, nullptr, 0, g, Cin, Cout, 0, per, fwd_group(Cin), work);
+  });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long count = g.M * Cout;
@@ -771,15 +828,16 @@ size_t wgrad_work_elems(const Geo& g, int Cin, int Cout) {
 
 cudaError_t conv3_wgrad(const bf16* dz, const bf16* x, float* dw, float* work, const Geo& g, int Cin, int Cout,
                         cudaStream_t st) {
-  static const cudaError_t attr = cudaFuncSetAttribute(k_conv3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)wgrad_smem(kMaxC));
+  const cudaError_t attr = conv_attrs_once();
   if (attr != cudaSuccess) return attr;
   const int group = wgrad_group(Cin);
   const int chunk = wgrad_chunk(g, Cin);
   const int nchunks = (int)((g.M + chunk - 1) / chunk);
   const unsigned ngroups = (unsigned)((27 + group - 1) / group);
-  k_conv3_wgrad_tc<<<dim3(ngroups, (unsigned)nchunks), kTileM, wgrad_smem(Cout), st>>>(dz, x, work, g, Cin, Cout,
-                                                                                       group, chunk);
+  with_cin(Cin, [&](auto cc) {
+    k_conv3_wgrad_tc<decltype(cc)::value><<<dim3(ngroups, (unsigned)nchunks), kTileM, wgrad_smem(Cout), st>>>(
+        dz, x, work, g, Cin, Cout, group, chunk);
+  });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long count = 27LL * Cin * Cout;
