@@ -778,8 +778,10 @@ cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf1
   const int per = work ? fwd_offsets_per_split(g) : 27;
   const int nsplit = (27 + per - 1) / per;
   const char* conv_env = std::getenv("CLAIRE_CONV");
-  if (nsplit == 1 && halo_fits(g, Cin, Cout) && !(conv_env && std::strcmp(conv_env, "gather") == 0)) {
-    // the same MMAs from a shared-memory halo (k_conv3_fwd_halo): no per-offset gather
+  if (halo_fits(g, Cin, Cout) && !(conv_env && std::strcmp(conv_env, "gather") == 0)) {
+    // the same MMAs from a shared-memory halo (k_conv3_fwd_halo): no per-offset gather, and no offset split even
+    // on grids with few voxel tiles (a halo tile's 27 offsets cost one staging; the choice depends on the
+    // per-sample grid and the channels only, so a sample's output does not depend on its batch)
     static std::once_flag once;
     static cudaError_t hattr = cudaSuccess;
     std::call_once(once, [] {

@@ -43,11 +43,12 @@ def _idx(idx):
 
 # ---------------------------------------------------------------------------------------------------------------
 # single layers (channels-last CUDA tensors; BF16 activations and weights, FP32 gradients)
-def conv3_fwd(x, w, bias=None, skip=None, relu=False, y=None, yf=None, accum=False):
-    """y / yf = act(conv3(x, w) + bias + skip); x [B, n1, n2, n3, Cin] bf16, w [Cout, 27, Cin] bf16."""
+def conv3_fwd(x, w, bias=None, skip=None, relu=False, y=None, yf=None, accum=False, split=True):
+    """y / yf = act(conv3(x, w) + bias + skip); x [B, n1, n2, n3, Cin] bf16, w [Cout, 27, Cin] bf16. split=False
+    passes no workspace, so a gathering forward runs its 27 offsets in one CTA per voxel tile (no split-K)."""
     B, n1, n2, n3, cin = x.shape
     cout = w.shape[0]
-    nbytes = lib().claire_nn_fwd_workspace_bytes(B, n1, n2, n3, cout)
+    nbytes = lib().claire_nn_fwd_workspace_bytes(B, n1, n2, n3, cout) if split else 0
     work = _torch().empty(nbytes // 4, dtype=_torch().float32, device="cuda") if nbytes else None
     _ok(lib().claire_nn_conv3_fwd(_ptr(x), _ptr(w), _ptr(bias), _ptr(skip), _ptr(y), _ptr(yf), int(bool(accum)), B,
                                   n1, n2, n3, cin, cout, int(bool(relu)), _ptr(work), _stream()), "claire_nn_conv3_fwd")

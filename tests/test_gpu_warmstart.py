@@ -79,8 +79,10 @@ def test_conv3_forward(ws_mod, shape, cin, cout):
 @pytest.mark.parametrize("shape,cin,cout", HALO_CASES)
 def test_conv3_forward_from_halo_is_bit_identical_to_the_gather_kernel(ws_mod, shape, cin, cout, monkeypatch):
     """The forward convolution from a shared-memory halo (A operands as descriptors into the halo) against the
-    kernel that gathers each offset's neighbour rows (CLAIRE_CONV=gather): the same MMAs in the same K order, so the
-    same bits, with bias, skip, ReLU and FP32 accumulation."""
+    kernel that gathers each offset's neighbour rows (CLAIRE_CONV=gather, all 27 offsets in one CTA per tile): the
+    same MMAs in the same K order, so the same bits, with bias, skip, ReLU and FP32 accumulation. (The halo form
+    also serves the grids whose gathering forward would split the offsets over CTAs; those agree to rounding, and
+    both are held to the oracle by test_conv3_forward.)"""
     r = np.random.default_rng(7 + cin + cout)
     xg, _ = bf16(r.standard_normal(shape + (cin,)))
     wg, _ = bf16(r.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin))
@@ -95,7 +97,7 @@ def test_conv3_forward_from_halo_is_bit_identical_to_the_gather_kernel(ws_mod, s
             monkeypatch.delenv("CLAIRE_CONV", raising=False)
         y = torch.empty(shape + (cout,), dtype=torch.bfloat16, device="cuda")
         acc = base.clone()
-        ws_mod.conv3_fwd(xg, wg, bias=bg, skip=sg, relu=True, y=y, yf=acc, accum=True)
+        ws_mod.conv3_fwd(xg, wg, bias=bg, skip=sg, relu=True, y=y, yf=acc, accum=True, split=False)
         outs.append((y.cpu(), acc.cpu()))
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
