@@ -424,12 +424,54 @@ __global__ void k_relu_bwd(const float* __restrict__ dy, const bf16* __restrict_
 }
 
 // per-block channel sums: blockDim = (256 / C) C threads, thread t owns channel t % C and rows t / C + k rpb
-constexpr int kBiasBlocks = 304;
+constexpr int kBiasBlocks = 1216;  // 8 per SM: enough rows in flight for the fused ReLU backward
 __global__ void k_chan_sum(const float* __restrict__ dz, long long M, int C, float* __restrict__ part) {
   __shared__ float sh[256];
   const int c = threadIdx.x % C, r = threadIdx.x / C, rpb = blockDim.x / C;
   float s = 0.f;
   for (long long m = (long long)blockIdx.x * rpb + r; m < M; m += (long long)gridDim.x * rpb) s += dz[m * C + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < C) {
+    float t = 0.f;
+    for (int k = 0; k < rpb; ++k) t += sh[k * C + threadIdx.x];
+    part[(long long)blockIdx.x * C + threadIdx.x] = t;
+  }
+}
+
+// dzb = bf16(dy (y > 0)) (and dz = dy (y > 0) in FP32 when dz is given) fused with k_chan_sum's per-block channel
+// sums of dy (y > 0): the same rows per thread in the same order, so the same bias gradient, without re-reading dz;
+// the FP32 dz is written only for a layer whose gradient also feeds a skip connection (the weight and input
+// gradients read dzb)
+__global__ void k_relu_bwd_bias(const float* __restrict__ dy, const bf16* __restrict__ y, float* __restrict__ dz,
+                                bf16* __restrict__ dzb, long long M, int C, float* __restrict__ part) {
+  __shared__ float sh[256];
+  const int c = threadIdx.x % C, r = threadIdx.x / C, rpb = blockDim.x / C;
+  const long long step = (long long)gridDim.x * rpb;
+  float s = 0.f;
+  long long m = (long long)blockIdx.x * rpb + r;
+  // four rows' loads in flight, summed in row order
+  for (; m + 3 * step < M; m += 4 * step) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = (m + u * step) * C + c;
+      v[u] = (y == nullptr || __bfloat162float(y[i]) > 0.f) ? dy[i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (dz) dz[(m + u * step) * C + c] = v[u];
+      dzb[(m + u * step) * C + c] = __float2bfloat16_rn(v[u]);
+      s += v[u];
+    }
+  }
+  for (; m < M; m += step) {
+    const long long i = m * C + c;
+    const float v = (y == nullptr || __bfloat162float(y[i]) > 0.f) ? dy[i] : 0.f;
+    if (dz) dz[i] = v;
+    dzb[i] = __float2bfloat16_rn(v);
+    s += v;
+  }
   sh[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x < C) {
@@ -873,6 +915,16 @@ cudaError_t relu_bwd(const float* dy, const bf16* y, float* dz, bf16* dzb, long 
 }
 
 size_t bias_work_elems(int C) { return size_t(kBiasBlocks) * size_t(C); }
+
+cudaError_t relu_bwd_bias(const float* dy, const bf16* y, float* dz, bf16* dzb, long long M, int C, float* db,
+                          float* work, cudaStream_t st) {
+  const int threads = (256 / C) * C;
+  k_relu_bwd_bias<<<kBiasBlocks, threads, 0, st>>>(dy, y, dz, dzb, M, C, work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_chunks<<<sum_blocks(C), 256, 0, st>>>(work, kBiasBlocks, C, db);
+  return cudaGetLastError();
+}
 
 cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* work, cudaStream_t st) {
   const int threads = (256 / C) * C;

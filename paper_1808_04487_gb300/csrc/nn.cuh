@@ -48,6 +48,10 @@ cudaError_t relu_bwd(const float* dy, const bf16* y, float* dz, bf16* dzb, long 
 // db[c] = sum_m dz[m][c]; work holds bias_work_elems(C) floats
 size_t bias_work_elems(int C);
 cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* work, cudaStream_t st);
+// dzb = bf16(dy (y > 0)), dz = dy (y > 0) when dz != nullptr, and db = bias_grad of dy (y > 0), bit for bit, in
+// one pass
+cudaError_t relu_bwd_bias(const float* dy, const bf16* y, float* dz, bf16* dzb, long long M, int C, float* db,
+                          float* work, cudaStream_t st);
 // 2x2x2 average pooling (fine geometry gf) and its adjoint (dx overwritten or accumulated)
 cudaError_t pool_fwd(const bf16* x, bf16* y, const Geo& gf, int C, cudaStream_t st);
 cudaError_t pool_bwd(const float* dy, float* dx, int accum, const Geo& gf, int C, cudaStream_t st);

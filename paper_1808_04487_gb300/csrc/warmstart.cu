@@ -272,8 +272,8 @@ claire_status loss_grad(claire_ws* w, const float* images, const float* targets,
         const nn::Geo g = w->geo(l.level, nb);
         const float* dy = l.out >= 0 ? w->T[l.out].g : w->dpred;
         const bf16* y = (l.out >= 0 && l.relu) ? w->T[l.out].y : nullptr;
-        WS_CUDA(w, nn::relu_bwd(dy, y, w->dz, w->dzb, g.M * l.cout, st));
-        WS_CUDA(w, nn::bias_grad(w->dz, g.M, l.cout, w->G + l.boff, w->work, st));
+        WS_CUDA(w, nn::relu_bwd_bias(dy, y, l.skip >= 0 ? w->dz : nullptr, w->dzb, g.M, l.cout, w->G + l.boff,
+                                     w->work, st));
         WS_CUDA(w, nn::conv3_wgrad(w->dzb, w->T[l.in].y, w->G + l.woff, w->work, g, l.cin, l.cout, st));
         if (l.in != 0) {
           WS_CUDA(w, nn::weight_flip(w->Pb + l.woff, w->Wt + l.woff, l.cin, l.cout, st));
