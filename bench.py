@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the two-level preconditioner variant")
     ap.add_argument("--large-check", type=int, default=256, help="large: grid of the BF16-vs-FP32 history check")
+    ap.add_argument("--large-precond", type=lambda t: tuple(int(x) for x in t.split(",")), default=(0, 1),
+                    help="large: preconditioners to run, comma-separated (0 spectral, 1 two-level)")
     ap.add_argument("--study", default=None,
                     choices=[None, "precision", "batch", "warmstart", "models", "large", "oracle"],
                     help="precision: FP32 and FP32 + BF16 gradient history against the FP64 path; batch: 64 "
@@ -918,10 +920,11 @@ def paper_synthetic_on_device(n, dev):
 
 def large_study(args):
     """Large single-GPU grids (Tab. 4, Sec. 4.7): the H1-div synthetic problem of Sec. 4.2 (beta_v 1e-3, beta_w
-    1e-4, H1, spectral preconditioner, FP32 fields, to ||g|| <= 1e-2 ||g(0)||) at --size (default 1024^3) with the
-    gradient history of the state stored in BF16 (bf16_mask = 1), which with the lean workspace layout lets the
-    1024^3 problem fit in HBM. Reports time, GN/matvec/PDE counts and the device memory in use; at --large-check
-    (default 256) the same problem is also solved with and without BF16 storage to state the error this adds."""
+    1e-4, H1, FP32 fields, to ||g|| <= 1e-2 ||g(0)||) at --size (1024 for Tab. 4's grid) with the gradient history
+    of the state stored in BF16 (bf16_mask = 1), which with the lean workspace layout lets the 1024^3 problem fit in
+    HBM, once per preconditioner in --large-precond (spectral, and the two-level preconditioner of Sec. 2.3.3 that
+    Tab. 4 uses). Reports time, GN/matvec/PDE counts and the device memory in use; at --large-check (default 256)
+    the same problem is also solved with and without BF16 storage to state the error this adds."""
     import torch
 
     import paper_1808_04487_gb300 as pkg
@@ -957,29 +960,36 @@ def large_study(args):
     n = (args.size,) * 3
     mT, v = paper_synthetic_on_device(n, dev)
     torch.cuda.empty_cache()  # return the FP64 temporaries of the composition before the workspace is allocated
-    free0, total = torch.cuda.mem_get_info()
-    ctx = pkg.Context(n, precision="f32", bf16_mask=1, **kw)
-    mR = ctx.transport(mT, v, +1)
-    free1, _ = torch.cuda.mem_get_info()
-    runs = []
-    for it in range(max(1, args.steps) + 1):  # the first solve also runs the gather autotuner
-        v.zero_()
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        _, rep, st = ctx.register(mT, mR, v)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - a
-        runs.append(dt)
-        log("%s solve %d: %.2f s, %d GN, %d matvecs, status %s" % (n, it, dt, rep["gn_iters"], rep["matvecs"], st))
-    out["runs"].append({"n": list(n), "seconds": min(runs[1:]) if len(runs) > 1 else runs[0], "status": st,
-                        **{k: rep[k] for k in keys}, "rel_mismatch": rep["mismatch_rel"],
-                        "rel_grad": rep["gnorm_rel"], "bf16_gradient_history": True,
-                        "workspace_gb": ctx.workspace_bytes() / 1e9,
-                        "device_used_gb": (total - free1) / 1e9, "device_total_gb": total / 1e9,
-                        "caller_arrays_gb": 5 * mT.numel() * 4 / 1e9,
-                        "note": "Tab. 4 (Sec. 4.7) context: the paper's 1024^3 run took 136.8 s on 256 and 15.5 s on "
-                                "4096 MPI tasks (two-level preconditioner, CPU cluster)"})
-    ctx.close()
+    mR = None
+    for name, precond in (("spectral", 0), ("two-level", 1)):
+        if precond not in args.large_precond:
+            continue
+        ctx = pkg.Context(n, precision="f32", bf16_mask=1, precond=precond, **kw)
+        if mR is None:
+            mR = ctx.transport(mT, v, +1)
+        free1, total = torch.cuda.mem_get_info()
+        runs = []
+        for it in range(max(1, args.steps) + 1):  # the first solve also runs the gather autotuner
+            v.zero_()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            _, rep, st = ctx.register(mT, mR, v)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - a
+            runs.append(dt)
+            log("%s %s solve %d: %.2f s, %d GN, %d matvecs, %d coarse matvecs, status %s"
+                % (n, name, it, dt, rep["gn_iters"], rep["matvecs"], rep["coarse_matvecs"], st))
+        out["runs"].append({"n": list(n), "preconditioner": name,
+                            "seconds": min(runs[1:]) if len(runs) > 1 else runs[0], "status": st,
+                            **{k: rep[k] for k in keys + ("coarse_matvecs",)}, "rel_mismatch": rep["mismatch_rel"],
+                            "rel_grad": rep["gnorm_rel"], "bf16_gradient_history": True,
+                            "workspace_gb": ctx.workspace_bytes() / 1e9,
+                            "device_used_gb": (total - free1) / 1e9, "device_total_gb": total / 1e9,
+                            "caller_arrays_gb": 5 * mT.numel() * 4 / 1e9})
+        ctx.close()
+        torch.cuda.empty_cache()
+    out["note"] = ("Tab. 4 (Sec. 4.7) context: the paper's 1024^3 run took 136.8 s on 256 and 15.5 s on 4096 MPI "
+                   "tasks (two-level preconditioner, CPU cluster)")
     print(json.dumps(out), flush=True)
     return 0
 

@@ -133,7 +133,7 @@ claire_status claire_destroy(claire_ctx* ctx);
 /* Message of the last failure on ctx ("" if none). The pointer stays valid until the next call on ctx. */
 const char* claire_last_error(const claire_ctx* ctx);
 
-/* Bytes of device workspace the context holds. */
+/* Bytes of device workspace the context holds (with the two-level preconditioner: including its coarse context). */
 size_t claire_workspace_bytes(const claire_ctx* ctx);
 
 /* ---- transport (Eq. (2) state, Eq. (4) continuity-form adjoint; Sec. 2.3.1 semi-Lagrangian RK2) ----------------

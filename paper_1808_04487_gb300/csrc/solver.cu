@@ -61,13 +61,17 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
   }
   ok &= takeT(W.b, 3 * N);
   ok &= takeC(W.spec, 6 * Ns);
-  for (T** p : {&W.s, &W.vtrial}) ok &= takeT(*p, 3 * N);
+  ok &= takeT(W.s, 3 * N);
   if (c->is_coarse) {
-    // the two-level preconditioner's coarse problem keeps its restricted m_T and v here
+    // the two-level preconditioner's coarse problem keeps its restricted m_T and v here; it runs no line search
+    // (no trial velocity) and restricts v through W.Gh (no master copy V^)
     ok &= takeT(W.vdev, 3 * N);
     ok &= takeT(W.mTdev, N);
+    for (cplx<T>** p : {&W.Gh, &W.Rh, &W.Sh, &W.VTh}) ok &= takeC(*p, 3 * Ns);
+  } else {
+    ok &= takeT(W.vtrial, 3 * N);
+    for (cplx<T>** p : {&W.Vh, &W.Vtrh, &W.Gh, &W.Rh, &W.Sh, &W.VTh}) ok &= takeC(*p, 3 * Ns);
   }
-  for (cplx<T>** p : {&W.Vh, &W.Vtrh, &W.Gh, &W.Rh, &W.Sh, &W.VTh}) ok &= takeC(*p, 3 * Ns);
   // the transform of the time integral and the inverse-transform work array share the six spectra of W.spec:
   // neither is live while a spectral operator works in W.spec
   W.Bh = W.spec;
@@ -88,12 +92,13 @@ template <class T> claire_status alloc_work(claire_ctx* c) {
 template <class T> size_t work_bytes(const claire_opts& o, const Dims& d, bool coarse) {
   const long long N = d.N, Ns = d.Ns;
   const int nt = o.nt;
-  // dX, dY; m history; (rho, rho lambda ping/pong); lambda ping/pong; b; s, vtrial; (coarse: v, m_T)
-  const long long elems = 3 * N * 2 + (nt + 1) * N + (o.divfree ? 0 : 3 * N) + 2 * N + 3 * N + 2 * 3 * N +
-                          (coarse ? 4 * N : 0);
+  // dX, dY; m history; (rho, rho lambda ping/pong); lambda ping/pong; b; s; vtrial (coarse: v, m_T instead)
+  const long long elems = 3 * N * 2 + (nt + 1) * N + (o.divfree ? 0 : 3 * N) + 2 * N + 3 * N + 3 * N +
+                          (coarse ? 4 * N : 3 * N);
   // gradient history, FP32/FP64 or BF16
   const size_t gm_bytes = (o.bf16_mask & 1) ? 2 * size_t(3 * (nt + 1) * N) : sizeof(T) * size_t(3 * (nt + 1) * N);
-  const long long celems = 6 * Ns + 6 * 3 * Ns;
+  // spec; the Fourier-domain solver vectors (V^, V^trial, G^, R^, S^, V~^; the coarse problem needs four)
+  const long long celems = 6 * Ns + (coarse ? 4 : 6) * 3 * Ns;
   const Launch3 L = launch3(d);
   const long long nbig = (long long)L.grid.x * L.grid.y * L.grid.z;
   // FP32 contexts also hold FP64 twiddle tables (stand-alone operators transform some inputs in FP64)
@@ -529,8 +534,8 @@ template <class T> claire_status coarse_linearize(claire_ctx* c, cudaStream_t st
   Work<T>& W = c->work<T>();
   claire_ctx* cc = c->coarse;
   Work<T>& Wc = cc->work<T>();
-  CL_TRY(tl_restrict<T>(c, cc, W.Vh, Wc.Vh, nullptr, nullptr, 3, false, Wc.partials, st));
-  CL_TRY(vec_c2r<T>(cc, Wc.Vh, Wc.vdev, st));
+  CL_TRY(tl_restrict<T>(c, cc, W.Vh, Wc.Gh, nullptr, nullptr, 3, false, Wc.partials, st));  // G^ is free here
+  CL_TRY(vec_c2r<T>(cc, Wc.Gh, Wc.vdev, st));
   return linearize<T>(cc, Wc.mTdev, Wc.vdev, st);
 }
 
@@ -2241,7 +2246,9 @@ claire_status claire_destroy(claire_ctx* c) {
 
 const char* claire_last_error(const claire_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-size_t claire_workspace_bytes(const claire_ctx* c) { return c ? c->arena_bytes : 0; }
+size_t claire_workspace_bytes(const claire_ctx* c) {
+  return c ? c->arena_bytes + (c->coarse ? c->coarse->arena_bytes : 0) : 0;
+}
 
 claire_status claire_get_counters(const claire_ctx* c, claire_counters* out) {
   if (!c || !out) return CLAIRE_EINVAL;
