@@ -418,7 +418,8 @@ claire_status claire_ws_predict_f32(claire_ws* ws, claire_ctx* ctx, const float*
  * the weights of the adjoint convolution, [Cin][27][Cout]. relu_bwd: dz = dy where y > 0 (y NULL: everywhere),
  * FP32 dz and BF16 dzb. bias_grad: db[c] = sum_m dz[m][c] (work: claire_nn_bias_workspace_bytes). pool: 2x2x2
  * average over the fine grid (n1, n2, n3 even) and its adjoint; up: nearest-neighbour x2 from the coarse grid
- * (n1, n2, n3) and its adjoint (accum = 1 adds to dx). mse: loss partials (FP64, npartials blocks) of the mean
+ * (n1, n2, n3) and its adjoint (accum = 1 adds to dx); for both, the fine grid's B n1 n2 n3 C values must stay below
+ * 2^31 (CLAIRE_EINVAL otherwise). mse: loss partials (FP64, npartials blocks) of the mean
  * squared error over the first cu of C channels, grad (optional) = d loss / d pred. adam: one bias-corrected Adam
  * step number `step` >= 1; pb (optional) receives a BF16 copy of p. */
 claire_status claire_nn_conv3_fwd(const void* x, const void* w, const float* bias, const void* skip, void* y,

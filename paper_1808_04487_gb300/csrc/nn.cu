@@ -74,6 +74,58 @@ __device__ __forceinline__ int nb_of(const Geo& g, const Nbr& n, int off) {
   return (sel3(n.r1, off / 9) + sel3(n.r2, (off / 3) % 3)) * g.n3 + sel3(n.r3, off % 3);
 }
 
+// Epilogue of the forward kernels for 16 consecutive output channels c0 .. c0+15 of voxel row m (v: the FP32
+// accumulators): val = v + bias + skip, ReLU, then y (BF16) and/or yf (FP32, overwritten or accumulated), with
+// 16-byte accesses (the per-channel arithmetic and its order are those of a scalar loop over the channels)
+__device__ __forceinline__ void conv_epilogue16(float* v, long long m, int c0, int Cout, const float* __restrict__ bias,
+                                                const bf16* __restrict__ skip, bf16* __restrict__ y,
+                                                float* __restrict__ yf, int accum, int relu) {
+  const long long o = m * Cout + c0;
+  if (bias) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] += bias[c0 + j];
+  }
+  if (skip) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint4 u = *reinterpret_cast<const uint4*>(skip + o + 8 * h);
+      const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(b2[k]);
+        v[8 * h + 2 * k] += f.x;
+        v[8 * h + 2 * k + 1] += f.y;
+      }
+    }
+  }
+  if (relu) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+  }
+  if (y) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint4 u;
+      __nv_bfloat162* b2 = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) b2[k] = __floats2bfloat162_rn(v[8 * h + 2 * k], v[8 * h + 2 * k + 1]);
+      *reinterpret_cast<uint4*>(y + o + 8 * h) = u;
+    }
+  }
+  if (yf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4* d = reinterpret_cast<float4*>(yf + o + 4 * q);
+      float4 r = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      if (accum) {
+        const float4 a = *d;
+        r = make_float4(a.x + r.x, a.y + r.y, a.z + r.z, a.w + r.w);
+      }
+      *d = r;
+    }
+  }
+}
+
 // Forward convolution on tcgen05: 128 threads; thread r stages row r (voxel m0 + r). Offsets [off0, off1) of the
 // 27 (split-K when the grid has few voxel tiles: blockIdx.y picks the range), taken G = group at a time so that
 // a K step spans G Cin = min(64, Cin) or more channels: the A tile row r holds x[nb(m0 + r, off), ci] for the G
@@ -136,28 +188,28 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict_
       ok = __syncthreads_and(mine) != 0;
       if (!ok) break;
     }
-    unsigned char* As = sm + sidx * stage_bytes;
-    unsigned char* Bs = As + a_bytes;
+    // neighbour rows (zero-filled past the last voxel) and the weight slice by cp.async: all of the thread's
+    // copies in flight at once
+    const uint32_t As = base + sidx * stage_bytes;
+    const uint32_t Bs = As + a_bytes;
     for (int off = oa; off < ob; ++off) {
-      const uint4* src = reinterpret_cast<const uint4*>(x + (long long)nb_of(g, nb, off) * Cin);
+      const bf16* src = valid ? x + (long long)nb_of(g, nb, off) * Cin : x;
       const int kb = (off - oa) * Cin;
-      for (int c = 0; c < nvec; ++c) {
-        const uint4 v = valid ? src[c] : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(As + tc::kmajor_offset(tid, kb + 8 * c, KS)) = v;
-      }
+      for (int c = 0; c < nvec; ++c)
+        tc::cp_async_16_zfill(As + tc::kmajor_offset(tid, kb + 8 * c, KS), src + 8 * c, valid);
     }
     const int nv = nk / 8;
     auto stage_w = [&](int nvc) {
       for (int q = tid; q < Cout * nvc; q += kTileM) {
         const int co = q / nvc, c = q - co * nvc;
-        *reinterpret_cast<uint4*>(Bs + tc::kmajor_offset(co, 8 * c, KS)) =
-            *reinterpret_cast<const uint4*>(w + ((long long)co * 27 + oa) * Cin + 8 * c);
+        tc::cp_async_16(Bs + tc::kmajor_offset(co, 8 * c, KS), w + ((long long)co * 27 + oa) * Cin + 8 * c);
       }
     };
     if (CIN > 0 && nk == KS)
       stage_w(CIN > 0 ? (CIN < 64 ? 64 / CIN : 1) * CIN / 8 : 1);  // a full step: a constant divisor
     else
       stage_w(nv);
+    tc::cp_async_wait_all();
     tc::fence_smem_to_async();
     __syncthreads();
     if (tid == 0) {
@@ -193,21 +245,11 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict_
       tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
       if (r < g.M) {
         if (part) {
-          float* dst = part + ((long long)blockIdx.y * g.M + r) * Cout + c0;
+          float4* dst = reinterpret_cast<float4*>(part + ((long long)blockIdx.y * g.M + r) * Cout + c0);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) dst[j] = v[j];
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int co = c0 + j;
-            const long long o = (long long)r * Cout + co;
-            float val = v[j];
-            if (bias) val += bias[co];
-            if (skip) val += __bfloat162float(skip[o]);
-            if (relu) val = fmaxf(val, 0.f);
-            if (y) y[o] = __float2bfloat16_rn(val);
-            if (yf) yf[o] = accum ? yf[o] + val : val;
-          }
+          conv_epilogue16(v, r, c0, Cout, bias, skip, y, yf, accum, relu);
         }
       }
     }
@@ -221,11 +263,21 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_tc(const bf16* __restrict_
 __global__ void k_conv3_reduce(const float* __restrict__ part, int nsplit, const float* __restrict__ bias,
                                const bf16* __restrict__ skip, bf16* __restrict__ y, float* __restrict__ yf, int accum,
                                long long count, int Cout, int relu) {
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < count;
-       o += (long long)gridDim.x * blockDim.x) {
+  const long long step = (long long)gridDim.x * blockDim.x;
+  const int co_step = (int)(step % Cout);
+  long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int co = (int)(o % Cout);
+  for (; o < count; o += step, co = co + co_step >= Cout ? co + co_step - Cout : co + co_step) {
     float val = 0.f;
-    for (int sp = 0; sp < nsplit; ++sp) val += part[(long long)sp * count + o];
-    const int co = (int)(o % Cout);
+    int sp = 0;
+    for (; sp + 8 <= nsplit; sp += 8) {  // eight loads in flight, added in split order
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = part[(long long)(sp + u) * count + o];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) val += v[u];
+    }
+    for (; sp < nsplit; ++sp) val += part[(long long)sp * count + o];
     if (bias) val += bias[co];
     if (skip) val += __bfloat162float(skip[o]);
     if (relu) val = fmaxf(val, 0.f);
@@ -372,33 +424,66 @@ __global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restric
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
-// dst[i] = sum_c part[c][i] in a fixed order: a CTA takes 32 consecutive i, each of its 8 warps sums one contiguous
-// eighth of the chunks in order (coalesced 128-byte rows), and the 8 range sums are added in order. (One thread per
-// i summing all chunks in order left a few dozen CTAs on the GPU, each thread a chain of ~190 strided loads.)
-__global__ void __launch_bounds__(256) k_sum_chunks(const float* __restrict__ part, int nchunks, long long count,
-                                                    float* __restrict__ dst) {
-  __shared__ float red[8][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int per = (nchunks + 7) / 8;
-  const int c0 = w * per, c1 = min(nchunks, c0 + per);
-  for (long long base = (long long)blockIdx.x * 32; base < count; base += (long long)gridDim.x * 32) {
-    const long long i = base + lane;
+// Fixed-order sums over chunks: dst[i] = sum_c part[c][i]. A 256-thread CTA takes opb consecutive outputs i
+// (opb = 32, or 8 for short outputs such as per-channel bias partials); thread t sums range r = t / opb, one
+// contiguous (256 / opb)-th of the chunks, in chunk order with eight loads in flight, and the range sums are added in
+// range order. Two independent jobs share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias
+// gradient of a layer is summed in the launch that sums its weight gradient. (One thread per i summing all chunks
+// in order left a few dozen CTAs on the GPU, each thread a chain of ~190 strided loads.)
+struct SumJob {
+  const float* part;
+  float* dst;
+  long long count;
+  int nchunks, opb, blocks;
+};
+inline SumJob sum_job(const float* part, int nchunks, long long count, float* dst) {
+  SumJob j;
+  j.part = part;
+  j.dst = dst;
+  j.count = count;
+  j.nchunks = nchunks;
+  j.opb = count < 32 * 152 ? 8 : 32;
+  const long long b = (count + j.opb - 1) / j.opb;
+  j.blocks = (int)(b < 4864 ? (b > 0 ? b : 1) : 4864);
+  return j;
+}
+__global__ void __launch_bounds__(256) k_sum_chunks(SumJob a, SumJob b) {
+  __shared__ float red[256];
+  const bool first = (int)blockIdx.x < a.blocks;
+  const SumJob& j = first ? a : b;
+  const int blk = first ? (int)blockIdx.x : (int)blockIdx.x - a.blocks;
+  const int oi = threadIdx.x % j.opb, r = threadIdx.x / j.opb, R = 256 / j.opb;
+  const int per = (j.nchunks + R - 1) / R;
+  const int c0 = r * per, c1 = min(j.nchunks, c0 + per);
+  for (long long base = (long long)blk * j.opb; base < j.count; base += (long long)j.blocks * j.opb) {
+    const long long i = base + oi;
     float s = 0.f;
-    if (i < count)
-      for (int c = c0; c < c1; ++c) s += part[(long long)c * count + i];
-    red[w][lane] = s;
+    if (i < j.count) {
+      int c = c0;
+      for (; c + 8 <= c1; c += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = j.part[(long long)(c + u) * j.count + i];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+      }
+      for (; c < c1; ++c) s += j.part[(long long)c * j.count + i];
+    }
+    red[threadIdx.x] = s;
     __syncthreads();
-    if (w == 0 && i < count) {
-      float t = red[0][lane];
-      for (int k = 1; k < 8; ++k) t += red[k][lane];
-      dst[i] = t;
+    if ((int)threadIdx.x < j.opb && base + threadIdx.x < j.count) {
+      float t = red[threadIdx.x];
+      for (int k = 1; k < R; ++k) t += red[k * j.opb + threadIdx.x];
+      j.dst[base + threadIdx.x] = t;
     }
     __syncthreads();
   }
 }
-inline unsigned sum_blocks(long long count) {
-  const long long b = (count + 31) / 32;
-  return (unsigned)(b < 4864 ? (b > 0 ? b : 1) : 4864);
+inline cudaError_t sum_chunks(const SumJob& a, const SumJob* b, cudaStream_t st) {
+  SumJob none = a;
+  none.blocks = 0;
+  k_sum_chunks<<<a.blocks + (b ? b->blocks : 0), 256, 0, st>>>(a, b ? *b : none);
+  return cudaGetLastError();
 }
 
 __global__ void k_wt_flip(const bf16* __restrict__ w, bf16* __restrict__ wt, int Cin, int Cout) {
@@ -410,6 +495,22 @@ __global__ void k_wt_flip(const bf16* __restrict__ w, bf16* __restrict__ wt, int
     const int off = (int)(t % 27);
     const int co = (int)(t / 27);
     wt[((long long)ci * 27 + (26 - off)) * Cout + co] = w[i];
+  }
+}
+
+// k_wt_flip for a table of layers in one launch: element i of the concatenated weights belongs to the layer t with
+// start[t] <= i < start[t + 1]
+__global__ void k_wt_flip_all(const bf16* __restrict__ w, bf16* __restrict__ wt, FlipTable tab) {
+  const long long total = tab.start[tab.n];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int t = 0;
+    while (t + 1 < tab.n && i >= tab.start[t + 1]) ++t;
+    const int j = (int)(i - tab.start[t]);  // below 27 x 128 x 128 (32-bit index arithmetic)
+    const int Cin = tab.cin[t], Cout = tab.cout[t];
+    const int q = j / Cin, ci = j - q * Cin;
+    const int co = q / 27, off = q - co * 27;
+    wt[tab.woff[t] + (ci * 27 + (26 - off)) * Cout + co] = w[tab.woff[t] + j];
   }
 }
 
@@ -481,80 +582,191 @@ __global__ void k_relu_bwd_bias(const float* __restrict__ dy, const bf16* __rest
   }
 }
 
-// fine voxel of the 2x2x2 block (d = 4 d1 + 2 d2 + d3) under coarse voxel (b, k1, k2, k3)
-__device__ __forceinline__ long long fine_of(const Geo& gc, int b, int k1, int k2, int k3, int d) {
-  return (((long long)b * (2 * gc.n1) + 2 * k1 + (d >> 2)) * (2 * gc.n2) + 2 * k2 + ((d >> 1) & 1)) * (2 * gc.n3) +
-         2 * k3 + (d & 1);
+// Pooling and upsampling: thread (coarse voxel p, channel vector cv) moves V channels (V = 8 BF16 or 4 FP32 in
+// one 16-byte access when C allows, else 1) between p and the 2 x 2 x 2 fine voxels under it, fine voxel
+// d = 4 d1 + 2 d2 + d3 at f0 + d1 P + d2 R + d3 (R = fine row, P = fine plane); sums run over d in ascending order.
+struct Block8 {
+  long long f0;
+  long long R, P;
+  __device__ __forceinline__ long long at(int d) const { return f0 + (d >> 2) * P + ((d >> 1) & 1) * R + (d & 1); }
+};
+__device__ __forceinline__ Block8 block_of(const Geo& gc, int p) {
+  const Vox v = vox_of(gc, p);
+  Block8 k;
+  k.R = 2LL * gc.n3;
+  k.P = 4LL * gc.n2 * gc.n3;
+  k.f0 = ((long long)(v.b * gc.n1 + v.i1) * 2 * (2 * gc.n2) + 2 * v.i2) * (2 * gc.n3) + 2 * v.i3;
+  return k;
 }
-__device__ __forceinline__ long long coarse_of(const Geo& gc, long long f) {
-  const int N3 = 2 * gc.n3, N2 = 2 * gc.n2, N1 = 2 * gc.n1;
-  const int j3 = (int)(f % N3);
-  long long t = f / N3;
-  const int j2 = (int)(t % N2);
-  t /= N2;
-  const int j1 = (int)(t % N1);
-  const int b = (int)(t / N1);
-  return (((long long)b * gc.n1 + j1 / 2) * gc.n2 + j2 / 2) * gc.n3 + j3 / 2;
-}
-__device__ __forceinline__ void coarse_coords(const Geo& gc, long long p, int& b, int& k1, int& k2, int& k3) {
-  k3 = (int)(p % gc.n3);
-  long long t = p / gc.n3;
-  k2 = (int)(t % gc.n2);
-  t /= gc.n2;
-  k1 = (int)(t % gc.n1);
-  b = (int)(t / gc.n1);
-}
-
-__global__ void k_pool_fwd(const bf16* __restrict__ x, bf16* __restrict__ y, Geo gc, int C) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gc.M * C;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    int b, k1, k2, k3;
-    coarse_coords(gc, i / C, b, k1, k2, k3);
-    float s = 0.f;
-    for (int d = 0; d < 8; ++d) s += __bfloat162float(x[fine_of(gc, b, k1, k2, k3, d) * C + c]);
-    y[i] = __float2bfloat16_rn(0.125f * s);
+template <int V> __device__ __forceinline__ void ld_vec(const bf16* p, float* f) {
+  if constexpr (V == 8) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 t = __bfloat1622float2(h[k]);
+      f[2 * k] = t.x;
+      f[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) f[k] = __bfloat162float(p[k]);
   }
 }
-__global__ void k_pool_bwd(const float* __restrict__ dy, float* __restrict__ dx, int accum, Geo gc, int C) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gc.M * 8 * C;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float v = 0.125f * dy[coarse_of(gc, i / C) * C + i % C];
-    dx[i] = accum ? dx[i] + v : v;
+template <int V> __device__ __forceinline__ void ld_vec(const float* p, float* f) {
+  if constexpr (V == 4) {
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    f[0] = u.x;
+    f[1] = u.y;
+    f[2] = u.z;
+    f[3] = u.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) f[k] = p[k];
   }
 }
-__global__ void k_up_fwd(const bf16* __restrict__ x, bf16* __restrict__ y, Geo gc, int C) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gc.M * 8 * C;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] = x[coarse_of(gc, i / C) * C + i % C];
-}
-__global__ void k_up_bwd(const float* __restrict__ dy, float* __restrict__ dx, int accum, Geo gc, int C) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < gc.M * C;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    int b, k1, k2, k3;
-    coarse_coords(gc, i / C, b, k1, k2, k3);
-    float s = 0.f;
-    for (int d = 0; d < 8; ++d) s += dy[fine_of(gc, b, k1, k2, k3, d) * C + c];
-    dx[i] = accum ? dx[i] + s : s;
+template <int V> __device__ __forceinline__ void st_vec(float* p, const float* f) {
+  if constexpr (V == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(f[0], f[1], f[2], f[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) p[k] = f[k];
   }
 }
 
+template <int V>
+__global__ void k_pool_fwd(const bf16* __restrict__ x, bf16* __restrict__ y, Geo gc, int C, FastDiv by_g) {
+  const long long total = gc.M * (C / V);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)by_g.div((unsigned)i), c = (int)(i - (long long)p * (C / V)) * V;
+    const Block8 k = block_of(gc, p);
+    float s[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) s[j] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      float f[V];
+      ld_vec<V>(x + k.at(d) * C + c, f);
+#pragma unroll
+      for (int j = 0; j < V; ++j) s[j] += f[j];
+    }
+    bf16* dst = y + (long long)p * C + c;
+    if constexpr (V == 8) {
+      uint4 u;
+      __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(0.125f * s[2 * j], 0.125f * s[2 * j + 1]);
+      *reinterpret_cast<uint4*>(dst) = u;
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) dst[j] = __float2bfloat16_rn(0.125f * s[j]);
+    }
+  }
+}
+template <int V>
+__global__ void k_pool_bwd(const float* __restrict__ dy, float* __restrict__ dx, int accum, Geo gc, int C,
+                           FastDiv by_g) {
+  const long long total = gc.M * (C / V);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)by_g.div((unsigned)i), c = (int)(i - (long long)p * (C / V)) * V;
+    const Block8 k = block_of(gc, p);
+    float v[V];
+    ld_vec<V>(dy + (long long)p * C + c, v);
+#pragma unroll
+    for (int j = 0; j < V; ++j) v[j] *= 0.125f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      float* dst = dx + k.at(d) * C + c;
+      float o[V];
+      if (accum) {
+        ld_vec<V>(dst, o);
+#pragma unroll
+        for (int j = 0; j < V; ++j) o[j] += v[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) o[j] = v[j];
+      }
+      st_vec<V>(dst, o);
+    }
+  }
+}
+template <int V>
+__global__ void k_up_fwd(const bf16* __restrict__ x, bf16* __restrict__ y, Geo gc, int C, FastDiv by_g) {
+  const long long total = gc.M * (C / V);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)by_g.div((unsigned)i), c = (int)(i - (long long)p * (C / V)) * V;
+    const Block8 k = block_of(gc, p);
+    if constexpr (V == 8) {
+      const uint4 u = *reinterpret_cast<const uint4*>(x + (long long)p * C + c);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) *reinterpret_cast<uint4*>(y + k.at(d) * C + c) = u;
+    } else {
+      bf16 u[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) u[j] = x[(long long)p * C + c + j];
+#pragma unroll
+      for (int d = 0; d < 8; ++d)
+#pragma unroll
+        for (int j = 0; j < V; ++j) y[k.at(d) * C + c + j] = u[j];
+    }
+  }
+}
+template <int V>
+__global__ void k_up_bwd(const float* __restrict__ dy, float* __restrict__ dx, int accum, Geo gc, int C,
+                         FastDiv by_g) {
+  const long long total = gc.M * (C / V);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)by_g.div((unsigned)i), c = (int)(i - (long long)p * (C / V)) * V;
+    const Block8 k = block_of(gc, p);
+    float s[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) s[j] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      float f[V];
+      ld_vec<V>(dy + k.at(d) * C + c, f);
+#pragma unroll
+      for (int j = 0; j < V; ++j) s[j] += f[j];
+    }
+    float* dst = dx + (long long)p * C + c;
+    if (accum) {
+      float o[V];
+      ld_vec<V>(dst, o);
+#pragma unroll
+      for (int j = 0; j < V; ++j) s[j] += o[j];
+    }
+    st_vec<V>(dst, s);
+  }
+}
+
+// loss partials (FP64) and gradient of the mean squared error over the first cu of C channels: thread per voxel,
+// C gradient values written (zero past cu), 16-byte stores when C allows
 __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ pred, const float* __restrict__ target,
                                              float* __restrict__ grad, long long M, int C, int cu, double inv_count,
                                              double* __restrict__ partials) {
   double acc = 0.0;
   const float gscale = float(2.0 * inv_count);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M * C;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    float gval = 0.f;
-    if (c < cu) {
-      const float e = pred[i] - target[(i / C) * cu + c];
-      acc += double(e) * double(e);
-      gval = gscale * e;
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (long long)gridDim.x * blockDim.x) {
+    float e[4] = {0.f, 0.f, 0.f, 0.f};  // the first min(cu, 4) errors
+    for (int c = 0; c < cu; ++c) {
+      const float ec = pred[m * C + c] - target[m * cu + c];
+      acc += double(ec) * double(ec);
+      if (c < 4) e[c] = ec;
     }
-    if (grad) grad[i] = gval;
+    if (!grad) continue;
+    float* g = grad + m * C;
+    if (C % 4 == 0 && cu <= 4) {
+      *reinterpret_cast<float4*>(g) = make_float4(gscale * e[0], 1 < cu ? gscale * e[1] : 0.f,
+                                                  2 < cu ? gscale * e[2] : 0.f, 3 < cu ? gscale * e[3] : 0.f);
+      for (int c = 4; c < C; c += 4) *reinterpret_cast<float4*>(g + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int c = 0; c < C; ++c) g[c] = c < cu ? gscale * (pred[m * C + c] - target[m * cu + c]) : 0.f;
+    }
   }
   __shared__ double red[8];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -583,17 +795,37 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, floa
   }
 }
 
-// network input: channel 0 = m_T, channel 1 = sdiff (m_R - m_T) (formed in FP32 before rounding), others 0
-__global__ void k_pack_images(const float* __restrict__ src, bf16* __restrict__ dst, long long M, int C,
-                              float sdiff) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M * C;
+// network input of a minibatch: sample b (of nb) is images[idx[b]] = (m_T, m_R), [2][N0]; channel 0 = m_T,
+// channel 1 = sdiff (m_R - m_T) (formed in FP32 before rounding), channels 2 .. C-1 zero; thread per voxel
+__global__ void k_pack_images(const float* __restrict__ images, SampleIdx idx, int nb, bf16* __restrict__ dst,
+                              long long N0, int C, float sdiff) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb * N0;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long long m = i / C;
-    float v = 0.f;
-    if (c == 0) v = src[m];
-    if (c == 1) v = sdiff * (src[M + m] - src[m]);
-    dst[i] = __float2bfloat16_rn(v);
+    const int b = (int)(i / N0);
+    const long long m = i - b * N0;
+    const float* src = images + idx.v[b] * 2 * N0;
+    const float v0 = src[m], v1 = sdiff * (src[N0 + m] - src[m]);
+    bf16* d = dst + i * C;
+    if (C % 8 == 0) {
+      uint4 u = make_uint4(0u, 0u, 0u, 0u);
+      __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      u.x = *reinterpret_cast<unsigned*>(&h);
+      *reinterpret_cast<uint4*>(d) = u;
+      for (int c = 8; c < C; c += 8) *reinterpret_cast<uint4*>(d + c) = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      for (int c = 0; c < C; ++c) d[c] = __float2bfloat16_rn(c == 0 ? v0 : (c == 1 ? v1 : 0.f));
+    }
+  }
+}
+// targets of a minibatch: dst[b][m][c] = s * targets[idx[b]][c][m] (ncomp components); thread per voxel
+__global__ void k_interleave_batch(const float* __restrict__ targets, SampleIdx idx, int nb, float* __restrict__ dst,
+                                   long long N0, int ncomp, float s) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb * N0;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / N0);
+    const long long m = i - b * N0;
+    const float* src = targets + idx.v[b] * ncomp * N0 + m;
+    for (int c = 0; c < ncomp; ++c) dst[i * ncomp + c] = s * src[c * N0];
   }
 }
 __global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst, long long M, int ncomp, int C,
@@ -603,12 +835,6 @@ __global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst,
     const int c = (int)(i / M);
     dst[i] = s * src[(i - (long long)c * M) * C + c];
   }
-}
-__global__ void k_interleave(const float* __restrict__ src, float* __restrict__ dst, long long M, int ncomp,
-                             float s) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M * ncomp;
-       i += (long long)gridDim.x * blockDim.x)
-    dst[i] = s * src[(long long)(i % ncomp) * M + i / ncomp];
 }
 __global__ void k_add_f32(const float* __restrict__ a, float* __restrict__ b, long long count) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -661,24 +887,32 @@ inline int fwd_offsets_per_split(const Geo& g) {
 inline size_t wgrad_smem(int Cout) { return 1024 + 2 * (size_t(kTileM) * kTileK * 2 + size_t(Cout) * kTileK * 2) + 32; }
 
 // ---- forward convolution from a shared-memory halo -----------------------------------------------------------
-// A CTA covers a tile of 8 (i3) x 16 (i2) voxels of one i1 plane of one sample (128 rows of the implicit GEMM).
-// Its input halo -- the 10 x 18 x 3 voxels around the tile, periodic -- is loaded once, as Cin/8 planes of 16-byte
-// voxel rows (8 channels each): [plane][hz][hy][hx] x 16 B. In that layout the A operand of every neighbour offset
-// is a shifted view of the halo that a matrix descriptor expresses directly -- core matrix (row group g, channel
-// group j) at plane j, rows (o1, g + o2, o3 .. o3 + 7): leading (K) byte offset = one plane, stride (M) byte offset =
-// one halo row of 10 voxels = 160 B -- so no per-offset staging is needed: one thread issues the 27 Cin / 16 MMAs
-// back to back against the resident weights (K-major [Cout][27 Cin]). The MMAs run in the K order of
-// k_conv3_fwd_tc (offsets ascending, 16 channels at a time), so the accumulator and the result are the same.
-constexpr int kHaloRows = 3 * 18 * 10;
-constexpr uint32_t kHaloPlane = kHaloRows * 16;
+// A CTA covers tz (1 or 2) planes of a tile of 8 (i3) x 16 (i2) voxels of one sample (128 rows of the implicit
+// GEMM per plane, each plane its own TMEM accumulator). Its input halo -- the 10 x 18 x (tz + 2) voxels around the
+// tile, periodic -- is loaded once, as Cin/8 planes of 16-byte voxel rows (8 channels each):
+// [plane][hz][hy][hx] x 16 B. In that layout the A operand of every neighbour offset is a shifted view of the halo
+// that a matrix descriptor expresses directly -- core matrix (row group g, channel group j) at plane j, rows
+// (p + o1, g + o2, o3 .. o3 + 7) for tile plane p: leading (K) byte offset = one plane, stride (M) byte offset = one
+// halo row of 10 voxels = 160 B -- so no per-offset staging is needed: one thread issues the 27 Cin / 16 MMAs per
+// tile plane back to back against the resident weights (K-major [Cout][27 Cin]). The MMAs of a voxel run in the K
+// order of k_conv3_fwd_tc (offsets ascending, 16 channels at a time), so its accumulator and result are the same;
+// two planes share one weight load and read (tz + 2) / tz halo rows per voxel row instead of 3.
+constexpr int kHaloRowsPerZ = 18 * 10;
+inline int halo_rows(int tz) { return (tz + 2) * kHaloRowsPerZ; }
 
-inline size_t halo_smem(int Cin, int Cout) {
-  const size_t halo = (size_t(Cin / 8) * kHaloPlane + 1023) / 1024 * 1024;
+inline size_t halo_smem(int Cin, int Cout, int tz) {
+  const size_t halo = (size_t(Cin / 8) * halo_rows(tz) * 16 + 1023) / 1024 * 1024;
   return 1024 + halo + size_t(Cout) * 27 * Cin * 2 + 64;
 }
 inline bool halo_fits(const Geo& g, int Cin, int Cout) {
   return Cin % 16 == 0 && Cin <= 64 && g.n3 % 8 == 0 && g.n2 % 16 == 0 && 27LL * Cout * Cin * 2 <= 110592 &&
-         halo_smem(Cin, Cout) <= 227 * 1024;
+         halo_smem(Cin, Cout, 1) <= 227 * 1024;
+}
+// tile planes per CTA: two where the grid has enough tiles for several waves of two-plane CTAs and the halo stays
+// small, else one
+inline int halo_tz(const Geo& g, int Cin, int Cout) {
+  const long long tiles = (long long)(g.n3 / 8) * (g.n2 / 16) * g.n1 * g.B;
+  return (g.n1 % 2 == 0 && Cin <= 32 && tiles / 2 >= 4 * 152 && halo_smem(Cin, Cout, 2) <= 227 * 1024) ? 2 : 1;
 }
 
 template <int CIN>  // CIN > 0: the input channel count at compile time (constant divisors), else Cin_rt
@@ -686,45 +920,48 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_halo(const bf16* __restric
                                                            const float* __restrict__ bias,
                                                            const bf16* __restrict__ skip, bf16* __restrict__ y,
                                                            float* __restrict__ yf, int accum, Geo g, int Cin_rt,
-                                                           int Cout, int relu) {
+                                                           int Cout, int relu, int tz) {
   const int Cin = CIN > 0 ? CIN : Cin_rt;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* sm = sm_raw + ((1024u - (tc::smem_addr(sm_raw) & 1023u)) & 1023u);
   const int nplanes = Cin / 8;
   const int K = 27 * Cin;
+  const int hrows = (tz + 2) * kHaloRowsPerZ;
+  const uint32_t hplane = (uint32_t)hrows * 16u;  // bytes of one channel-group plane of the halo
   unsigned char* halo = sm;
-  unsigned char* Bs = sm + (size_t(nplanes) * kHaloPlane + 1023) / 1024 * 1024;
+  unsigned char* Bs = sm + (size_t(nplanes) * hplane + 1023) / 1024 * 1024;
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(Bs + size_t(Cout) * K * 2);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = tc::tmem_cols(Cout);
+  const uint32_t ncols = tc::tmem_cols(tz * Cout);
   const uint32_t b0 = tc::smem_addr(bar);
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
   if (tid == 0) tc::mbar_init(b0, 1);
-  // the tile: blockIdx.x = ((b n1 + z) ty + iy) tx + ix
-  const int tx = g.n3 / 8, ty = g.n2 / 16;
+  // the tile: blockIdx.x = ((b (n1 / tz) + zt) ty + iy) tx + ix
+  const int tx = g.n3 / 8, ty = g.n2 / 16, nzt = g.n1 / tz;
   int t = blockIdx.x;
   const int ix = t % tx;
   t /= tx;
   const int iy = t % ty;
   t /= ty;
-  const int z = t % g.n1, b = t / g.n1;
+  const int z = (t % nzt) * tz, b = t / nzt;
   const int x0 = 8 * ix, y0 = 16 * iy;
-  for (int q = tid; q < nplanes * kHaloRows; q += 128) {
-    const int cc = q / kHaloRows, r = q - cc * kHaloRows;
-    const int hz = r / 180, rr = r - hz * 180;
+  // halo rows and weights by cp.async: every copy of the thread in flight at once, none through registers
+  const uint32_t hsm = tc::smem_addr(halo), bsm = tc::smem_addr(Bs);
+  for (int q = tid; q < nplanes * hrows; q += 128) {
+    const int cc = q / hrows, r = q - cc * hrows;
+    const int hz = r / kHaloRowsPerZ, rr = r - hz * kHaloRowsPerZ;
     const int hy = rr / 10, hx = rr - hy * 10;
     const int gz = pw(z + hz - 1, g.n1), gy = pw(y0 + hy - 1, g.n2), gx = pw(x0 + hx - 1, g.n3);
     const long long vox = ((long long)(b * g.n1 + gz) * g.n2 + gy) * g.n3 + gx;
-    *reinterpret_cast<uint4*>(halo + (size_t(cc) * kHaloRows + r) * 16) =
-        *reinterpret_cast<const uint4*>(x + vox * Cin + 8 * cc);
+    tc::cp_async_16(hsm + (uint32_t)(cc * hrows + r) * 16u, x + vox * Cin + 8 * cc);
   }
   const int nv = K / 8;
   for (int q = tid; q < Cout * nv; q += 128) {
     const int co = q / nv, c = q - co * nv;
-    *reinterpret_cast<uint4*>(Bs + tc::kmajor_offset(co, 8 * c, K)) =
-        *reinterpret_cast<const uint4*>(w + (long long)co * K + 8 * c);
+    tc::cp_async_16(bsm + (uint32_t)tc::kmajor_offset(co, 8 * c, K), w + (long long)co * K + 8 * c);
   }
+  tc::cp_async_wait_all();
   tc::fence_smem_to_async();
   tc::fence_before();
   __syncthreads();
@@ -732,15 +969,16 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_halo(const bf16* __restric
   const uint32_t tmem = *slot;
   if (tid == 0) {
     const uint32_t idesc = tc::idesc_bf16(kTileM, Cout);
-    const uint32_t hbase = tc::smem_addr(halo), bbase = tc::smem_addr(Bs);
     const int kpo = Cin / 16;  // MMAs per offset
-    for (int off = 0; off < 27; ++off) {
-      const int o1 = off / 9, o2 = (off / 3) % 3, o3 = off % 3;
-      const uint32_t row0 = (uint32_t)((o1 * 18 + o2) * 10 + o3);
-      for (int kk = 0; kk < kpo; ++kk) {
-        const uint64_t ad = tc::smem_desc(hbase + 2u * kk * kHaloPlane + 16u * row0, kHaloPlane, 160u);
-        const uint64_t bd = tc::smem_desc(bbase + 256u * (off * kpo + kk), 128u, 16u * K);
-        tc::mma_bf16(tmem, ad, bd, idesc, (off > 0 || kk > 0) ? 1u : 0u);
+    for (int p = 0; p < tz; ++p) {
+      for (int off = 0; off < 27; ++off) {
+        const int o1 = off / 9, o2 = (off / 3) % 3, o3 = off % 3;
+        const uint32_t row0 = (uint32_t)(((p + o1) * 18 + o2) * 10 + o3);
+        for (int kk = 0; kk < kpo; ++kk) {
+          const uint64_t ad = tc::smem_desc(hsm + 2u * kk * hplane + 16u * row0, hplane, 160u);
+          const uint64_t bd = tc::smem_desc(bsm + 256u * (off * kpo + kk), 128u, 16u * K);
+          tc::mma_bf16(tmem + (uint32_t)(p * Cout), ad, bd, idesc, (off > 0 || kk > 0) ? 1u : 0u);
+        }
       }
     }
     tc::commit(b0);
@@ -752,21 +990,13 @@ __global__ void __launch_bounds__(128, 1) k_conv3_fwd_halo(const bf16* __restric
     if (tid == 0) atomicExch(&g_nn_error, 1);
     tc::mbar_wait(b0, 0, kWaitCycles);  // whatever is still in flight, bounded
   } else {
-    const int r = 32 * warp + lane;  // this lane's accumulator row: voxel (x0 + r % 8, y0 + r / 8)
-    const long long m = ((long long)(b * g.n1 + z) * g.n2 + y0 + (r >> 3)) * g.n3 + x0 + (r & 7);
-    for (int c0 = 0; c0 < Cout; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int co = c0 + j;
-        const long long o = m * Cout + co;
-        float val = v[j];
-        if (bias) val += bias[co];
-        if (skip) val += __bfloat162float(skip[o]);
-        if (relu) val = fmaxf(val, 0.f);
-        if (y) y[o] = __float2bfloat16_rn(val);
-        if (yf) yf[o] = accum ? yf[o] + val : val;
+    const int r = 32 * warp + lane;  // this lane's accumulator row: voxel (x0 + r % 8, y0 + r / 8) of each plane
+    for (int p = 0; p < tz; ++p) {
+      const long long m = ((long long)(b * g.n1 + z + p) * g.n2 + y0 + (r >> 3)) * g.n3 + x0 + (r & 7);
+      for (int c0 = 0; c0 < Cout; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(p * Cout + c0), v);
+        conv_epilogue16(v, m, c0, Cout, bias, skip, y, yf, accum, relu);
       }
     }
   }
@@ -833,10 +1063,11 @@ cudaError_t conv3_fwd(const bf16* x, const bf16* w, const float* bias, const bf1
           hattr = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     });
     if (hattr != cudaSuccess) return hattr;
-    const unsigned htiles = (unsigned)((g.n3 / 8) * (g.n2 / 16) * g.n1 * g.B);
+    const int tz = halo_tz(g, Cin, Cout);
+    const unsigned htiles = (unsigned)((g.n3 / 8) * (g.n2 / 16) * (g.n1 / tz) * g.B);
     auto go = [&](auto cc) {
-      k_conv3_fwd_halo<decltype(cc)::value><<<htiles, kTileM, halo_smem(Cin, Cout), st>>>(x, w, bias, skip, y, yf,
-                                                                                          accum, g, Cin, Cout, relu);
+      k_conv3_fwd_halo<decltype(cc)::value><<<htiles, kTileM, halo_smem(Cin, Cout, tz), st>>>(
+          x, w, bias, skip, y, yf, accum, g, Cin, Cout, relu, tz);
     };
     switch (Cin) {
       case 16: go(std::integral_constant<int, 16>()); break;
@@ -871,7 +1102,7 @@ size_t wgrad_work_elems(const Geo& g, int Cin, int Cout) {
 }
 
 cudaError_t conv3_wgrad(const bf16* dz, const bf16* x, float* dw, float* work, const Geo& g, int Cin, int Cout,
-                        cudaStream_t st) {
+                        cudaStream_t st, const float* bias_part, float* db) {
   const cudaError_t attr = conv_attrs_once();
   if (attr != cudaSuccess) return attr;
   const int group = wgrad_group(Cin);
@@ -884,9 +1115,10 @@ cudaError_t conv3_wgrad(const bf16* dz, const bf16* x, float* dw, float* work, c
   });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const long long count = 27LL * Cin * Cout;
-  k_sum_chunks<<<sum_blocks(count), 256, 0, st>>>(work, nchunks, count, dw);
-  return cudaGetLastError();
+  const SumJob jw = sum_job(work, nchunks, 27LL * Cin * Cout, dw);
+  if (!bias_part) return sum_chunks(jw, nullptr, st);
+  const SumJob jb = sum_job(bias_part, kBiasBlocks, Cout, db);
+  return sum_chunks(jw, &jb, st);
 }
 
 cudaError_t status(cudaStream_t st) {
@@ -904,6 +1136,14 @@ cudaError_t status(cudaStream_t st) {
   return cudaSuccess;
 }
 
+cudaError_t weight_flip_all(const bf16* w, bf16* wt, const FlipTable& tab, cudaStream_t st) {
+  if (tab.n < 1 || tab.n > FlipTable::kMax) return cudaErrorInvalidValue;
+  for (int t = 0; t < tab.n; ++t)
+    if (tab.cin[t] < 1 || tab.cout[t] < 1 || 27LL * tab.cin[t] * tab.cout[t] >= (1LL << 31))
+      return cudaErrorInvalidValue;
+  k_wt_flip_all<<<nblocks(tab.start[tab.n]), 256, 0, st>>>(w, wt, tab);
+  return cudaGetLastError();
+}
 cudaError_t weight_flip(const bf16* w, bf16* wt, int Cin, int Cout, cudaStream_t st) {
   k_wt_flip<<<nblocks(27LL * Cin * Cout), 256, 0, st>>>(w, wt, Cin, Cout);
   return cudaGetLastError();
@@ -921,9 +1161,8 @@ cudaError_t relu_bwd_bias(const float* dy, const bf16* y, float* dz, bf16* dzb, 
   const int threads = (256 / C) * C;
   k_relu_bwd_bias<<<kBiasBlocks, threads, 0, st>>>(dy, y, dz, dzb, M, C, work);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_sum_chunks<<<sum_blocks(C), 256, 0, st>>>(work, kBiasBlocks, C, db);
-  return cudaGetLastError();
+  if (e != cudaSuccess || !db) return e;
+  return sum_chunks(sum_job(work, kBiasBlocks, C, db), nullptr, st);
 }
 
 cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* work, cudaStream_t st) {
@@ -931,26 +1170,37 @@ cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* wor
   k_chan_sum<<<kBiasBlocks, threads, 0, st>>>(dz, M, C, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sum_chunks<<<sum_blocks(C), 256, 0, st>>>(work, kBiasBlocks, C, db);
-  return cudaGetLastError();
+  return sum_chunks(sum_job(work, kBiasBlocks, C, db), nullptr, st);
 }
 
 cudaError_t pool_fwd(const bf16* x, bf16* y, const Geo& gf, int C, cudaStream_t st) {
   const Geo gc = mkgeo(gf.B, gf.n1 / 2, gf.n2 / 2, gf.n3 / 2);
-  k_pool_fwd<<<nblocks(gc.M * C), 256, 0, st>>>(x, y, gc, C);
+  if (C % 8 == 0)
+    k_pool_fwd<8><<<nblocks(gc.M * C / 8), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)(C / 8)));
+  else
+    k_pool_fwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)C));
   return cudaGetLastError();
 }
 cudaError_t pool_bwd(const float* dy, float* dx, int accum, const Geo& gf, int C, cudaStream_t st) {
   const Geo gc = mkgeo(gf.B, gf.n1 / 2, gf.n2 / 2, gf.n3 / 2);
-  k_pool_bwd<<<nblocks(gf.M * C), 256, 0, st>>>(dy, dx, accum, gc, C);
+  if (C % 4 == 0)
+    k_pool_bwd<4><<<nblocks(gc.M * C / 4), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)(C / 4)));
+  else
+    k_pool_bwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)C));
   return cudaGetLastError();
 }
 cudaError_t up_fwd(const bf16* x, bf16* y, const Geo& gc, int C, cudaStream_t st) {
-  k_up_fwd<<<nblocks(gc.M * 8 * C), 256, 0, st>>>(x, y, gc, C);
+  if (C % 8 == 0)
+    k_up_fwd<8><<<nblocks(gc.M * C / 8), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)(C / 8)));
+  else
+    k_up_fwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)C));
   return cudaGetLastError();
 }
 cudaError_t up_bwd(const float* dy, float* dx, int accum, const Geo& gc, int C, cudaStream_t st) {
-  k_up_bwd<<<nblocks(gc.M * C), 256, 0, st>>>(dy, dx, accum, gc, C);
+  if (C % 4 == 0)
+    k_up_bwd<4><<<nblocks(gc.M * C / 4), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)(C / 4)));
+  else
+    k_up_bwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)C));
   return cudaGetLastError();
 }
 
@@ -968,16 +1218,20 @@ cudaError_t adam(float* p, const float* g, float* m1, float* m2, bf16* pb, long 
   return cudaGetLastError();
 }
 
-cudaError_t pack_images(const float* src, bf16* dst, long long M, int C, float sdiff, cudaStream_t st) {
-  k_pack_images<<<nblocks(M * C), 256, 0, st>>>(src, dst, M, C, sdiff);
+cudaError_t pack_images(const float* images, const SampleIdx& idx, int nb, bf16* dst, long long N0, int C,
+                        float sdiff, cudaStream_t st) {
+  if (nb < 1 || nb > SampleIdx::kMax) return cudaErrorInvalidValue;
+  k_pack_images<<<nblocks(nb * N0), 256, 0, st>>>(images, idx, nb, dst, N0, C, sdiff);
+  return cudaGetLastError();
+}
+cudaError_t interleave_batch(const float* targets, const SampleIdx& idx, int nb, float* dst, long long N0, int ncomp,
+                             float s, cudaStream_t st) {
+  if (nb < 1 || nb > SampleIdx::kMax) return cudaErrorInvalidValue;
+  k_interleave_batch<<<nblocks(nb * N0), 256, 0, st>>>(targets, idx, nb, dst, N0, ncomp, s);
   return cudaGetLastError();
 }
 cudaError_t unpack(const float* src, float* dst, long long M, int ncomp, int C, float s, cudaStream_t st) {
   k_unpack<<<nblocks(M * ncomp), 256, 0, st>>>(src, dst, M, ncomp, C, s);
-  return cudaGetLastError();
-}
-cudaError_t interleave(const float* src, float* dst, long long M, int ncomp, float s, cudaStream_t st) {
-  k_interleave<<<nblocks(M * ncomp), 256, 0, st>>>(src, dst, M, ncomp, s);
   return cudaGetLastError();
 }
 cudaError_t add(const float* a, float* b, long long count, cudaStream_t st) {
@@ -1004,6 +1258,10 @@ inline claire_status st_of(cudaError_t e) {
 inline bool geo_args(int B, int n1, int n2, int n3) { return B > 0 && n1 > 0 && n2 > 0 && n3 > 0; }
 inline bool pool_args(int B, int n1, int n2, int n3) {
   return geo_args(B, n1, n2, n3) && n1 % 2 == 0 && n2 % 2 == 0 && n3 % 2 == 0;
+}
+// pooling and upsampling index fine voxels and channels in 32 bits: the fine grid's values below 2^31
+inline bool fine_fits(int B, int n1, int n2, int n3, int C, int scale) {
+  return C > 0 && (long long)B * n1 * n2 * n3 * scale * C < (1LL << 31);
 }
 }  // namespace
 
@@ -1064,23 +1322,23 @@ claire_status claire_nn_bias_grad(const float* dz, long long M, int C, float* db
 }
 
 claire_status claire_nn_pool_fwd(const void* x, void* y, int B, int n1, int n2, int n3, int C, void* stream) {
-  if (!x || !y || !pool_args(B, n1, n2, n3) || C <= 0) return CLAIRE_EINVAL;
+  if (!x || !y || !pool_args(B, n1, n2, n3) || !fine_fits(B, n1, n2, n3, C, 1)) return CLAIRE_EINVAL;
   return st_of(pool_fwd(static_cast<const bf16*>(x), static_cast<bf16*>(y), mkgeo(B, n1, n2, n3), C,
                         (cudaStream_t)stream));
 }
 claire_status claire_nn_pool_bwd(const float* dy, float* dx, int accum, int B, int n1, int n2, int n3, int C,
                                  void* stream) {
-  if (!dy || !dx || !pool_args(B, n1, n2, n3) || C <= 0) return CLAIRE_EINVAL;
+  if (!dy || !dx || !pool_args(B, n1, n2, n3) || !fine_fits(B, n1, n2, n3, C, 1)) return CLAIRE_EINVAL;
   return st_of(pool_bwd(dy, dx, accum ? 1 : 0, mkgeo(B, n1, n2, n3), C, (cudaStream_t)stream));
 }
 claire_status claire_nn_up_fwd(const void* x, void* y, int B, int n1, int n2, int n3, int C, void* stream) {
-  if (!x || !y || !geo_args(B, n1, n2, n3) || C <= 0) return CLAIRE_EINVAL;
+  if (!x || !y || !geo_args(B, n1, n2, n3) || !fine_fits(B, n1, n2, n3, C, 8)) return CLAIRE_EINVAL;
   return st_of(
       up_fwd(static_cast<const bf16*>(x), static_cast<bf16*>(y), mkgeo(B, n1, n2, n3), C, (cudaStream_t)stream));
 }
 claire_status claire_nn_up_bwd(const float* dy, float* dx, int accum, int B, int n1, int n2, int n3, int C,
                                void* stream) {
-  if (!dy || !dx || !geo_args(B, n1, n2, n3) || C <= 0) return CLAIRE_EINVAL;
+  if (!dy || !dx || !geo_args(B, n1, n2, n3) || !fine_fits(B, n1, n2, n3, C, 8)) return CLAIRE_EINVAL;
   return st_of(up_bwd(dy, dx, accum ? 1 : 0, mkgeo(B, n1, n2, n3), C, (cudaStream_t)stream));
 }
 

@@ -37,6 +37,21 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
 // make this thread's generic-proxy shared-memory writes visible to the tensor core (async proxy)
 __device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// 16-byte global -> shared copy that does not hold a register or wait (L2 only: each CTA reads its rows once);
+// cp_async_wait_all waits for all of this thread's copies. Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async_16(uint32_t sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(gsrc) : "memory");
+}
+// as cp_async_16, but with src_bytes = 0 the 16 shared-memory bytes are zero-filled and nothing is read
+__device__ __forceinline__ void cp_async_16_zfill(uint32_t sdst, const void* gsrc, bool valid) {
+  const uint32_t n = valid ? 16u : 0u;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sdst), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

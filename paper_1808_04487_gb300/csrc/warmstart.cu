@@ -111,6 +111,7 @@ struct claire_ws {
   float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr;
   bf16 *Pb = nullptr, *Wt = nullptr;
   float *pred = nullptr, *dpred = nullptr, *tgt = nullptr, *dz = nullptr, *work = nullptr;
+  float* bwork = nullptr;  // per-block bias-gradient partials of the layer being differentiated
   bf16* dzb = nullptr;
   double* part = nullptr;
   double* hpart = nullptr;
@@ -222,9 +223,11 @@ claire_status ws_destroy(claire_ws* w) {
 // forward pass for samples img[b] = images + idx[b] * 2 N0 (idx == nullptr: b); prediction left in w->pred
 claire_status forward(claire_ws* w, const float* images, const int* idx, int nb, cudaStream_t st) {
   const long long N0 = w->N(0);
-  for (int b = 0; b < nb; ++b) {
-    const long long s = idx ? idx[b] : b;
-    WS_CUDA(w, nn::pack_images(images + s * 2 * N0, w->T[0].y + b * N0 * 16, N0, 16, kDiffScale, st));
+  for (int b0 = 0; b0 < nb; b0 += nn::SampleIdx::kMax) {
+    const int nc = std::min(nb - b0, nn::SampleIdx::kMax);
+    nn::SampleIdx si;
+    for (int b = 0; b < nc; ++b) si.v[b] = idx ? idx[b0 + b] : b0 + b;
+    WS_CUDA(w, nn::pack_images(images, si, nc, w->T[0].y + b0 * N0 * 16, N0, 16, kDiffScale, st));
   }
   for (const Op& op : w->ops) {
     if (op.kind == 0) {
@@ -257,13 +260,28 @@ claire_status loss_grad(claire_ws* w, const float* images, const float* targets,
                         bool backward, double* loss, cudaStream_t st) {
   CL_TRY(forward(w, images, idx, nb, st));
   const long long N0 = w->N(0);
-  for (int b = 0; b < nb; ++b) {
-    const long long s = idx ? idx[b] : b;
-    WS_CUDA(w, nn::interleave(targets + s * 3 * N0, w->tgt + b * N0 * 3, N0, 3, w->vscale, st));
+  for (int b0 = 0; b0 < nb; b0 += nn::SampleIdx::kMax) {
+    const int nc = std::min(nb - b0, nn::SampleIdx::kMax);
+    nn::SampleIdx si;
+    for (int b = 0; b < nc; ++b) si.v[b] = idx ? idx[b0 + b] : b0 + b;
+    WS_CUDA(w, nn::interleave_batch(targets, si, nc, w->tgt + b0 * N0 * 3, N0, 3, w->vscale, st));
   }
   const long long M0 = N0 * nb;
   WS_CUDA(w, nn::mse(w->pred, w->tgt, backward ? w->dpred : nullptr, M0, 16, 3, w->part, claire_ws::kParts, st));
   if (backward) {
+    // the adjoint-convolution weights of every layer that passes a gradient to its input, in one launch
+    nn::FlipTable ft;
+    ft.n = 0;
+    ft.start[0] = 0;
+    for (const Layer& l : w->layers) {
+      if (l.in == 0) continue;
+      ft.cin[ft.n] = l.cin;
+      ft.cout[ft.n] = l.cout;
+      ft.woff[ft.n] = l.woff;
+      ft.start[ft.n + 1] = ft.start[ft.n] + 27LL * l.cin * l.cout;
+      ++ft.n;
+    }
+    WS_CUDA(w, nn::weight_flip_all(w->Pb, w->Wt, ft, st));
     std::vector<char> written(w->T.size(), 0);
     for (int k = (int)w->ops.size() - 1; k >= 0; --k) {
       const Op& op = w->ops[k];
@@ -272,11 +290,12 @@ claire_status loss_grad(claire_ws* w, const float* images, const float* targets,
         const nn::Geo g = w->geo(l.level, nb);
         const float* dy = l.out >= 0 ? w->T[l.out].g : w->dpred;
         const bf16* y = (l.out >= 0 && l.relu) ? w->T[l.out].y : nullptr;
-        WS_CUDA(w, nn::relu_bwd_bias(dy, y, l.skip >= 0 ? w->dz : nullptr, w->dzb, g.M, l.cout, w->G + l.boff,
-                                     w->work, st));
-        WS_CUDA(w, nn::conv3_wgrad(w->dzb, w->T[l.in].y, w->G + l.woff, w->work, g, l.cin, l.cout, st));
+        // the bias gradient's partials, summed in the weight gradient's reduction launch
+        WS_CUDA(w, nn::relu_bwd_bias(dy, y, l.skip >= 0 ? w->dz : nullptr, w->dzb, g.M, l.cout, nullptr, w->bwork,
+                                     st));
+        WS_CUDA(w, nn::conv3_wgrad(w->dzb, w->T[l.in].y, w->G + l.woff, w->work, g, l.cin, l.cout, st, w->bwork,
+                                   w->G + l.boff));
         if (l.in != 0) {
-          WS_CUDA(w, nn::weight_flip(w->Pb + l.woff, w->Wt + l.woff, l.cin, l.cout, st));
           WS_CUDA(w, nn::conv3_fwd(w->dzb, w->Wt + l.woff, nullptr, nullptr, nullptr, w->T[l.in].g,
                                    written[l.in], g, l.cout, l.cin, 0, w->work, st));
           written[l.in] = 1;
@@ -337,7 +356,6 @@ claire_status claire_ws_create(int batch, int n1, int n2, int n3, float vscale, 
   for (const Layer& l : w->layers) {
     const nn::Geo g = w->geo(l.level, batch);
     work = std::max(work, nn::wgrad_work_elems(g, l.cin, l.cout));
-    work = std::max(work, nn::bias_work_elems(l.cout));
     work = std::max(work, nn::fwd_work_elems(g, l.cout));  // forward split-K partials
     work = std::max(work, nn::fwd_work_elems(g, l.cin));   // input-gradient (adjoint convolution) partials
     dmax = std::max(dmax, size_t(g.M) * l.cout);
@@ -349,8 +367,8 @@ claire_status claire_ws_create(int batch, int n1, int n2, int n3, float vscale, 
   const size_t M0 = size_t(w->N(0)) * batch;
   ok = ok && w->alloc(w->pred, M0 * 16) && w->alloc(w->dpred, M0 * 16) && w->alloc(w->tgt, M0 * 3) &&
        w->alloc(w->dz, dmax) && w->alloc(w->dzb, dmax) && w->alloc(w->work, work) &&
-       w->alloc(w->part, claire_ws::kParts) && w->alloc(w->img, 2 * size_t(w->N(0))) &&
-       w->alloc(w->vnet, 3 * size_t(w->N(0)));
+       w->alloc(w->bwork, nn::bias_work_elems(128)) && w->alloc(w->part, claire_ws::kParts) &&
+       w->alloc(w->img, 2 * size_t(w->N(0))) && w->alloc(w->vnet, 3 * size_t(w->N(0)));
   ok = ok && cudaMallocHost(&w->hpart, sizeof(double) * claire_ws::kParts) == cudaSuccess;
   if (!ok) {
     ws_destroy(w);

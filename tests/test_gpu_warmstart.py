@@ -51,9 +51,11 @@ CONV_CASES = [((2, 6, 5, 8), 16, 16), ((1, 3, 4, 4), 32, 48), ((2, 6, 5, 8), 64,
 # weights within 108 KB)
 HALO_CASES = [((2, 4, 16, 8), 16, 16), ((1, 3, 16, 16), 32, 64), ((2, 2, 32, 8), 64, 32), ((1, 4, 16, 8), 16, 128),
               ((1, 2, 16, 24), 48, 16)]
+# grids with enough tiles (at least 4 x 152 two-plane CTAs, n1 even, Cin <= 32) for two tile planes per CTA
+HALO_TZ2_CASES = [((4, 38, 16, 64), 16, 16), ((2, 38, 16, 128), 32, 16)]
 
 
-@pytest.mark.parametrize("shape,cin,cout", CONV_CASES + HALO_CASES)
+@pytest.mark.parametrize("shape,cin,cout", CONV_CASES + HALO_CASES + HALO_TZ2_CASES)
 def test_conv3_forward(ws_mod, shape, cin, cout):
     r = np.random.default_rng(cin * 1000 + cout)
     xg, x = bf16(r.standard_normal(shape + (cin,)))
@@ -76,7 +78,7 @@ def test_conv3_forward(ws_mod, shape, cin, cout):
     assert np.all(np.abs(host(acc) - ref2) <= 4e-5 * (mag + np.abs(host(base))))
 
 
-@pytest.mark.parametrize("shape,cin,cout", HALO_CASES)
+@pytest.mark.parametrize("shape,cin,cout", HALO_CASES + HALO_TZ2_CASES)
 def test_conv3_forward_from_halo_is_bit_identical_to_the_gather_kernel(ws_mod, shape, cin, cout, monkeypatch):
     """The forward convolution from a shared-memory halo (A operands as descriptors into the halo) against the
     kernel that gathers each offset's neighbour rows (CLAIRE_CONV=gather, all 27 offsets in one CTA per tile): the
@@ -159,6 +161,22 @@ def test_relu_bias_pool_up(ws_mod):
     assert np.allclose(host(acc), dy + W.pool_adjoint(c), rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("C", [128, 12, 3])
+def test_pool_up_channel_widths(ws_mod, C):
+    # 16-byte channel vectors (C % 8 == 0 BF16, C % 4 == 0 FP32) and single channels
+    r = np.random.default_rng(40 + C)
+    yg, y = bf16(r.standard_normal((2, 4, 6, 8, C)))
+    assert np.all(np.abs(host(ws_mod.pool_fwd(yg)) - W.pool(y)) <= 2.0 ** -8 * np.abs(W.pool(y)) + 1e-7)
+    assert np.array_equal(host(ws_mod.up_fwd(yg)), W.up(y))
+    cg, c = f32(r.standard_normal((2, 2, 3, 4, C)))
+    dyg, dy = f32(r.standard_normal((2, 4, 6, 8, C)))
+    assert np.allclose(host(ws_mod.pool_bwd(cg)), W.pool_adjoint(c), rtol=1e-6, atol=1e-7)
+    assert np.allclose(host(ws_mod.up_bwd(dyg)), W.up_adjoint(dy), rtol=1e-5, atol=1e-6)
+    acc = cg.clone()
+    ws_mod.up_bwd(dyg, dx=acc, accum=True)
+    assert np.allclose(host(acc), c + W.up_adjoint(dy), rtol=1e-5, atol=1e-6)
+
+
 def test_mse_and_adam(ws_mod):
     r = np.random.default_rng(13)
     pg, p = f32(r.standard_normal((4096, 16)))
@@ -236,6 +254,13 @@ def test_network_loss_and_gradient(small_net):
     # selecting rows by index is the same as passing them
     v1 = small_net.forward(img_g, idx=[1]).cpu().numpy()
     assert np.array_equal(v1[0], v[1])
+    # the minibatch gathered by index (images and targets) gives the loss and gradients of the same rows passed
+    # in that order, bit for bit
+    loss_i = small_net.loss(img_g, tgt_g, idx=[1, 0], backward=True)
+    grads_i = small_net.get_grads()
+    loss_p = small_net.loss(img_g[[1, 0]].contiguous(), tgt_g[[1, 0]].contiguous(), backward=True)
+    assert loss_i == loss_p
+    assert np.array_equal(grads_i, small_net.get_grads())
 
 
 def test_training_step_decreases_loss(small_net):
