@@ -425,9 +425,9 @@ __global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restric
 }
 
 // Fixed-order sums over chunks: dst[i] = sum_c part[c][i]. A 256-thread CTA takes opb consecutive outputs i
-// (opb = 32, or 8 for short outputs such as per-channel bias partials); thread t sums range r = t / opb, one
-// contiguous (256 / opb)-th of the chunks, in chunk order with eight loads in flight, and the range sums are added in
-// range order. Two independent jobs share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias
+// (opb = 32; 8 or 4 for short outputs such as per-channel bias partials, so that more threads share the chunks);
+// thread t sums range r = t / opb, one contiguous (256 / opb)-th of the chunks, in chunk order with eight loads in
+// flight, and the range sums are added in range order. Two independent jobs share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias
 // gradient of a layer is summed in the launch that sums its weight gradient. (One thread per i summing all chunks
 // in order left a few dozen CTAs on the GPU, each thread a chain of ~190 strided loads.)
 struct SumJob {
@@ -442,7 +442,7 @@ inline SumJob sum_job(const float* part, int nchunks, long long count, float* ds
   j.dst = dst;
   j.count = count;
   j.nchunks = nchunks;
-  j.opb = count < 32 * 152 ? 8 : 32;
+  j.opb = count < 1024 ? 4 : (count < 32 * 152 ? 8 : 32);
   const long long b = (count + j.opb - 1) / j.opb;
   j.blocks = (int)(b < 4864 ? (b > 0 ? b : 1) : 4864);
   return j;
@@ -459,15 +459,14 @@ __global__ void __launch_bounds__(256) k_sum_chunks(SumJob a, SumJob b) {
     const long long i = base + oi;
     float s = 0.f;
     if (i < j.count) {
-      int c = c0;
-      for (; c + 8 <= c1; c += 8) {
+      for (int c = c0; c < c1; c += 8) {  // the last batch's loads past c1 are skipped
         float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = j.part[(long long)(c + u) * j.count + i];
+        for (int u = 0; u < 8; ++u) v[u] = c + u < c1 ? j.part[(long long)(c + u) * j.count + i] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s += v[u];
+        for (int u = 0; u < 8; ++u)
+          if (c + u < c1) s += v[u];
       }
-      for (; c < c1; ++c) s += j.part[(long long)c * j.count + i];
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -498,19 +497,23 @@ __global__ void k_wt_flip(const bf16* __restrict__ w, bf16* __restrict__ wt, int
   }
 }
 
-// k_wt_flip for a table of layers in one launch: element i of the concatenated weights belongs to the layer t with
-// start[t] <= i < start[t + 1]
-__global__ void k_wt_flip_all(const bf16* __restrict__ w, bf16* __restrict__ wt, FlipTable tab) {
-  const long long total = tab.start[tab.n];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    int t = 0;
-    while (t + 1 < tab.n && i >= tab.start[t + 1]) ++t;
-    const int j = (int)(i - tab.start[t]);  // below 27 x 128 x 128 (32-bit index arithmetic)
-    const int Cin = tab.cin[t], Cout = tab.cout[t];
-    const int q = j / Cin, ci = j - q * Cin;
-    const int co = q / 27, off = q - co * 27;
-    wt[tab.woff[t] + (ci * 27 + (26 - off)) * Cout + co] = w[tab.woff[t] + j];
+// k_wt_flip for a table of layers in one launch: CTA (layer t, offset off) transposes the Cout x Cin slice
+// w[co][off][ci] into wt[ci][26 - off][co] through shared memory (coalesced reads along ci, writes along co)
+__global__ void __launch_bounds__(256) k_wt_flip_all(const bf16* __restrict__ w, bf16* __restrict__ wt,
+                                                     FlipTable tab) {
+  __shared__ bf16 tile[kMaxC][kMaxC + 2];
+  const int t = blockIdx.x / 27, off = blockIdx.x - 27 * (blockIdx.x / 27);
+  const int Cin = tab.cin[t], Cout = tab.cout[t];
+  const bf16* src = w + tab.woff[t];
+  bf16* dst = wt + tab.woff[t];
+  for (int q = threadIdx.x; q < Cout * Cin; q += 256) {
+    const int co = q / Cin, ci = q - co * Cin;
+    tile[co][ci] = src[(co * 27 + off) * Cin + ci];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < Cout * Cin; q += 256) {
+    const int ci = q / Cout, co = q - ci * Cout;
+    dst[(ci * 27 + 26 - off) * Cout + co] = tile[co][ci];
   }
 }
 
@@ -1139,9 +1142,8 @@ cudaError_t status(cudaStream_t st) {
 cudaError_t weight_flip_all(const bf16* w, bf16* wt, const FlipTable& tab, cudaStream_t st) {
   if (tab.n < 1 || tab.n > FlipTable::kMax) return cudaErrorInvalidValue;
   for (int t = 0; t < tab.n; ++t)
-    if (tab.cin[t] < 1 || tab.cout[t] < 1 || 27LL * tab.cin[t] * tab.cout[t] >= (1LL << 31))
-      return cudaErrorInvalidValue;
-  k_wt_flip_all<<<nblocks(tab.start[tab.n]), 256, 0, st>>>(w, wt, tab);
+    if (tab.cin[t] < 1 || tab.cout[t] < 1 || tab.cin[t] > kMaxC || tab.cout[t] > kMaxC) return cudaErrorInvalidValue;
+  k_wt_flip_all<<<27 * tab.n, 256, 0, st>>>(w, wt, tab);
   return cudaGetLastError();
 }
 cudaError_t weight_flip(const bf16* w, bf16* wt, int Cin, int Cout, cudaStream_t st) {

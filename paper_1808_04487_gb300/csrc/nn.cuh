@@ -44,13 +44,13 @@ cudaError_t conv3_wgrad(const bf16* dz, const bf16* x, float* dw, float* work, c
                         cudaStream_t st, const float* bias_part = nullptr, float* db = nullptr);
 // wt[Cin][27][Cout] with wt[ci][26 - off][co] = w[co][off][ci]: the weights of the adjoint convolution
 cudaError_t weight_flip(const bf16* w, bf16* wt, int Cin, int Cout, cudaStream_t st);
-// weight_flip for every layer of a table in one launch: layer t's weights lie at w + woff[t] (27 cin cout values)
-// and go to wt + woff[t]; start[t] = sum of the sizes of layers 0 .. t-1
+// weight_flip for every layer of a table in one launch: layer t's weights lie at w + woff[t] (27 cin cout values,
+// cin and cout at most 128) and go to wt + woff[t]
 struct FlipTable {
   static constexpr int kMax = 32;
   int n;
   int cin[kMax], cout[kMax];
-  long long woff[kMax], start[kMax + 1];
+  long long woff[kMax];
 };
 cudaError_t weight_flip_all(const bf16* w, bf16* wt, const FlipTable& tab, cudaStream_t st);
 // dz = dy (y > 0) (y == nullptr: dz = dy), FP32 and BF16 copies

@@ -272,13 +272,11 @@ claire_status loss_grad(claire_ws* w, const float* images, const float* targets,
     // the adjoint-convolution weights of every layer that passes a gradient to its input, in one launch
     nn::FlipTable ft;
     ft.n = 0;
-    ft.start[0] = 0;
     for (const Layer& l : w->layers) {
       if (l.in == 0) continue;
       ft.cin[ft.n] = l.cin;
       ft.cout[ft.n] = l.cout;
       ft.woff[ft.n] = l.woff;
-      ft.start[ft.n + 1] = ft.start[ft.n] + 27LL * l.cin * l.cout;
       ++ft.n;
     }
     WS_CUDA(w, nn::weight_flip_all(w->Pb, w->Wt, ft, st));
