@@ -527,61 +527,99 @@ __global__ void k_relu_bwd(const float* __restrict__ dy, const bf16* __restrict_
   }
 }
 
-// per-block channel sums: blockDim = (256 / C) C threads, thread t owns channel t % C and rows t / C + k rpb
 constexpr int kBiasBlocks = 1216;  // 8 per SM: enough rows in flight for the fused ReLU backward
-__global__ void k_chan_sum(const float* __restrict__ dz, long long M, int C, float* __restrict__ part) {
-  __shared__ float sh[256];
-  const int c = threadIdx.x % C, r = threadIdx.x / C, rpb = blockDim.x / C;
-  float s = 0.f;
-  for (long long m = (long long)blockIdx.x * rpb + r; m < M; m += (long long)gridDim.x * rpb) s += dz[m * C + c];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x < C) {
-    float t = 0.f;
-    for (int k = 0; k < rpb; ++k) t += sh[k * C + threadIdx.x];
-    part[(long long)blockIdx.x * C + threadIdx.x] = t;
+
+// Per-block channel sums of v = dy (y > 0) (y null: v = dy), fused with dzb = bf16(v) and dz = v (each written only
+// when given): thread t owns the V channels V g .. V g + V - 1, g = t % G (G = C / V; V = 4, one 16-byte load of
+// dy, where C allows) and the rows t / G + k rpb (rpb = blockDim / G), four rows' loads in flight, summed in row
+// order; the rpb row sums of a channel are then added in order. The bias gradient (bias_grad, relu_bwd_bias) is the
+// fixed-order sum of these partials over the blocks; the FP32 dz is written only for a layer whose gradient also
+// feeds a skip connection (the weight and input gradients read dzb).
+template <int V> __device__ __forceinline__ void relu_row(const float* __restrict__ dy, const bf16* __restrict__ y,
+                                                          long long i, float* v) {
+  if constexpr (V == 4) {
+    const float4 d = *reinterpret_cast<const float4*>(dy + i);
+    v[0] = d.x;
+    v[1] = d.y;
+    v[2] = d.z;
+    v[3] = d.w;
+    if (y) {
+      const uint2 u = *reinterpret_cast<const uint2*>(y + i);
+      const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+      const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+      v[0] = a.x > 0.f ? v[0] : 0.f;
+      v[1] = a.y > 0.f ? v[1] : 0.f;
+      v[2] = b.x > 0.f ? v[2] : 0.f;
+      v[3] = b.y > 0.f ? v[3] : 0.f;
+    }
+  } else {
+    v[0] = (y == nullptr || __bfloat162float(y[i]) > 0.f) ? dy[i] : 0.f;
   }
 }
-
-// dzb = bf16(dy (y > 0)) (and dz = dy (y > 0) in FP32 when dz is given) fused with k_chan_sum's per-block channel
-// sums of dy (y > 0): the same rows per thread in the same order, so the same bias gradient, without re-reading dz;
-// the FP32 dz is written only for a layer whose gradient also feeds a skip connection (the weight and input
-// gradients read dzb)
-__global__ void k_relu_bwd_bias(const float* __restrict__ dy, const bf16* __restrict__ y, float* __restrict__ dz,
-                                bf16* __restrict__ dzb, long long M, int C, float* __restrict__ part) {
-  __shared__ float sh[256];
-  const int c = threadIdx.x % C, r = threadIdx.x / C, rpb = blockDim.x / C;
-  const long long step = (long long)gridDim.x * rpb;
-  float s = 0.f;
-  long long m = (long long)blockIdx.x * rpb + r;
-  // four rows' loads in flight, summed in row order
-  for (; m + 3 * step < M; m += 4 * step) {
-    float v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const long long i = (m + u * step) * C + c;
-      v[u] = (y == nullptr || __bfloat162float(y[i]) > 0.f) ? dy[i] : 0.f;
+template <int V> __device__ __forceinline__ void relu_store(float* __restrict__ dz, bf16* __restrict__ dzb, long long i,
+                                                            const float* v) {
+  if constexpr (V == 4) {
+    if (dz) *reinterpret_cast<float4*>(dz + i) = make_float4(v[0], v[1], v[2], v[3]);
+    if (dzb) {
+      uint2 u;
+      *reinterpret_cast<__nv_bfloat162*>(&u.x) = __floats2bfloat162_rn(v[0], v[1]);
+      *reinterpret_cast<__nv_bfloat162*>(&u.y) = __floats2bfloat162_rn(v[2], v[3]);
+      *reinterpret_cast<uint2*>(dzb + i) = u;
     }
+  } else {
+    if (dz) dz[i] = v[0];
+    if (dzb) dzb[i] = __float2bfloat16_rn(v[0]);
+  }
+}
+template <int V>
+__global__ void __launch_bounds__(256) k_relu_bwd_bias(const float* __restrict__ dy, const bf16* __restrict__ y,
+                                                       float* __restrict__ dz, bf16* __restrict__ dzb, long long M,
+                                                       int C, float* __restrict__ part) {
+  __shared__ float sh[256 * V];
+  const int G = C / V;
+  const int g = threadIdx.x % G, r = threadIdx.x / G, rpb = blockDim.x / G;
+  const int c0 = V * g;
+  const long long step = (long long)gridDim.x * rpb;
+  float s[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) s[j] = 0.f;
+  long long m = (long long)blockIdx.x * rpb + r;
+  for (; m + 3 * step < M; m += 4 * step) {
+    float v[4][V];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) relu_row<V>(dy, y, (m + u * step) * C + c0, v[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (dz) dz[(m + u * step) * C + c] = v[u];
-      dzb[(m + u * step) * C + c] = __float2bfloat16_rn(v[u]);
-      s += v[u];
+      relu_store<V>(dz, dzb, (m + u * step) * C + c0, v[u]);
+#pragma unroll
+      for (int j = 0; j < V; ++j) s[j] += v[u][j];
     }
   }
   for (; m < M; m += step) {
-    const long long i = m * C + c;
-    const float v = (y == nullptr || __bfloat162float(y[i]) > 0.f) ? dy[i] : 0.f;
-    if (dz) dz[i] = v;
-    dzb[i] = __float2bfloat16_rn(v);
-    s += v;
+    float v[V];
+    relu_row<V>(dy, y, m * C + c0, v);
+    relu_store<V>(dz, dzb, m * C + c0, v);
+#pragma unroll
+    for (int j = 0; j < V; ++j) s[j] += v[j];
   }
-  sh[threadIdx.x] = s;
+#pragma unroll
+  for (int j = 0; j < V; ++j) sh[threadIdx.x * V + j] = s[j];
   __syncthreads();
-  if (threadIdx.x < C) {
+  if ((int)threadIdx.x < C) {
+    const int gx = threadIdx.x / V, j = threadIdx.x - gx * V;
     float t = 0.f;
-    for (int k = 0; k < rpb; ++k) t += sh[k * C + threadIdx.x];
+    for (int k = 0; k < rpb; ++k) t += sh[(k * G + gx) * V + j];
     part[(long long)blockIdx.x * C + threadIdx.x] = t;
+  }
+}
+// per-block channel sums of (dy, y, dz, dzb) as above, 16-byte rows where C allows
+inline void launch_relu_bwd_bias(const float* dy, const bf16* y, float* dz, bf16* dzb, long long M, int C,
+                                 float* part, cudaStream_t st) {
+  if (C % 4 == 0) {
+    const int G = C / 4;
+    k_relu_bwd_bias<4><<<kBiasBlocks, (256 / G) * G, 0, st>>>(dy, y, dz, dzb, M, C, part);
+  } else {
+    k_relu_bwd_bias<1><<<kBiasBlocks, (256 / C) * C, 0, st>>>(dy, y, dz, dzb, M, C, part);
   }
 }
 
@@ -782,19 +820,49 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ pred, con
   }
 }
 
+__device__ __forceinline__ float adam_one(float& p, float g, float& m1, float& m2, float lr, float b1, float b2,
+                                          float eps, float c1, float c2) {
+  const float a = b1 * m1 + (1.f - b1) * g;
+  const float v = b2 * m2 + (1.f - b2) * g * g;
+  m1 = a;
+  m2 = v;
+  p = p - lr * (a * c1) / (sqrtf(v * c2) + eps);
+  return p;
+}
+// one Adam step per element; four elements per thread with 16-byte accesses where count and the pointers allow
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
                        float* __restrict__ m2, bf16* __restrict__ pb, long long count, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+                       float eps, float c1, float c2, int vec) {
+  if (vec) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+      float4 P = reinterpret_cast<float4*>(p)[i], A = reinterpret_cast<float4*>(m1)[i],
+             B = reinterpret_cast<float4*>(m2)[i];
+      const float4 G = reinterpret_cast<const float4*>(gr)[i];
+      adam_one(P.x, G.x, A.x, B.x, lr, b1, b2, eps, c1, c2);
+      adam_one(P.y, G.y, A.y, B.y, lr, b1, b2, eps, c1, c2);
+      adam_one(P.z, G.z, A.z, B.z, lr, b1, b2, eps, c1, c2);
+      adam_one(P.w, G.w, A.w, B.w, lr, b1, b2, eps, c1, c2);
+      reinterpret_cast<float4*>(p)[i] = P;
+      reinterpret_cast<float4*>(m1)[i] = A;
+      reinterpret_cast<float4*>(m2)[i] = B;
+      if (pb) {
+        uint2 u;
+        *reinterpret_cast<__nv_bfloat162*>(&u.x) = __floats2bfloat162_rn(P.x, P.y);
+        *reinterpret_cast<__nv_bfloat162*>(&u.y) = __floats2bfloat162_rn(P.z, P.w);
+        reinterpret_cast<uint2*>(pb)[i] = u;
+      }
+    }
+    return;
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
-    const float g = gr[i];
-    const float a = b1 * m1[i] + (1.f - b1) * g;
-    const float v = b2 * m2[i] + (1.f - b2) * g * g;
-    m1[i] = a;
-    m2[i] = v;
-    const float np = p[i] - lr * (a * c1) / (sqrtf(v * c2) + eps);
-    p[i] = np;
-    if (pb) pb[i] = __float2bfloat16_rn(np);
+    float P = p[i], A = m1[i], B = m2[i];
+    adam_one(P, gr[i], A, B, lr, b1, b2, eps, c1, c2);
+    p[i] = P;
+    m1[i] = A;
+    m2[i] = B;
+    if (pb) pb[i] = __float2bfloat16_rn(P);
   }
 }
 
@@ -1160,16 +1228,14 @@ size_t bias_work_elems(int C) { return size_t(kBiasBlocks) * size_t(C); }
 
 cudaError_t relu_bwd_bias(const float* dy, const bf16* y, float* dz, bf16* dzb, long long M, int C, float* db,
                           float* work, cudaStream_t st) {
-  const int threads = (256 / C) * C;
-  k_relu_bwd_bias<<<kBiasBlocks, threads, 0, st>>>(dy, y, dz, dzb, M, C, work);
+  launch_relu_bwd_bias(dy, y, dz, dzb, M, C, work, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !db) return e;
   return sum_chunks(sum_job(work, kBiasBlocks, C, db), nullptr, st);
 }
 
 cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* work, cudaStream_t st) {
-  const int threads = (256 / C) * C;
-  k_chan_sum<<<kBiasBlocks, threads, 0, st>>>(dz, M, C, work);
+  launch_relu_bwd_bias(dz, nullptr, nullptr, nullptr, M, C, work, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return sum_chunks(sum_job(work, kBiasBlocks, C, db), nullptr, st);
@@ -1216,7 +1282,10 @@ cudaError_t adam(float* p, const float* g, float* m1, float* m2, bf16* pb, long 
                  float b2, float eps, int t, cudaStream_t st) {
   const float c1 = float(1.0 / (1.0 - std::pow(double(b1), t)));
   const float c2 = float(1.0 / (1.0 - std::pow(double(b2), t)));
-  k_adam<<<nblocks(count), 256, 0, st>>>(p, g, m1, m2, pb, count, lr, b1, b2, eps, c1, c2);
+  const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                       reinterpret_cast<uintptr_t>(m1) | reinterpret_cast<uintptr_t>(m2);
+  const int vec = count % 4 == 0 && (al & 15) == 0 && (reinterpret_cast<uintptr_t>(pb) & 7) == 0;
+  k_adam<<<nblocks(vec ? count / 4 : count), 256, 0, st>>>(p, g, m1, m2, pb, count, lr, b1, b2, eps, c1, c2, vec);
   return cudaGetLastError();
 }
 
