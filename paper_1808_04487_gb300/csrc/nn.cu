@@ -424,10 +424,10 @@ __global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restric
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
-// Fixed-order sums over chunks: dst[i] = sum_c part[c][i]. A 256-thread CTA takes opb consecutive outputs i
-// (opb = 32; 8 or 4 for short outputs such as per-channel bias partials, so that more threads share the chunks);
-// thread t sums range r = t / opb, one contiguous (256 / opb)-th of the chunks, in chunk order with eight loads in
-// flight, and the range sums are added in range order. Two independent jobs share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias
+// Fixed-order sums over chunks: dst[i] = sum_c part[c][i]. A 256-thread CTA takes opb consecutive outputs i;
+// thread t sums range r = t / opb, one contiguous R-th of the chunks (R = 256 / opb: about eight chunks per range,
+// from R = 1 for a few chunks of many outputs to R = 64 for the 1216 per-block bias partials of a few channels), in
+// chunk order with eight loads in flight, and the R range sums are added in range order. Two independent jobs share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias
 // gradient of a layer is summed in the launch that sums its weight gradient. (One thread per i summing all chunks
 // in order left a few dozen CTAs on the GPU, each thread a chain of ~190 strided loads.)
 struct SumJob {
@@ -442,7 +442,9 @@ inline SumJob sum_job(const float* part, int nchunks, long long count, float* ds
   j.dst = dst;
   j.count = count;
   j.nchunks = nchunks;
-  j.opb = count < 1024 ? 4 : (count < 32 * 152 ? 8 : 32);
+  int R = 1;
+  while (R < 64 && 8 * 2 * R <= nchunks) R *= 2;
+  j.opb = 256 / R;
   const long long b = (count + j.opb - 1) / j.opb;
   j.blocks = (int)(b < 4864 ? (b > 0 ? b : 1) : 4864);
   return j;
