@@ -411,7 +411,9 @@ claire_status claire_ws_predict_f32(claire_ws* ws, claire_ctx* ctx, const float*
                                     int kmax, void* stream);
 
 /* The network's layers one by one (used to check each against a reference). BF16 tensors are passed as void*,
- * channels-last [B][n1][n2][n3][C]; C, Cin, Cout multiples of 16 in [16, 128]; B n1 n2 n3 a multiple of 16.
+ * channels-last [B][n1][n2][n3][C]; C, Cin, Cout multiples of 16 in [16, 128]; B n1 n2 n3 a multiple of 16. The
+ * convolutions read and write 16-byte vectors: x, w, skip, y, yf, work of conv3_fwd and dz, x of conv3_wgrad must be
+ * 16-byte aligned (CLAIRE_EINVAL otherwise); the other layers take any alignment of their element type.
  * conv3_fwd: y (BF16) and/or yf (FP32; overwritten, or added to with accum = 1) = act(conv(x, w) + bias + skip),
  * w [Cout][27][Cin]; bias, skip, y, yf optional (y or yf required); work optional (see below). conv3_wgrad: dw[Cout][27][Cin] =
  * sum over voxels of dz[m][co] x[nb(m, off)][ci] (work: claire_nn_wgrad_workspace_bytes). weight_flip: wt =

@@ -18,8 +18,10 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 
 #include "impl.cuh"
@@ -36,6 +38,13 @@ constexpr int kTileK = 64;                         // voxels per K step of the w
 constexpr long long kWaitCycles = 2000000000LL;    // bound of every tensor-core wait (~1 s at 2 GHz)
 
 __device__ int g_nn_error = 0;                     // set by a CTA whose tensor-core wait timed out
+
+// true when every given pointer (null ones ignored) is a multiple of `bytes`
+inline bool aligned_to(unsigned bytes, std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs)
+    if (reinterpret_cast<uintptr_t>(p) % bytes) return false;
+  return true;
+}
 
 __device__ __forceinline__ int pw(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -617,7 +626,7 @@ __global__ void __launch_bounds__(256) k_relu_bwd_bias(const float* __restrict__
 // per-block channel sums of (dy, y, dz, dzb) as above, 16-byte rows where C allows
 inline void launch_relu_bwd_bias(const float* dy, const bf16* y, float* dz, bf16* dzb, long long M, int C,
                                  float* part, cudaStream_t st) {
-  if (C % 4 == 0) {
+  if (C % 4 == 0 && aligned_to(16, {dy, dz}) && aligned_to(8, {y, dzb})) {
     const int G = C / 4;
     k_relu_bwd_bias<4><<<kBiasBlocks, (256 / G) * G, 0, st>>>(dy, y, dz, dzb, M, C, part);
   } else {
@@ -790,7 +799,7 @@ __global__ void k_up_bwd(const float* __restrict__ dy, float* __restrict__ dx, i
 // C gradient values written (zero past cu), 16-byte stores when C allows
 __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ pred, const float* __restrict__ target,
                                              float* __restrict__ grad, long long M, int C, int cu, double inv_count,
-                                             double* __restrict__ partials) {
+                                             double* __restrict__ partials, int vec) {
   double acc = 0.0;
   const float gscale = float(2.0 * inv_count);
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M;
@@ -803,7 +812,7 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ pred, con
     }
     if (!grad) continue;
     float* g = grad + m * C;
-    if (C % 4 == 0 && cu <= 4) {
+    if (vec) {
       *reinterpret_cast<float4*>(g) = make_float4(gscale * e[0], 1 < cu ? gscale * e[1] : 0.f,
                                                   2 < cu ? gscale * e[2] : 0.f, 3 < cu ? gscale * e[3] : 0.f);
       for (int c = 4; c < C; c += 4) *reinterpret_cast<float4*>(g + c) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1245,7 +1254,7 @@ cudaError_t bias_grad(const float* dz, long long M, int C, float* db, float* wor
 
 cudaError_t pool_fwd(const bf16* x, bf16* y, const Geo& gf, int C, cudaStream_t st) {
   const Geo gc = mkgeo(gf.B, gf.n1 / 2, gf.n2 / 2, gf.n3 / 2);
-  if (C % 8 == 0)
+  if (C % 8 == 0 && aligned_to(16, {x, y}))
     k_pool_fwd<8><<<nblocks(gc.M * C / 8), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)(C / 8)));
   else
     k_pool_fwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)C));
@@ -1253,21 +1262,21 @@ cudaError_t pool_fwd(const bf16* x, bf16* y, const Geo& gf, int C, cudaStream_t 
 }
 cudaError_t pool_bwd(const float* dy, float* dx, int accum, const Geo& gf, int C, cudaStream_t st) {
   const Geo gc = mkgeo(gf.B, gf.n1 / 2, gf.n2 / 2, gf.n3 / 2);
-  if (C % 4 == 0)
+  if (C % 4 == 0 && aligned_to(16, {dy, dx}))
     k_pool_bwd<4><<<nblocks(gc.M * C / 4), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)(C / 4)));
   else
     k_pool_bwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)C));
   return cudaGetLastError();
 }
 cudaError_t up_fwd(const bf16* x, bf16* y, const Geo& gc, int C, cudaStream_t st) {
-  if (C % 8 == 0)
+  if (C % 8 == 0 && aligned_to(16, {x, y}))
     k_up_fwd<8><<<nblocks(gc.M * C / 8), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)(C / 8)));
   else
     k_up_fwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(x, y, gc, C, FastDiv((unsigned)C));
   return cudaGetLastError();
 }
 cudaError_t up_bwd(const float* dy, float* dx, int accum, const Geo& gc, int C, cudaStream_t st) {
-  if (C % 4 == 0)
+  if (C % 4 == 0 && aligned_to(16, {dy, dx}))
     k_up_bwd<4><<<nblocks(gc.M * C / 4), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)(C / 4)));
   else
     k_up_bwd<1><<<nblocks(gc.M * C), 256, 0, st>>>(dy, dx, accum, gc, C, FastDiv((unsigned)C));
@@ -1276,7 +1285,8 @@ cudaError_t up_bwd(const float* dy, float* dx, int accum, const Geo& gc, int C, 
 
 cudaError_t mse(const float* pred, const float* target, float* grad, long long M, int C, int cu, double* partials,
                 int nb, cudaStream_t st) {
-  k_mse<<<nb, 256, 0, st>>>(pred, target, grad, M, C, cu, 1.0 / double(M * cu), partials);
+  const int vec = C % 4 == 0 && cu <= 4 && aligned_to(16, {grad});
+  k_mse<<<nb, 256, 0, st>>>(pred, target, grad, M, C, cu, 1.0 / double(M * cu), partials, vec);
   return cudaGetLastError();
 }
 
@@ -1353,6 +1363,7 @@ claire_status claire_nn_conv3_fwd(const void* x, const void* w, const float* bia
                                   float* yf, int accum, int B, int n1, int n2, int n3, int Cin, int Cout, int relu,
                                   float* work, void* stream) {
   if (!x || !w || (!y && !yf) || !geo_args(B, n1, n2, n3)) return CLAIRE_EINVAL;
+  if (!aligned_to(16, {x, w, skip, y, yf, work}) || !aligned_to(4, {bias})) return CLAIRE_EINVAL;
   const Geo g = mkgeo(B, n1, n2, n3);
   if (!conv_geo_ok(g) || !conv_chan_ok(Cin) || !conv_chan_ok(Cout)) return CLAIRE_EINVAL;
   return st_of(conv3_fwd(static_cast<const bf16*>(x), static_cast<const bf16*>(w), bias,
@@ -1370,6 +1381,7 @@ size_t claire_nn_wgrad_workspace_bytes(int B, int n1, int n2, int n3, int Cin, i
 claire_status claire_nn_conv3_wgrad(const void* dz, const void* x, float* dw, float* work, int B, int n1, int n2,
                                     int n3, int Cin, int Cout, void* stream) {
   if (!dz || !x || !dw || !work || !geo_args(B, n1, n2, n3)) return CLAIRE_EINVAL;
+  if (!aligned_to(16, {dz, x}) || !aligned_to(4, {dw, work})) return CLAIRE_EINVAL;
   const Geo g = mkgeo(B, n1, n2, n3);
   if (!conv_geo_ok(g) || !conv_chan_ok(Cin) || !conv_chan_ok(Cout)) return CLAIRE_EINVAL;
   return st_of(conv3_wgrad(static_cast<const bf16*>(dz), static_cast<const bf16*>(x), dw, work, g, Cin, Cout,

@@ -81,6 +81,20 @@ def test_radix_support_matches_the_batched_grids():
         assert m == 1 and (n // 2) * 2 == n
 
 
+def test_convolutions_reject_pointers_off_the_16_byte_grid(L):
+    """Host-only: the convolutions move 16-byte vectors, so a tensor pointer that is not 16-byte aligned is refused
+    before any device work (the pointers below are never dereferenced)."""
+    f = L.claire_nn_conv3_fwd
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_int] * 8 + [ctypes.c_void_p, ctypes.c_void_p]
+    assert f(0x10002, 0x20000, None, None, 0x30000, None, 0, 1, 16, 16, 16, 16, 16, 0, None, None) == 1
+    assert f(0x10000, 0x20000, None, None, 0x30008, None, 0, 1, 16, 16, 16, 16, 16, 0, None, None) == 1
+    g = L.claire_nn_conv3_wgrad
+    g.restype = ctypes.c_int
+    g.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] * 6 + [ctypes.c_void_p]
+    assert g(0x10004, 0x20000, 0x30000, 0x40000, 1, 16, 16, 16, 16, 16, None) == 1
+
+
 def test_convolution_workspaces_follow_the_batch_invariant_split_rule(L):
     """Host-only sizing of the convolution workspaces (no device call). The forward split-K over the 27 neighbour
     offsets is chosen from the per-sample grid alone, so a sample's result does not depend on its batch: the

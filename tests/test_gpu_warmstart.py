@@ -175,6 +175,12 @@ def test_pool_up_channel_widths(ws_mod, C):
     acc = cg.clone()
     ws_mod.up_bwd(dyg, dx=acc, accum=True)
     assert np.allclose(host(acc), c + W.up_adjoint(dy), rtol=1e-5, atol=1e-6)
+    # storage off the 16-byte grid takes the single-channel kernels: the same values
+    buf = torch.empty(yg.numel() + 1, dtype=yg.dtype, device="cuda")
+    ym = buf[1:].view(yg.shape)
+    ym.copy_(yg)
+    assert torch.equal(ws_mod.pool_fwd(ym), ws_mod.pool_fwd(yg))
+    assert torch.equal(ws_mod.up_fwd(ym), ws_mod.up_fwd(yg))
 
 
 def test_mse_and_adam(ws_mod):
