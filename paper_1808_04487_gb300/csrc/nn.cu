@@ -355,13 +355,34 @@ __global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restric
     const Nbr nb = nbr_of(g, vox_of(g, valid ? mv : c0));
     // issue this step's loads before waiting for the stage
     uint4 va[8], vb[8];
+    if constexpr (CIN > 0) {
+      // half h stages the A vectors v = 8 h .. 8 h + 7 of its voxel (v = j CV + cv: offset j, channel vector cv),
+      // so one neighbour index serves the CV vectors of an offset
+      constexpr int CV = CIN / 8;
+      if constexpr (CV <= 8) {
+        const bf16* row = x;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int v = half + 2 * q;
-      va[q] = make_uint4(0u, 0u, 0u, 0u);
-      if (valid && v < nva) {
-        const int j = v / cvec, cv = v - j * cvec;
-        va[q] = *reinterpret_cast<const uint4*>(x + (long long)nb_of(g, nb, off_first + j) * Cin + 8 * cv);
+        for (int q = 0; q < 8; ++q) {
+          const int j = half * (8 / CV) + q / CV;
+          if (q % CV == 0) row = x + (long long)nb_of(g, nb, off_first + (j < ng ? j : 0)) * CIN;
+          va[q] = (valid && j < ng) ? *reinterpret_cast<const uint4*>(row + 8 * (q % CV)) : make_uint4(0u, 0u, 0u, 0u);
+        }
+      } else {
+        // one offset of 16 channel vectors: half h takes vectors 8 h .. 8 h + 7
+        const bf16* row = x + (long long)nb_of(g, nb, off_first) * CIN + 64 * half;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          va[q] = valid ? *reinterpret_cast<const uint4*>(row + 8 * q) : make_uint4(0u, 0u, 0u, 0u);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int v = half + 2 * q;
+        va[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (valid && v < nva) {
+          const int j = v / cvec, cv = v - j * cvec;
+          va[q] = *reinterpret_cast<const uint4*>(x + (long long)nb_of(g, nb, off_first + j) * Cin + 8 * cv);
+        }
       }
     }
 #pragma unroll
@@ -382,12 +403,11 @@ __global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restric
     const uint32_t koff_a = (uint32_t)(k >> 3) * a_kgroup + kpos, koff_b = (uint32_t)(k >> 3) * b_kgroup + kpos;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int v = half + 2 * q;
-      if (v < nva) {
-        const int j = v / cvec, cv = v - j * cvec;
-        *reinterpret_cast<uint4*>(As + ((j * Cin + 8 * cv) >> 3) * 128 + koff_a) = va[q];
-      }
-      if (v < nvb) *reinterpret_cast<uint4*>(Bs + v * 128 + koff_b) = vb[q];
+      // A vector v (offset j, channel vector cv) is core-matrix row group (j Cin + 8 cv) / 8 = v
+      const int v = CIN > 0 ? 8 * half + q : half + 2 * q;
+      if (v < nva) *reinterpret_cast<uint4*>(As + v * 128 + koff_a) = va[q];
+      const int vbv = half + 2 * q;
+      if (vbv < nvb) *reinterpret_cast<uint4*>(Bs + vbv * 128 + koff_b) = vb[q];
     }
     tc::fence_smem_to_async();
     __syncthreads();
@@ -436,8 +456,9 @@ __global__ void __launch_bounds__(128, 5) k_conv3_wgrad_tc(const bf16* __restric
 // Fixed-order sums over chunks: dst[i] = sum_c part[c][i]. A 256-thread CTA takes opb consecutive outputs i;
 // thread t sums range r = t / opb, one contiguous R-th of the chunks (R = 256 / opb: about eight chunks per range,
 // from R = 1 for a few chunks of many outputs to R = 64 for the 1216 per-block bias partials of a few channels), in
-// chunk order with eight loads in flight, and the R range sums are added in range order. Two independent jobs share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias
-// gradient of a layer is summed in the launch that sums its weight gradient. (One thread per i summing all chunks
+// chunk order with eight loads in flight, and the R range sums are added in range order. Two independent jobs
+// share one launch (CTAs [0, a.blocks) take job a, the rest job b), so the bias gradient of a layer is summed in
+// the launch that sums its weight gradient. (One thread per i summing all chunks
 // in order left a few dozen CTAs on the GPU, each thread a chain of ~190 strided loads.)
 struct SumJob {
   const float* part;
