@@ -1011,11 +1011,20 @@ inline bool halo_fits(const Geo& g, int Cin, int Cout) {
   return Cin % 16 == 0 && Cin <= 64 && g.n3 % 8 == 0 && g.n2 % 16 == 0 && 27LL * Cout * Cin * 2 <= 110592 &&
          halo_smem(Cin, Cout, 1) <= 227 * 1024;
 }
-// tile planes per CTA: two where the grid has enough tiles for several waves of two-plane CTAs and the halo stays
-// small, else one
+// tile planes per CTA: four or two where the grid has enough tiles for about three or four CTAs per SM of that
+// size and the halo stays small (C_in <= 32), else one
+// the CTAs that fit an SM by shared memory also fit its 512 tensor-memory columns (tz Cout accumulator columns each)
+inline bool halo_planes_fit(int Cin, int Cout, int tz) {
+  const size_t sm = halo_smem(Cin, Cout, tz);
+  if (sm > 227 * 1024) return false;
+  const size_t ctas = (228 * 1024) / (sm + 1024);
+  return ctas * tc::tmem_cols(tz * Cout) <= 512;
+}
 inline int halo_tz(const Geo& g, int Cin, int Cout) {
   const long long tiles = (long long)(g.n3 / 8) * (g.n2 / 16) * g.n1 * g.B;
-  return (g.n1 % 2 == 0 && Cin <= 32 && tiles / 2 >= 4 * 152 && halo_smem(Cin, Cout, 2) <= 227 * 1024) ? 2 : 1;
+  if (Cin > 32) return 1;
+  if (g.n1 % 4 == 0 && tiles / 4 >= 3 * 152 && halo_planes_fit(Cin, Cout, 4)) return 4;
+  return (g.n1 % 2 == 0 && tiles / 2 >= 4 * 152 && halo_planes_fit(Cin, Cout, 2)) ? 2 : 1;
 }
 
 template <int CIN>  // CIN > 0: the input channel count at compile time (constant divisors), else Cin_rt

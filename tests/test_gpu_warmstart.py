@@ -51,8 +51,9 @@ CONV_CASES = [((2, 6, 5, 8), 16, 16), ((1, 3, 4, 4), 32, 48), ((2, 6, 5, 8), 64,
 # weights within 108 KB)
 HALO_CASES = [((2, 4, 16, 8), 16, 16), ((1, 3, 16, 16), 32, 64), ((2, 2, 32, 8), 64, 32), ((1, 4, 16, 8), 16, 128),
               ((1, 2, 16, 24), 48, 16)]
-# grids with enough tiles (at least 4 x 152 two-plane CTAs, n1 even, Cin <= 32) for two tile planes per CTA
-HALO_TZ2_CASES = [((4, 38, 16, 64), 16, 16), ((2, 38, 16, 128), 32, 16)]
+# grids with enough tiles (Cin <= 32; n1 even and at least 4 x 152 two-plane CTAs, or n1 a multiple of 4 and at
+# least 3 x 152 four-plane CTAs, as the last case) for two or four tile planes per CTA
+HALO_TZ2_CASES = [((4, 38, 16, 64), 16, 16), ((2, 38, 16, 128), 32, 16), ((4, 32, 16, 128), 16, 16)]
 
 
 @pytest.mark.parametrize("shape,cin,cout", CONV_CASES + HALO_CASES + HALO_TZ2_CASES)
