@@ -990,7 +990,7 @@ inline int fwd_offsets_per_split(const Geo& g) {
 inline size_t wgrad_smem(int Cout) { return 1024 + 2 * (size_t(kTileM) * kTileK * 2 + size_t(Cout) * kTileK * 2) + 32; }
 
 // ---- forward convolution from a shared-memory halo -----------------------------------------------------------
-// A CTA covers tz (1 or 2) planes of a tile of 8 (i3) x 16 (i2) voxels of one sample (128 rows of the implicit
+// A CTA covers tz (1, 2 or 4) planes of a tile of 8 (i3) x 16 (i2) voxels of one sample (128 rows of the implicit
 // GEMM per plane, each plane its own TMEM accumulator). Its input halo -- the 10 x 18 x (tz + 2) voxels around the
 // tile, periodic -- is loaded once, as Cin/8 planes of 16-byte voxel rows (8 channels each):
 // [plane][hz][hy][hx] x 16 B. In that layout the A operand of every neighbour offset is a shifted view of the halo
@@ -999,7 +999,7 @@ inline size_t wgrad_smem(int Cout) { return 1024 + 2 * (size_t(kTileM) * kTileK 
 // halo row of 10 voxels = 160 B -- so no per-offset staging is needed: one thread issues the 27 Cin / 16 MMAs per
 // tile plane back to back against the resident weights (K-major [Cout][27 Cin]). The MMAs of a voxel run in the K
 // order of k_conv3_fwd_tc (offsets ascending, 16 channels at a time), so its accumulator and result are the same;
-// two planes share one weight load and read (tz + 2) / tz halo rows per voxel row instead of 3.
+// the tz planes share one weight load and read (tz + 2) / tz halo rows per voxel row instead of 3.
 constexpr int kHaloRowsPerZ = 18 * 10;
 inline int halo_rows(int tz) { return (tz + 2) * kHaloRowsPerZ; }
 
